@@ -1,0 +1,346 @@
+"""Benchmark: Strassen C = A.B at n = 16384, FP32 inputs N(0,1), 3xBF16 split
+leaves on the tcgen05 tensor cores, through libstark.so.
+
+One step = one full product (zero C, divide A and B into every leaf operand,
+one leaf-product launch with the combine fused in its epilogue) on inputs
+already resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n 16384] [--depth 2] [--dtype bf16|tf32]
+
+Multi-GPU (torchrun, one rank per GPU): every rank multiplies its own
+independent pair of matrices (the units of this workload are independent
+products), no collective on the data path; value = all ranks' flops / the
+slowest rank's time ("scaling": "weak").
+
+--impl reference times the CPU oracle (plain C, the classical FP64 triple
+loop that defines the result) on the host cores, on a bounded sample of rows
+of the same product per step, reported in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective TFLOP/s (2n³/t) at n=16384, stated error vs FP64; p50/p99 serve latency"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n, seed, budget_s=12.0, rows_cap=256):
+    """The oracle's classical FP64 row product on the host cores, on a bounded
+    row sample of the n x n workload; eff TFLOP/s = 2 n^2 rows / t."""
+    import oracle
+    from paper_1811_07325_gb300 import synth
+    A = synth.normal(n, seed, 0)
+    B = synth.normal(n, seed, 1)
+    oracle.gemm_rows(A, B, np.arange(min(4, n)))  # warm (page-in, thread pool)
+    t0 = time.perf_counter()
+    oracle.gemm_rows(A, B, np.arange(min(16, n)))
+    per_row = (time.perf_counter() - t0) / min(16, n)
+    rows = int(max(16, min(rows_cap, budget_s / max(per_row, 1e-9))))
+    idx = synth.sample_rows(n, rows, seed + 1)
+    t0 = time.perf_counter()
+    oracle.gemm_rows(A, B, idx)
+    t = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 2.0 * n * n * rows / t / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"classical FP64 row products (C rows = A rows . B), {rows} of {n} rows, "
+                      f"{t:.1f} s on {threads} OpenMP threads"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle, timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1811_07325_gb300 import synth
+    n = args.n
+    A = synth.normal(n, args.seed, 0)
+    B = synth.normal(n, args.seed, 1)
+    rows_per_step = args.ref_rows
+    for w in range(args.warmup):
+        oracle.gemm_rows(A, B, np.arange(rows_per_step) + w * rows_per_step)
+    times = []
+    for k in range(args.steps):
+        idx = (np.arange(rows_per_step) + k * rows_per_step) % n
+        t0 = time.perf_counter()
+        oracle.gemm_rows(A, B, idx)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = 2.0 * n * n * rows_per_step / t / 1e12
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"classical FP64 oracle, {rows_per_step} of {n} rows of C per step"
+    return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"strassen n={n} (CPU oracle, row-sampled)", "n": n},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--depth", type=int, default=2)
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1811_07325_gb300 import stark, synth
+
+    n, d = args.n, args.depth
+    dt = stark.DType.F32_SPLIT_BF16 if args.dtype == "bf16" else stark.DType.F32_SPLIT_TF32
+    seed = args.seed + 7919 * rank  # independent product per rank
+    A_h = torch.from_numpy(synth.normal(n, seed, 0)).pin_memory()
+    B_h = torch.from_numpy(synth.normal(n, seed, 1)).pin_memory()
+    A = A_h.cuda()
+    B = B_h.cuda()
+    C = torch.empty_like(A)
+    plan = stark.Plan(n, d, dt)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.mul(A, B, C)
+    plan.check()
+
+    # ---------------------------------------------------------------- timed region
+    plan.set_timing(args.steps)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = stark.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.mul(A, B, C)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = stark.launch_count() - launches0
+    plan.check()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phases = plan.phase_ms()
+    plan.set_timing(0)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = 2.0 * n ** 3
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---------------------------------------------------------------- error vs FP64
+    error = None
+    if not args.no_check and rank == 0:
+        import oracle
+        rows = synth.sample_rows(n, 256, args.seed + 5)
+        want = oracle.gemm_rows(A_h.numpy(), B_h.numpy(), rows)
+        got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        an = float(torch.linalg.vector_norm(A.double()).item())
+        bn = float(torch.linalg.vector_norm(B.double()).item())
+        diff = got - want
+        error = {"max_abs_over_normA_normB": float(np.abs(diff).max() / (an * bn)),
+                 "rel_rms": float(np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))),
+                 "rows_checked": int(rows.size), "reference": "oracle classical FP64 rows",
+                 "bound": 1e-6}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    C_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    plan.mul_host(A_h, B_h, C_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.mul_host(A_h, B_h, C_h)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 4,
+           "d2h_bytes_per_step": n * n * 4, "ms_per_step": e2e_s * 1e3}
+
+    # ---------------------------------------------------------------- roofline of the leaf kernel
+    pk = peaks()
+    leaf_flops = 3 * 2.0 * plan.leaves * plan.leaf ** 3  # three bf16 products per leaf
+    achieved = leaf_flops / (phases["leaf_combine"] * 1e-3) / 1e12
+    roofline = {"kernel": "leaf_tc_kernel (3xBF16 leaf GEMMs + fused combine)", "bound": "tensor",
+                "achieved": achieved, "peak": pk["bf16_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16_sustained"], "traffic": None,
+                "peak_source": f"{pk['source']} bf16 sustained",
+                "algorithmic_flops_per_launch": leaf_flops,
+                "launch_ms": phases["leaf_combine"]}
+    divide_bytes = 2 * (n * n * 4) + plan.workspace_bytes  # read A, B; write every leaf operand (hi+lo)
+
+    comparators = None
+    if not args.no_comparators and rank == 0:
+        comparators = {}
+        for name, tdt in (("torch_matmul_bf16", torch.bfloat16), ("torch_matmul_fp32", torch.float32)):
+            prev = torch.backends.cuda.matmul.allow_tf32
+            torch.backends.cuda.matmul.allow_tf32 = False
+            a, b = A.to(tdt), B.to(tdt)
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 3
+            for _ in range(reps):
+                torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            comparators[name] = flops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+            torch.backends.cuda.matmul.allow_tf32 = prev
+            del a, b
+        torch.cuda.empty_cache()
+        try:
+            a64, b64 = A.double(), B.double()
+            p64 = stark.Plan(n, 3, stark.DType.F64)
+            c64 = torch.empty_like(a64)
+            p64.mul(a64, b64, c64)
+            p64.check()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p64.mul(a64, b64, c64)
+            e1.record()
+            torch.cuda.synchronize()
+            comparators["strassen_fp64_d3"] = flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            p64.close()
+            e0.record()
+            torch.matmul(a64, b64)
+            e1.record()
+            torch.cuda.synchronize()
+            comparators["torch_matmul_fp64"] = flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            del a64, b64, c64
+        except Exception as ex:  # report, do not hide
+            comparators["fp64_error"] = str(ex)
+        comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, args.seed)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32 in/out, 3xbf16 tensor-core leaves, fp32 accumulate"
+               if args.dtype == "bf16" else "f32 in/out, 3xtf32 tensor-core leaves, fp32 accumulate",
+               "data": "synthetic",
+               "config": {"workload": f"strassen n={n} depth={plan.depth} fp32 N(0,1) split-{args.dtype}",
+                          "n": n, "depth": plan.depth, "leaves": plan.leaves, "leaf": plan.leaf,
+                          "tile": list(plan.tile), "per_rank": "one independent product per rank",
+                          "l2": "inputs (2 x 1 GiB) and workspace larger than L2; no flush needed"},
+               "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+               "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
+               "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
+               "error_vs_fp64": error, "comparators": comparators, "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * stark.h -- C ABI of libstark.so: Strassen matrix multiplication C = A*B on
+ * one NVIDIA GB300 (sm_103a), after "Stark: Fast and Scalable Strassen's
+ * Matrix Multiplication using Apache Spark" (arXiv 1811.07325).
+ *
+ * The method (Alg. 1, Sec. III-A): split A and B into 2x2 quadrants, form the
+ * operand sums of the seven products M1..M7, multiply, and recombine
+ * C11 = M1+M4-M5+M7, C12 = M3+M5, C21 = M2+M4, C22 = M1-M2+M3+M6 (the paper
+ * prints -M3 in C22; +M3 is the identity that equals A*B).  Recursing `depth`
+ * times gives 7^depth leaf products of side L = n_pad / 2^depth.  Stark runs
+ * every recursion level at once by tagging blocks with their M-index path
+ * (Sec. III-B, Alg. 3-5); here the tags are a device-resident table, the
+ * divide phase is one kernel that writes every leaf operand, the leaves are
+ * one tensor-core launch, and the combine runs in that launch's epilogue.
+ *
+ * Conventions (all entry points):
+ *  - Matrices are square, row-major, contiguous, leading dimension n.
+ *  - "Device pointer" means memory of the current CUDA device; "host pointer"
+ *    means ordinary (preferably pinned) host memory.  The caller owns every
+ *    pointer it passes; the library never frees caller memory.
+ *  - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *    default stream).  Calls taking a stream are asynchronous on it unless
+ *    stated otherwise; inputs must stay alive and unmodified until the work
+ *    completes on that stream.
+ *  - Every call returns a stark_status; no call aborts the process.  CUDA
+ *    runtime failures map to STARK_ECUDA, a device-side timeout (a bounded
+ *    wait inside a kernel that gave up) to STARK_ETIMEOUT.
+ *  - A plan may be used by one stream at a time; different plans are
+ *    independent.
+ */
+#ifndef STARK_H
+#define STARK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STARK_API __attribute__((visibility("default")))
+#else
+#define STARK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  STARK_F64 = 0,            /* fp64 in/out; fp64 leaves on CUDA cores                  */
+  STARK_F32_SPLIT_BF16 = 1, /* fp32 in/out; leaves as 3 bf16 products (hi*hi + hi*lo +  */
+                            /* lo*hi, x = hi + lo) on tcgen05 tensor cores, fp32 accum. */
+  STARK_F32_SPLIT_TF32 = 2, /* fp32 in/out; the same with TF32 halves                   */
+  STARK_I64 = 3             /* int64 in/out; exact modulo 2^64 (two's complement)       */
+} stark_dtype;
+
+typedef enum {
+  STARK_OK = 0,
+  STARK_EINVAL = 1,      /* bad argument (null pointer, n < 0, depth out of range, ...) */
+  STARK_ENOMEM = 2,      /* device or host allocation failed, or over the memory budget */
+  STARK_EUNSUPPORTED = 3,/* valid request this build or device cannot serve            */
+  STARK_ETIMEOUT = 4,    /* a bounded device-side wait expired; results are invalid    */
+  STARK_EBUSY = 5,       /* the request is still queued or running                      */
+  STARK_ENOTFOUND = 6,   /* unknown request id                                           */
+  STARK_ECUDA = 7        /* a CUDA runtime call failed                                   */
+} stark_status;
+
+typedef struct stark_plan_s *stark_plan_t;
+
+/* What a plan decided; filled by stark_plan_get_info. */
+typedef struct {
+  int64_t n;               /* problem side                                              */
+  int64_t n_pad;           /* padded side: multiple of 2^depth * tile granularity       */
+  int64_t leaf;            /* L = n_pad / 2^depth                                        */
+  int32_t depth;           /* recursion levels                                           */
+  int32_t dtype;           /* stark_dtype                                                 */
+  int64_t leaves;          /* 7^depth                                                    */
+  int64_t workspace_bytes; /* device bytes the plan owns (leaf operands, tables, ...)    */
+  int32_t tile_m, tile_n;  /* leaf GEMM output tile                                      */
+  int32_t reserved[6];
+} stark_plan_info;
+
+/* ----------------------------------------------------------------- plans */
+
+/* Build a plan for n x n products with `depth` recursion levels (Alg. 1 /
+ * Alg. 2: depth = log2 of the number of partitions per side, the paper's
+ * p - q).  depth = -1 lets the library choose (cost model over the leaf
+ * GEMM and divide traffic).  depth 0 multiplies classically (one leaf).
+ * Allocates the plan's device workspace on the current device.
+ * Errors: EINVAL (n < 0 or > 2^20, depth < -1 or > 4, unknown dtype, out == NULL),
+ * ENOMEM, ECUDA, EUNSUPPORTED (current device is not a GB300 / sm_103). */
+STARK_API stark_status stark_plan_create(int64_t n, int depth, stark_dtype dtype, stark_plan_t *out);
+
+/* Release a plan and its workspace (waits for the device to finish using it).
+ * NULL is accepted and ignored. */
+STARK_API stark_status stark_plan_destroy(stark_plan_t plan);
+
+STARK_API stark_status stark_plan_get_info(stark_plan_t plan, stark_plan_info *info);
+
+/* C = A * B.  A, B, C: device pointers to n x n matrices of the plan's
+ * element type (double, float, float, int64_t).  C is overwritten; it may not
+ * alias A or B.  Enqueues: zero C, divide A, divide B, one leaf-product launch
+ * whose epilogue accumulates every leaf into C with the combine signs.
+ * Asynchronous on `stream`; capturable in a CUDA graph (no allocation, no
+ * synchronisation).  n == 0 is a no-op. */
+STARK_API stark_status stark_mul(stark_plan_t plan, const void *A, const void *B, void *C, void *stream);
+
+/* The same product, end to end from host memory: copies A and B host->device
+ * into plan-owned buffers, runs stark_mul, copies C device->host and waits
+ * for completion.  A, B, C: host pointers (pinned memory gives full copy
+ * bandwidth).  Synchronous. */
+STARK_API stark_status stark_mul_host(stark_plan_t plan, const void *A, const void *B, void *C, void *stream);
+
+/* Partial product for sharding the leaves across devices (the independent
+ * products of one recursion tree, Sec. III-C): C = sum over leaves l in
+ * [leaf_begin, leaf_end) of that leaf's signed combine contributions.
+ * Summing the C of any partition of [0, 7^depth) gives A*B.  Same pointer
+ * rules as stark_mul. */
+STARK_API stark_status stark_mul_leaves(stark_plan_t plan, const void *A, const void *B, void *C, int64_t leaf_begin,
+                              int64_t leaf_end, void *stream);
+
+/* Divide phase only (Alg. 3): writes every leaf operand of A and of B into
+ * the plan's workspace and returns read-only device pointers to it, for
+ * inspection by tests.  Layout: split dtypes hold [2*leaves][L][L] planes
+ * (hi planes, then lo planes; bf16 values, or TF32 values in fp32
+ * containers); F64/I64 hold [leaves][L][L].  A planes are row-major (the
+ * leaf's M x K operand); B planes are row-major K x N for F64/I64 and
+ * transposed (N x K) for the split dtypes.  The pointers stay valid until the
+ * plan is destroyed and are overwritten by the next product. */
+STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, const void *B, void *stream, const void **X,
+                                 const void **Y);
+
+/* Synchronise the plan's last stream and report any device-side error
+ * (STARK_ETIMEOUT) recorded by its kernels since the previous check; the
+ * error word is cleared. */
+STARK_API stark_status stark_plan_check(stark_plan_t plan, void *stream);
+
+/* Per-phase device timing with CUDA events recorded on the product's own
+ * stream.  stark_plan_set_timing(plan, k) pre-creates k event sets and
+ * records the phases of the next k products (k = 0 switches timing off);
+ * stark_plan_phase_ms waits for the last recorded product and returns the
+ * mean over the recorded products of: [0] zeroing C, [1] divide A and B,
+ * [2] leaf products with the fused combine.  Errors: EINVAL when nothing was
+ * recorded. */
+STARK_API stark_status stark_plan_set_timing(stark_plan_t plan, int records);
+STARK_API stark_status stark_plan_phase_ms(stark_plan_t plan, float out_ms[3]);
+
+/* ----------------------------------------------------------------- tables */
+
+/* The quadrant-index table ("block tags", Sec. III-B) for `depth` levels,
+ * computed on the host; no device is needed.  For leaf l (base-7 M-index
+ * path, top level most significant, so parent = l / 7 as in Alg. 5) and
+ * side s (0: A-operand terms, 1: B-operand terms, 2: C targets), entries
+ * [l*2^depth, l*2^depth + count[l]) of quad/sign list the quadrant paths q
+ * (base-4, digit 0..3 = 11,12,21,22, top level most significant) and signs.
+ * Arrays: count[7^depth], quad[7^depth * 2^depth], sign[7^depth * 2^depth]. */
+STARK_API stark_status stark_quadrant_table(int depth, int side, int32_t *count, int32_t *quad, int8_t *sign);
+
+/* ----------------------------------------------------------------- misc */
+
+STARK_API const char *stark_strerror(stark_status status);
+
+/* Self-check of the bounded device wait used by every kernel: launches one
+ * tiny kernel that waits on a device flag nothing sets, with a limit of
+ * `timeout_ns`, and synchronises.  Returns STARK_ETIMEOUT when the wait gave
+ * up and reported it as designed (the CUDA context stays usable);
+ * STARK_OK would mean the flag was seen set, which cannot happen. */
+STARK_API stark_status stark_selftest_bounded_wait(uint64_t timeout_ns);
+
+/* Number of kernels this library launched in this process so far. */
+STARK_API int64_t stark_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STARK_H */

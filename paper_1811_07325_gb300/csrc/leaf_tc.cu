@@ -1,0 +1,293 @@
+// leaf_tc.cu -- the leaf products M_l = X_l * Y_l of every leaf (Alg. 4,
+// "MulBlockMat") on the tcgen05 tensor cores, with the combine of Alg. 5
+// fused into the epilogue: each finished accumulator tile is added, with its
+// sign, into every C quadrant the leaf contributes to (the C targets of the
+// quadrant-index table), so no M_l is ever written to memory.
+//
+// Operands come from the divide kernel as split planes: X = X_hi + X_lo,
+// Y = Y_hi + Y_lo (bf16 halves, or tf32 halves in fp32 containers), and
+//   M ~= X_lo Y_hi + X_hi Y_lo + X_hi Y_hi
+// accumulates in fp32 in tensor memory (the lo*lo term is below fp32
+// resolution of the result and is dropped).  Both operands are K-major: the
+// X planes are row-major (M x K) and the Y planes are stored transposed
+// (N x K) by the divide kernel.
+//
+// Persistent kernel, one CTA per SM, warp-specialised:
+//   warp 0      TMA producer: per k-block, 4 tiles (X_hi, X_lo, Y_hi, Y_lo)
+//               into a STAGES-deep shared-memory ring (128-byte swizzle)
+//   warp 1      TMEM allocator + single-thread MMA issuer (3 MMAs per K=16
+//               (bf16) or K=8 (tf32) step), double-buffered accumulators
+//   warps 2..5  epilogue: tcgen05.ld the accumulator, signed vector atomics
+//               into C for every target of the leaf
+// Every mbarrier wait is bounded; on expiry the kernel records an error,
+// drains its in-flight copies and MMAs, frees TMEM and returns.
+#include "ptx.cuh"
+#include "stark_internal.h"
+
+namespace stark {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kThreads = 192;
+
+template <int BN, int STAGES, bool TF32>
+struct TcCfg {
+  static constexpr int BK = TF32 ? 32 : 64;         // elements per 128-byte row
+  static constexpr int A_BYTES = kBM * 128;          // one operand half tile
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int KSTEP_BYTES = 32;             // one MMA's K slice (16 bf16 / 8 tf32)
+  static constexpr int KSTEPS = 128 / KSTEP_BYTES;   // 4 MMAs (x3) per stage
+  static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
+  static constexpr int BAR_BYTES = 8 * (2 * STAGES + 4) + 16;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
+  static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32>();
+};
+
+template <int BN, int STAGES, bool TF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const LeafTcArgs p) {
+  using Cfg = TcCfg<BN, STAGES, TF32>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the 128-byte swizzle atoms
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar_base = sbase + STAGES * Cfg::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar_base + 8 * s; };
+  auto empty_bar = [&](int s) { return bar_base + 8 * (STAGES + s); };
+  auto accf_bar = [&](int a) { return bar_base + 8 * (2 * STAGES + a); };
+  auto acce_bar = [&](int a) { return bar_base + 8 * (2 * STAGES + 2 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * Cfg::STAGE_BYTES + 8 * (2 * STAGES + 4));
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+
+  const int tiles_m = p.L / kBM;
+  const int tiles_n = p.L / BN;
+  const int per_leaf = tiles_m * tiles_n;
+  const int num_items = (p.leaf_end - p.leaf_begin) * per_leaf;
+  const int kblocks = p.L / Cfg::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(accf_bar(a), 1);
+      mbar_init(acce_bar(a), 128);
+    }
+    fence_mbar_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_normal();
+      int s = 0;
+      uint32_t phase = 0;
+      uint32_t armed = 0, armed_phase = 0;  // per-stage: ever armed / parity of last arming
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
+        const int leaf = p.leaf_begin + item / per_leaf;
+        const int rem = item % per_leaf;
+        const int m0 = (rem / tiles_n) * kBM;
+        const int n0 = (rem % tiles_n) * BN;
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+          mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
+          const int k0 = kb * Cfg::BK;
+          tma_load_3d(st, &tmA, k0, m0, leaf, full_bar(s), pol);
+          tma_load_3d(st + Cfg::A_BYTES, &tmA, k0, m0, p.P + leaf, full_bar(s), pol);
+          tma_load_3d(st + 2 * Cfg::A_BYTES, &tmB, k0, n0, leaf, full_bar(s), pol);
+          tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB, k0, n0, p.P + leaf, full_bar(s), pol);
+          armed |= 1u << s;
+          armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
+          if (++s == STAGES) {
+            s = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        // let every copy already issued land before the CTA can exit
+        for (int t = 0; t < STAGES; ++t)
+          if (armed & (1u << t)) mbar_wait_bounded(full_bar(t), (armed_phase >> t) & 1, nullptr, 0, 200000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
+        if (!mbar_wait_bounded(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait_bounded(full_bar(s), phase, p.err, kDevTimeoutFull, p.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+#pragma unroll
+          for (int k = 0; k < Cfg::KSTEPS; ++k) {
+            const uint32_t off = k * Cfg::KSTEP_BYTES;
+            const uint64_t a_hi = smem_desc_k_sw128(st + off);
+            const uint64_t a_lo = smem_desc_k_sw128(st + Cfg::A_BYTES + off);
+            const uint64_t b_hi = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + off);
+            const uint64_t b_lo = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + off);
+            const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+            if constexpr (TF32) {
+              mma_tf32(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
+              mma_tf32(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
+              mma_tf32(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
+            } else {
+              mma_f16(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
+              mma_f16(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
+              mma_f16(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
+            }
+          }
+          issued = true;
+          mma_commit(empty_bar(s));  // stage free once these MMAs have read it
+          if (++s == STAGES) {
+            s = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(accf_bar(acc));  // accumulator complete
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+      if (!ok && issued) {
+        // Let the MMAs in flight finish before TMEM is released: commit to
+        // the accumulator-full barrier of the current buffer (whose pending
+        // phase has parity acc_phase) and wait for that phase, briefly.
+        mma_commit(accf_bar(acc));
+        mbar_wait_bounded(accf_bar(acc), acc_phase, nullptr, 0, 200000000ull);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int row_in_tile = quarter * 32 + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int item = blockIdx.x; item < num_items; item += gridDim.x) {
+      if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
+      tc_fence_after();
+      const int leaf = p.leaf_begin + item / per_leaf;
+      const int rem = item % per_leaf;
+      const int m0 = (rem / tiles_n) * kBM;
+      const int n0 = (rem % tiles_n) * BN;
+      const int nt = p.ccount[leaf];
+      const CTarget* tg = p.ctab + (int64_t)leaf * p.maxT;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) && ((p.ldc & 3) == 0);
+#pragma unroll 1
+      for (int chunk = 0; chunk < BN / 32; ++chunk) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + chunk * 32), r);
+        tmem_ld_wait();
+#pragma unroll 1
+        for (int t = 0; t < nt; ++t) {
+          const CTarget c = tg[t];
+          const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
+          const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
+          if (grow >= p.n || gcol >= p.n) continue;
+          float* dst = p.C + grow * p.ldc + gcol;
+          const float sg = (float)c.sign;
+          if (vec_ok && gcol + 32 <= p.n) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
+                                     sg * __uint_as_float(r[4 * j + 2]), sg * __uint_as_float(r[4 * j + 3]));
+              atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
+            }
+          } else {
+            const int64_t lim = p.n - gcol;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce_bar(acc));
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+}
+
+template <int BN, int STAGES, bool TF32>
+cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int num_sms,
+                       cudaStream_t st) {
+  using Cfg = TcCfg<BN, STAGES, TF32>;
+  if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  const int64_t items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM) * (a.L / BN);
+  if (items <= 0) return cudaSuccess;
+  if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int leaf_tc_smem_bytes(bool tf32, int bn) {
+  if (bn == 256) return tf32 ? TcCfg<256, 2, true>::SMEM : TcCfg<256, 2, false>::SMEM;
+  return tf32 ? TcCfg<128, 3, true>::SMEM : TcCfg<128, 3, false>::SMEM;
+}
+
+cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, bool tf32, int bn,
+                           int num_sms, cudaStream_t st) {
+  if (bn == 256) {
+    return tf32 ? launch_cfg<256, 2, true>(a, tmA, tmB, num_sms, st)
+                : launch_cfg<256, 2, false>(a, tmA, tmB, num_sms, st);
+  }
+  if (bn == 128) {
+    return tf32 ? launch_cfg<128, 3, true>(a, tmA, tmB, num_sms, st)
+                : launch_cfg<128, 3, false>(a, tmA, tmB, num_sms, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace stark

@@ -1,0 +1,535 @@
+// plan.cu -- plans (stark_plan_*), the product entry points (stark_mul*),
+// the quadrant-index table and small utilities of the C ABI.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "plan.h"
+#include "ptx.cuh"
+#include "stark_internal.h"
+
+namespace stark {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+bool device_is_sm100_family() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;  // this build carries sm_103a code only
+}
+
+// ------------------------------------------------------------------ tables
+
+void build_quadrant_table(int depth, int side, std::vector<int32_t>& count, std::vector<int32_t>& quad,
+                          std::vector<int8_t>& sign) {
+  int64_t P = 1;
+  for (int k = 0; k < depth; ++k) P *= 7;
+  const int maxT = 1 << depth;
+  count.assign((size_t)P, 0);
+  quad.assign((size_t)(P * maxT), 0);
+  sign.assign((size_t)(P * maxT), 0);
+  for (int64_t l = 0; l < P; ++l) {
+    // digits, top level first
+    int dig[8] = {0};
+    int64_t x = l;
+    for (int k = depth - 1; k >= 0; --k) {
+      dig[k] = (int)(x % 7);
+      x /= 7;
+    }
+    // enumerate the product of the per-level term lists
+    std::vector<std::pair<int32_t, int>> cur{{0, 1}};
+    for (int k = 0; k < depth; ++k) {
+      std::vector<std::pair<int32_t, int>> nxt;
+      for (auto& e : cur)
+        for (int q = 0; q < 4; ++q) {
+          const int c = side == 0 ? coef_a(dig[k], q) : side == 1 ? coef_b(dig[k], q) : coef_c(dig[k], q);
+          if (c != 0) nxt.push_back({e.first * 4 + q, e.second * c});
+        }
+      cur.swap(nxt);
+    }
+    count[(size_t)l] = (int32_t)cur.size();
+    for (size_t t = 0; t < cur.size(); ++t) {
+      quad[(size_t)(l * maxT) + t] = cur[t].first;
+      sign[(size_t)(l * maxT) + t] = (int8_t)cur[t].second;
+    }
+  }
+}
+
+void quadrant_offsets(int depth, int64_t npad, int32_t q, int64_t* row, int64_t* col) {
+  int64_t r = 0, c = 0;
+  for (int k = 1; k <= depth; ++k) {
+    const int digit = (q >> (2 * (depth - k))) & 3;
+    r += (int64_t)(digit >> 1) * (npad >> k);
+    c += (int64_t)(digit & 1) * (npad >> k);
+  }
+  *row = r;
+  *col = c;
+}
+
+// ------------------------------------------------------------------ TMA maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// planes [planes][L][L] of bf16 (or fp32 holding tf32), K innermost; box =
+// one 128-byte K slice x box_rows rows of one plane, 128-byte swizzle.
+bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int esz = tf32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(L * esz), (cuuint64_t)(L * L * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------ self test
+
+__global__ void wait_selftest_kernel(const int* flag, int* err, uint64_t timeout_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (*(volatile const int*)flag == 0) {
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      record_error(err, kDevTimeoutTest);
+      return;
+    }
+  }
+}
+
+cudaError_t launch_wait_selftest(int* buf, uint64_t timeout_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 1, 0, s>>>(buf, buf + 1, timeout_ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ planning
+
+int64_t pow7i(int d) {
+  int64_t p = 1;
+  for (int k = 0; k < d; ++k) p *= 7;
+  return p;
+}
+
+int tile_granularity(stark_dtype dt) { return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? 128 : 64; }
+
+int64_t padded_side(int64_t n, int depth, stark_dtype dt) {
+  const int64_t g = ((int64_t)1 << depth) * tile_granularity(dt);
+  return std::max<int64_t>(g, (n + g - 1) / g * g);
+}
+
+size_t element_size(stark_dtype dt) { return dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32 ? 4 : 8; }
+
+// Device bytes of the leaf operand planes of one product.
+int64_t operand_bytes(int64_t n, int depth, stark_dtype dt) {
+  const int64_t npad = padded_side(n, depth, dt);
+  const int64_t L = npad >> depth;
+  const int64_t P = pow7i(depth);
+  const int64_t per = dt == STARK_F32_SPLIT_BF16 ? 4 : 8;  // hi+lo bf16, hi+lo tf32, or one 8-byte value
+  return 2 * P * L * L * per;
+}
+
+// Roofline-style cost model for the depth choice: leaf tensor/CUDA-core
+// time plus divide and C traffic at HBM bandwidth (Sec. IV's idea of a
+// per-stage cost, with GB300 rates in place of Spark's).
+double model_seconds(int64_t n, int depth, stark_dtype dt) {
+  const int64_t npad = padded_side(n, depth, dt);
+  const double L = (double)(npad >> depth);
+  const double P = (double)pow7i(depth);
+  double flops = 2.0 * P * L * L * L;
+  double rate;
+  switch (dt) {
+    case STARK_F32_SPLIT_BF16: flops *= 3; rate = 1.7e15; break;
+    case STARK_F32_SPLIT_TF32: flops *= 3; rate = 0.85e15; break;
+    case STARK_F64: rate = 1.2e12; break;
+    default: rate = 4.0e12; break;
+  }
+  const double in_bytes = 2.0 * (double)n * n * element_size(dt);
+  const double ws = (double)operand_bytes(n, depth, dt);
+  const double c_bytes = (double)n * n * element_size(dt) * (1.0 + std::pow(3.0, depth) * 2.0 / 8.0);
+  const double items = P * (L / 128.0) * (L / 128.0);
+  const double waves = std::ceil(items / 148.0) / std::max(1.0, items / 148.0);
+  return flops / rate * waves + (in_bytes + ws + c_bytes) / 6.5e12 + 8e-6 * 3;
+}
+
+int choose_depth(int64_t n, stark_dtype dt) {
+  int best = 0;
+  double best_t = 1e300;
+  for (int d = 0; d <= kMaxDepth; ++d) {
+    if ((padded_side(n, d, dt) >> d) < tile_granularity(dt)) continue;
+    if (d > 0 && (n >> d) < 256) break;  // leaves below 256 are launch/latency bound
+    const double t = model_seconds(n, d, dt);
+    if (t < best_t) {
+      best_t = t;
+      best = d;
+    }
+  }
+  return best;
+}
+
+}  // namespace stark
+
+using namespace stark;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* stark_strerror(stark_status s) {
+  switch (s) {
+    case STARK_OK: return "ok";
+    case STARK_EINVAL: return "invalid argument";
+    case STARK_ENOMEM: return "out of memory or over the memory budget";
+    case STARK_EUNSUPPORTED: return "unsupported on this device or build";
+    case STARK_ETIMEOUT: return "a bounded device-side wait expired";
+    case STARK_EBUSY: return "request still pending";
+    case STARK_ENOTFOUND: return "unknown request id";
+    case STARK_ECUDA: return "CUDA runtime error";
+  }
+  return "unknown status";
+}
+
+int64_t stark_launch_count(void) { return g_launches.load(); }
+
+stark_status stark_quadrant_table(int depth, int side, int32_t* count, int32_t* quad, int8_t* sign) {
+  if (depth < 0 || depth > kMaxDepth || side < 0 || side > 2 || !count || !quad || !sign) return STARK_EINVAL;
+  std::vector<int32_t> c, q;
+  std::vector<int8_t> s;
+  build_quadrant_table(depth, side, c, q, s);
+  std::memcpy(count, c.data(), c.size() * sizeof(int32_t));
+  std::memcpy(quad, q.data(), q.size() * sizeof(int32_t));
+  std::memcpy(sign, s.data(), s.size());
+  return STARK_OK;
+}
+
+stark_status stark_plan_create(int64_t n, int depth, stark_dtype dt, stark_plan_t* out) {
+  if (!out) return STARK_EINVAL;
+  *out = nullptr;
+  if (n < 0 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;
+  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
+    return STARK_EINVAL;
+  if (n > (int64_t)1 << 20) return STARK_EINVAL;
+  if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
+  if (depth < 0) depth = choose_depth(n, dt);
+  auto* p = new (std::nothrow) stark_plan_s();
+  if (!p) return STARK_ENOMEM;
+  stark_status st = plan_init(p, n, depth, dt);
+  if (st != STARK_OK) {
+    plan_release(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return STARK_OK;
+}
+
+stark_status stark_plan_destroy(stark_plan_t p) {
+  if (!p) return STARK_OK;
+  cudaDeviceSynchronize();
+  plan_release(p);
+  delete p;
+  return STARK_OK;
+}
+
+stark_status stark_plan_get_info(stark_plan_t p, stark_plan_info* info) {
+  if (!p || !info) return STARK_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->n = p->n;
+  info->n_pad = p->npad;
+  info->leaf = p->L;
+  info->depth = p->depth;
+  info->dtype = p->dt;
+  info->leaves = p->P;
+  info->workspace_bytes = p->ws_bytes;
+  info->tile_m = p->is_tc ? 128 : 64;
+  info->tile_n = p->is_tc ? p->bn : 64;
+  return STARK_OK;
+}
+
+stark_status stark_mul(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  if (!p) return STARK_EINVAL;
+  return plan_run(p, A, B, C, 0, p->P, (cudaStream_t)stream);
+}
+
+stark_status stark_mul_leaves(stark_plan_t p, const void* A, const void* B, void* C, int64_t leaf_begin,
+                              int64_t leaf_end, void* stream) {
+  if (!p || leaf_begin < 0 || leaf_end > p->P || leaf_begin > leaf_end) return STARK_EINVAL;
+  return plan_run(p, A, B, C, leaf_begin, leaf_end, (cudaStream_t)stream);
+}
+
+stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
+  if (p->n == 0) return STARK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->n * p->n * p->esz;
+  if (!p->stage_A) {
+    if (cudaMalloc(&p->stage_A, bytes) != cudaSuccess || cudaMalloc(&p->stage_B, bytes) != cudaSuccess ||
+        cudaMalloc(&p->stage_C, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return STARK_ENOMEM;
+    }
+  }
+  if (cudaMemcpyAsync(p->stage_A, A, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STARK_ECUDA;
+  if (cudaMemcpyAsync(p->stage_B, B, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STARK_ECUDA;
+  stark_status st = plan_run(p, p->stage_A, p->stage_B, p->stage_C, 0, p->P, s);
+  if (st != STARK_OK) return st;
+  if (cudaMemcpyAsync(C, p->stage_C, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return STARK_ECUDA;
+  return stark_plan_check(p, stream);
+}
+
+stark_status stark_plan_check(stark_plan_t p, void* stream) {
+  if (!p) return STARK_EINVAL;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STARK_ECUDA;
+  if (e != 0) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return STARK_ETIMEOUT;
+  }
+  return STARK_OK;
+}
+
+stark_status stark_plan_set_timing(stark_plan_t p, int records) {
+  if (!p || records < 0 || records > 100000) return STARK_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
+  for (auto e : p->ev) cudaEventDestroy(e);
+  p->ev.clear();
+  p->timing_cap = 0;
+  p->timing_used = 0;
+  p->ev.resize((size_t)records * 4, nullptr);
+  for (auto& e : p->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return STARK_ECUDA;
+  p->timing_cap = records;
+  return STARK_OK;
+}
+
+stark_status stark_plan_phase_ms(stark_plan_t p, float out_ms[3]) {
+  if (!p || !out_ms || p->timing_used == 0) return STARK_EINVAL;
+  if (cudaEventSynchronize(p->ev[(size_t)(p->timing_used - 1) * 4 + 3]) != cudaSuccess) return STARK_ECUDA;
+  double sum[3] = {0, 0, 0};
+  for (int r = 0; r < p->timing_used; ++r)
+    for (int i = 0; i < 3; ++i) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p->ev[(size_t)r * 4 + i], p->ev[(size_t)r * 4 + i + 1]) != cudaSuccess)
+        return STARK_ECUDA;
+      sum[i] += ms;
+    }
+  for (int i = 0; i < 3; ++i) out_ms[i] = (float)(sum[i] / p->timing_used);
+  return STARK_OK;
+}
+
+stark_status stark_selftest_bounded_wait(uint64_t timeout_ns) {
+  int* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) return STARK_ENOMEM;
+  cudaMemset(buf, 0, 2 * sizeof(int));
+  stark_status st = STARK_OK;
+  if (launch_wait_selftest(buf, timeout_ns, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    st = STARK_ECUDA;
+  } else {
+    int h[2] = {0, 0};
+    cudaMemcpy(h, buf, sizeof(h), cudaMemcpyDeviceToHost);
+    st = h[1] == kDevTimeoutTest ? STARK_ETIMEOUT : STARK_OK;
+  }
+  cudaFree(buf);
+  return st;
+}
+
+}  // extern "C"
+
+// ====================================================================== plan internals
+namespace stark {
+
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
+  p->n = n;
+  p->depth = depth;
+  p->dt = dt;
+  p->is_tc = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+  p->esz = element_size(dt);
+  p->npad = padded_side(n, depth, dt);
+  p->L = p->npad >> depth;
+  p->P = pow7i(depth);
+  p->bn = (p->L % 256 == 0) ? 256 : 128;
+  cudaGetDevice(&p->device);
+  p->num_sms = device_sm_count();
+  if (p->L > 0x7FFFFFFF / 2) return STARK_EINVAL;
+
+  const int64_t ws = operand_bytes(n, depth, dt);
+  if (cudaMalloc(&p->X, (size_t)(ws / 2)) != cudaSuccess || cudaMalloc(&p->Y, (size_t)(ws / 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ENOMEM;
+  }
+  p->ws_bytes = ws;
+
+  // C targets of every leaf (side 2 of the quadrant-index table)
+  std::vector<int32_t> cnt, quad;
+  std::vector<int8_t> sign;
+  build_quadrant_table(depth, 2, cnt, quad, sign);
+  p->maxT = 1 << depth;
+  std::vector<CTarget> tab((size_t)(p->P * p->maxT));
+  for (int64_t l = 0; l < p->P; ++l)
+    for (int t = 0; t < cnt[(size_t)l]; ++t) {
+      int64_t r = 0, c = 0;
+      quadrant_offsets(depth, p->npad, quad[(size_t)(l * p->maxT + t)], &r, &c);
+      CTarget& e = tab[(size_t)(l * p->maxT + t)];
+      e.row_off = (int32_t)r;
+      e.col_off = (int32_t)c;
+      e.sign = sign[(size_t)(l * p->maxT + t)];
+      e.pad = 0;
+    }
+  const size_t tab_bytes = tab.size() * sizeof(CTarget);
+  if (cudaMalloc(&p->d_ctab, tab_bytes) != cudaSuccess || cudaMalloc(&p->d_ccount, cnt.size() * 4) != cudaSuccess ||
+      cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ENOMEM;
+  }
+  p->ws_bytes += (int64_t)(tab_bytes + cnt.size() * 4 + sizeof(int));
+  if (cudaMemcpy(p->d_ctab, tab.data(), tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_ccount, cnt.data(), cnt.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
+    return STARK_ECUDA;
+
+  if (p->is_tc) {
+    const bool tf32 = dt == STARK_F32_SPLIT_TF32;
+    if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * p->P, 128) ||
+        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, p->bn))
+      return STARK_EUNSUPPORTED;
+  }
+  return STARK_OK;
+}
+
+void plan_release(stark_plan_s* p) {
+  cudaFree(p->X);
+  cudaFree(p->Y);
+  cudaFree(p->d_ctab);
+  cudaFree(p->d_ccount);
+  cudaFree(p->d_err);
+  cudaFree(p->stage_A);
+  cudaFree(p->stage_B);
+  cudaFree(p->stage_C);
+  for (auto e : p->ev)
+    if (e) cudaEventDestroy(e);
+  p->ev.clear();
+  cudaGetLastError();
+}
+
+static stark_status to_status(cudaError_t e) {
+  if (e == cudaSuccess) return STARK_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? STARK_ENOMEM : STARK_ECUDA;
+}
+
+stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s) {
+  // divide phase: every leaf operand of A and of B
+  DivideArgs da{A, p->n, p->npad, p->L, p->X, nullptr};
+  DivideArgs db{B, p->n, p->npad, p->L, p->Y, nullptr};
+  InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
+  OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
+  if (p->is_tc) {
+    const int64_t half = p->P * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
+    da.out_lo = static_cast<char*>(p->X) + half;
+    db.out_lo = static_cast<char*>(p->Y) + half;
+  }
+  stark_status st = to_status(launch_divide(da, p->depth, 0, in, om, false, s));
+  if (st != STARK_OK) return st;
+  return to_status(launch_divide(db, p->depth, 1, in, om, p->is_tc, s));
+}
+
+stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
+                                 cudaStream_t s) {
+  if (p->n == 0) return STARK_OK;
+  if (!A || !B || !C) return STARK_EINVAL;
+  cudaEvent_t* ev = (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
+                        ? &p->ev[(size_t)(p->timing_used - 1) * 4]
+                        : nullptr;
+  if (ev) cudaEventRecord(ev[1], s);
+  stark_status st = plan_divide(p, A, B, s);
+  if (st != STARK_OK) return st;
+  if (ev) cudaEventRecord(ev[2], s);
+  // leaf products with the combine in the epilogue
+  if (p->is_tc) {
+    LeafTcArgs a{};
+    a.P = (int32_t)p->P;
+    a.L = (int32_t)p->L;
+    a.leaf_begin = (int32_t)lb;
+    a.leaf_end = (int32_t)le;
+    a.ctab = p->d_ctab;
+    a.ccount = p->d_ccount;
+    a.maxT = p->maxT;
+    a.C = static_cast<float*>(C);
+    a.ldc = p->n;
+    a.n = p->n;
+    a.err = p->d_err;
+    a.timeout_ns = p->timeout_ns;
+    st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
+  } else {
+    LeafCcArgs a{};
+    a.P = (int32_t)p->P;
+    a.L = (int32_t)p->L;
+    a.leaf_begin = (int32_t)lb;
+    a.leaf_end = (int32_t)le;
+    a.X = p->X;
+    a.Y = p->Y;
+    a.ctab = p->d_ctab;
+    a.ccount = p->d_ccount;
+    a.maxT = p->maxT;
+    a.C = C;
+    a.ldc = p->n;
+    a.n = p->n;
+    st = to_status(p->dt == STARK_F64 ? launch_leaf_f64(a, s) : launch_leaf_i64(a, s));
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  p->timing_active = false;
+  return st;
+}
+
+stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
+                      cudaStream_t s) {
+  if (p->n == 0) return STARK_OK;
+  if (!A || !B || !C) return STARK_EINVAL;
+  if (p->timing_used < p->timing_cap) {
+    cudaEventRecord(p->ev[(size_t)p->timing_used * 4], s);
+    ++p->timing_used;
+    p->timing_active = true;
+  }
+  if (cudaMemsetAsync(C, 0, (size_t)p->n * p->n * p->esz, s) != cudaSuccess) return to_status(cudaGetLastError());
+  return plan_run_accumulate(p, A, B, C, lb, le, s);
+}
+
+}  // namespace stark
+
+extern "C" stark_status stark_plan_operands(stark_plan_t p, const void* A, const void* B, void* stream,
+                                            const void** X, const void** Y) {
+  if (!p || !X || !Y) return STARK_EINVAL;
+  *X = p->X;
+  *Y = p->Y;
+  if (p->n == 0) return STARK_OK;
+  if (!A || !B) return STARK_EINVAL;
+  return stark::plan_divide(p, A, B, (cudaStream_t)stream);
+}

@@ -1,0 +1,71 @@
+// plan.h -- the plan object behind stark_plan_t and the helpers shared by
+// plans, batches and the server.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "stark_internal.h"
+
+namespace stark {
+
+constexpr int kMaxDepth = 4;
+constexpr uint64_t kDefaultTimeoutNs = 4000000000ull;  // 4 s per bounded device wait
+
+int64_t pow7i(int d);
+int tile_granularity(stark_dtype dt);
+int64_t padded_side(int64_t n, int depth, stark_dtype dt);
+size_t element_size(stark_dtype dt);
+int64_t operand_bytes(int64_t n, int depth, stark_dtype dt);
+double model_seconds(int64_t n, int depth, stark_dtype dt);
+int choose_depth(int64_t n, stark_dtype dt);
+
+}  // namespace stark
+
+struct stark_plan_s {
+  int64_t n = 0, npad = 0, L = 0, P = 1;
+  int depth = 0;
+  stark_dtype dt = STARK_F64;
+  bool is_tc = false;  // tensor-core (split) path
+  int bn = 128;        // leaf GEMM tile width (tensor-core path)
+  size_t esz = 8;      // element size of A, B, C
+  int device = 0;
+  int num_sms = 1;
+  // workspace: leaf operand planes; split paths hold [2P][L][L] (hi planes
+  // then lo planes), plain paths [P][L][L]
+  void* X = nullptr;
+  void* Y = nullptr;
+  int64_t ws_bytes = 0;
+  // quadrant-index table: C targets per leaf
+  stark::CTarget* d_ctab = nullptr;
+  int32_t* d_ccount = nullptr;
+  int32_t maxT = 1;
+  int* d_err = nullptr;
+  uint64_t timeout_ns = stark::kDefaultTimeoutNs;
+  CUtensorMap tmA;
+  CUtensorMap tmB;
+  // end-to-end staging (stark_mul_host), allocated on first use
+  void* stage_A = nullptr;
+  void* stage_B = nullptr;
+  void* stage_C = nullptr;
+  // optional phase timing: event sets for up to timing_cap products
+  int timing_cap = 0;
+  int timing_used = 0;
+  bool timing_active = false;  // the current product records events
+  std::vector<cudaEvent_t> ev;  // 4 per recorded product
+};
+
+namespace stark {
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt);
+void plan_release(stark_plan_s* p);
+// Enqueue C = sum over leaves [lb, le) of their combine contributions.
+stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
+                      cudaStream_t s);
+// Divide phase only: all leaf operands of A and B into the workspace.
+stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s);
+// The same without zeroing C first (C accumulates).
+stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
+                                 cudaStream_t s);
+}  // namespace stark

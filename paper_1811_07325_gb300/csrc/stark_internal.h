@@ -1,0 +1,115 @@
+// stark_internal.h -- shared declarations between the host side (plans,
+// batches, server) and the kernels of libstark.so.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/stark.h"
+
+namespace stark {
+
+// ------------------------------------------------------------------ tables
+// Alg. 1 coefficients per recursion level.  Quadrant q: 0 = X11, 1 = X12,
+// 2 = X21, 3 = X22.  Product m: 0..6 = M1..M7.
+//   A side: M1 A11+A22, M2 A21+A22, M3 A11, M4 A22, M5 A11+A12,
+//           M6 A21-A11, M7 A12-A22
+//   B side: M1 B11+B22, M2 B11, M3 B12-B22, M4 B21-B11, M5 B22,
+//           M6 B11+B12, M7 B21+B22
+//   C side: C11 = M1+M4-M5+M7, C12 = M3+M5, C21 = M2+M4, C22 = M1-M2+M3+M6
+__host__ __device__ constexpr int coef_a(int m, int q) {
+  constexpr signed char t[7][4] = {{1, 0, 0, 1}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 0, 0, 1},
+                                   {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}};
+  return t[m][q];
+}
+__host__ __device__ constexpr int coef_b(int m, int q) {
+  constexpr signed char t[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
+                                   {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}};
+  return t[m][q];
+}
+// coefficient of M_m in C quadrant q
+__host__ __device__ constexpr int coef_c(int m, int q) {
+  constexpr signed char t[4][7] = {{1, 0, 0, 1, -1, 0, 1}, {0, 0, 1, 0, 1, 0, 0},
+                                   {0, 1, 0, 1, 0, 0, 0}, {1, -1, 1, 0, 0, 1, 0}};
+  return t[q][m];
+}
+
+// One entry of the device quadrant-index table: where a leaf's product
+// lands in C and with which sign.
+struct CTarget {
+  int32_t row_off;  // element row offset of the target quadrant in C
+  int32_t col_off;  // element column offset
+  int32_t sign;     // +1 or -1
+  int32_t pad;
+};
+
+// Host construction of the per-leaf term lists (side 0 A, 1 B, 2 C).
+void build_quadrant_table(int depth, int side, std::vector<int32_t>& count, std::vector<int32_t>& quad,
+                          std::vector<int8_t>& sign);
+// Row/column element offsets of base-4 quadrant path q for side npad.
+void quadrant_offsets(int depth, int64_t npad, int32_t q, int64_t* row, int64_t* col);
+
+// ------------------------------------------------------------------ launches
+enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2 };
+enum InType { kInF32 = 0, kInF64 = 1, kInI64 = 2 };
+
+struct DivideArgs {
+  const void* X;      // n x n row-major input
+  int64_t n;          // input side
+  int64_t npad;       // padded side (zeros beyond n)
+  int64_t L;          // leaf side = npad >> depth
+  void* out_hi;       // planes [P][L][L] (split: hi part; plain: the value)
+  void* out_lo;       // planes [P][L][L] (split: lo part; plain: unused)
+};
+
+// Divide phase for one operand: writes the 7^depth leaf operand sums.
+// side 0 = A (row-major planes), side 1 = B; `trans` stores each B plane
+// transposed (N x K, K contiguous) for K-major tensor-core operands.
+cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, bool trans,
+                          cudaStream_t s);
+
+struct LeafTcArgs {
+  int32_t P;           // leaves per operand side (planes 0..P-1 hi, P..2P-1 lo)
+  int32_t L;           // leaf side
+  int32_t leaf_begin;  // leaves [leaf_begin, leaf_end) are computed
+  int32_t leaf_end;
+  const CTarget* ctab; // [P][maxT]
+  const int32_t* ccount;
+  int32_t maxT;
+  float* C;
+  int64_t ldc;
+  int64_t n;
+  int* err;
+  uint64_t timeout_ns;
+};
+
+// 3xBF16 / 3xTF32 leaf GEMMs with the combine fused in the epilogue.
+cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, bool tf32, int bn,
+                           int num_sms, cudaStream_t s);
+int leaf_tc_smem_bytes(bool tf32, int bn);
+
+struct LeafCcArgs {
+  int32_t P, L, leaf_begin, leaf_end;
+  const void* X;  // planes [P][L][L]
+  const void* Y;  // planes [P][L][L] (K x N, row-major)
+  const CTarget* ctab;
+  const int32_t* ccount;
+  int32_t maxT;
+  void* C;
+  int64_t ldc, n;
+};
+cudaError_t launch_leaf_f64(const LeafCcArgs& a, cudaStream_t s);
+cudaError_t launch_leaf_i64(const LeafCcArgs& a, cudaStream_t s);
+
+cudaError_t launch_wait_selftest(int* err, uint64_t timeout_ns, cudaStream_t s);
+
+// ------------------------------------------------------------------ misc
+void count_launch(int k = 1);
+int device_sm_count();
+bool device_is_sm100_family();
+bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows);
+
+}  // namespace stark

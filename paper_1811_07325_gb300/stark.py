@@ -1,0 +1,255 @@
+"""ctypes binding of libstark.so (``include/stark.h``).
+
+Argument marshalling only: every step of the multiplication runs in the CUDA
+kernels of libstark.so.  PyTorch supplies device memory and streams.  The
+library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1811_07325_gb300.build_lib``); importing this module fails
+loudly otherwise, and there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstark.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libstark.so is not built ({_LIB_PATH}); run __graft_entry__.build() first")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+
+class DType(enum.IntEnum):
+    F64 = 0
+    F32_SPLIT_BF16 = 1
+    F32_SPLIT_TF32 = 2
+    I64 = 3
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    EINVAL = 1
+    ENOMEM = 2
+    EUNSUPPORTED = 3
+    ETIMEOUT = 4
+    EBUSY = 5
+    ENOTFOUND = 6
+    ECUDA = 7
+
+
+class StarkError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = Status(status)
+        msg = _lib.stark_strerror(int(status)).decode()
+        super().__init__(f"{where}: {self.status.name} ({msg})" if where else f"{self.status.name} ({msg})")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("leaf", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("dtype", ctypes.c_int32), ("leaves", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+_i64, _i32, _vp, _ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int
+_SIGS = {
+    "stark_plan_create": ([_i64, _ci, _ci, ctypes.POINTER(_vp)], _ci),
+    "stark_plan_destroy": ([_vp], _ci),
+    "stark_plan_get_info": ([_vp, ctypes.POINTER(PlanInfo)], _ci),
+    "stark_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
+    "stark_mul_host": ([_vp, _vp, _vp, _vp, _vp], _ci),
+    "stark_mul_leaves": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _ci),
+    "stark_plan_operands": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _ci),
+    "stark_plan_check": ([_vp, _vp], _ci),
+    "stark_plan_set_timing": ([_vp, _ci], _ci),
+    "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
+    "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
+    "stark_strerror": ([_ci], ctypes.c_char_p),
+    "stark_selftest_bounded_wait": ([ctypes.c_uint64], _ci),
+    "stark_launch_count": ([], _i64),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+def _check(status, where):
+    if status != 0:
+        raise StarkError(status, where)
+
+
+def declared_symbols():
+    """Names of the entry points this binding uses (all declared in stark.h)."""
+    return sorted(_SIGS)
+
+
+def library_path():
+    return _LIB_PATH
+
+
+_TORCH_DTYPE = {}
+
+
+def _torch_dtype(dt):
+    import torch
+    return {DType.F64: torch.float64, DType.F32_SPLIT_BF16: torch.float32,
+            DType.F32_SPLIT_TF32: torch.float32, DType.I64: torch.int64}[DType(dt)]
+
+
+def _numpy_dtype(dt):
+    return {DType.F64: np.float64, DType.F32_SPLIT_BF16: np.float32,
+            DType.F32_SPLIT_TF32: np.float32, DType.I64: np.int64}[DType(dt)]
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _CudaBuffer:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 2, "strides": None}
+
+
+class Plan:
+    """A plan for n x n products (``stark_plan_create``)."""
+
+    def __init__(self, n: int, depth: int = -1, dtype: DType = DType.F32_SPLIT_BF16):
+        h = _vp()
+        _check(_lib.stark_plan_create(int(n), int(depth), int(dtype), ctypes.byref(h)), "stark_plan_create")
+        self._h = h
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(h, ctypes.byref(info)), "stark_plan_get_info")
+        self.n, self.n_pad, self.leaf, self.depth = info.n, info.n_pad, info.leaf, info.depth
+        self.dtype = DType(info.dtype)
+        self.leaves, self.workspace_bytes = info.leaves, info.workspace_bytes
+        self.tile = (info.tile_m, info.tile_n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.stark_plan_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- argument checks ---------------------------------------------------
+    def _check_tensor(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be on a CUDA device")
+        if t.dtype != _torch_dtype(self.dtype):
+            raise TypeError(f"{name} has dtype {t.dtype}, plan expects {_torch_dtype(self.dtype)}")
+        if tuple(t.shape) != (self.n, self.n) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.n}x{self.n} matrix")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def mul(self, A, B, C=None, stream=None):
+        """C = A @ B on the device (async on ``stream``, default: torch's current)."""
+        import torch
+        if C is None:
+            C = torch.empty((self.n, self.n), dtype=_torch_dtype(self.dtype), device=A.device)
+        a, b, c = self._check_tensor(A, "A"), self._check_tensor(B, "B"), self._check_tensor(C, "C")
+        _check(_lib.stark_mul(self._h, a, b, c, _stream_handle(stream)), "stark_mul")
+        return C
+
+    def mul_leaves(self, A, B, leaf_begin, leaf_end, C=None, stream=None):
+        import torch
+        if C is None:
+            C = torch.empty((self.n, self.n), dtype=_torch_dtype(self.dtype), device=A.device)
+        a, b, c = self._check_tensor(A, "A"), self._check_tensor(B, "B"), self._check_tensor(C, "C")
+        _check(_lib.stark_mul_leaves(self._h, a, b, c, int(leaf_begin), int(leaf_end), _stream_handle(stream)),
+               "stark_mul_leaves")
+        return C
+
+    def mul_host(self, A, B, C=None, stream=None):
+        """End to end from host memory (numpy arrays or CPU tensors, pinned is best)."""
+        def ptr(x, name):
+            if hasattr(x, "data_ptr"):
+                if x.is_cuda or tuple(x.shape) != (self.n, self.n) or not x.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous host {self.n}x{self.n} matrix")
+                return ctypes.c_void_p(x.data_ptr())
+            x = np.asarray(x)
+            if x.dtype != _numpy_dtype(self.dtype) or x.shape != (self.n, self.n) or not x.flags.c_contiguous:
+                raise ValueError(f"{name} must be a contiguous {self.n}x{self.n} {_numpy_dtype(self.dtype)} array")
+            return ctypes.c_void_p(x.ctypes.data)
+        if C is None:
+            C = np.empty((self.n, self.n), dtype=_numpy_dtype(self.dtype))
+        _check(_lib.stark_mul_host(self._h, ptr(A, "A"), ptr(B, "B"), ptr(C, "C"), _stream_handle(stream)),
+               "stark_mul_host")
+        return C
+
+    def operands(self, A, B, stream=None):
+        """Divide phase only; returns torch views (X, Y) of the leaf operand planes."""
+        import torch
+        a, b = self._check_tensor(A, "A"), self._check_tensor(B, "B")
+        x, y = _vp(), _vp()
+        _check(_lib.stark_plan_operands(self._h, a, b, _stream_handle(stream), ctypes.byref(x), ctypes.byref(y)),
+               "stark_plan_operands")
+        P, L = self.leaves, self.leaf
+        if self.dtype == DType.F32_SPLIT_BF16:
+            shape, ts, view = (2 * P, L, L), "<i2", torch.bfloat16
+        elif self.dtype == DType.F32_SPLIT_TF32:
+            shape, ts, view = (2 * P, L, L), "<f4", None
+        elif self.dtype == DType.F64:
+            shape, ts, view = (P, L, L), "<f8", None
+        else:
+            shape, ts, view = (P, L, L), "<i8", None
+        X = torch.as_tensor(_CudaBuffer(x.value, shape, ts), device=A.device)
+        Y = torch.as_tensor(_CudaBuffer(y.value, shape, ts), device=A.device)
+        if view is not None:
+            X, Y = X.view(view), Y.view(view)
+        return X, Y
+
+    def check(self, stream=None):
+        """Synchronise and raise on a device-side timeout."""
+        _check(_lib.stark_plan_check(self._h, _stream_handle(stream)), "stark_plan_check")
+
+    def set_timing(self, records=1):
+        """Record per-phase events for the next ``records`` products (0: off)."""
+        _check(_lib.stark_plan_set_timing(self._h, int(records)), "stark_plan_set_timing")
+
+    def phase_ms(self):
+        """Mean per-phase device time (ms) over the recorded products."""
+        out = (ctypes.c_float * 3)()
+        _check(_lib.stark_plan_phase_ms(self._h, out), "stark_plan_phase_ms")
+        return {"zero_c": out[0], "divide": out[1], "leaf_combine": out[2]}
+
+
+def quadrant_table(depth: int, side: int):
+    """(count[7^d], quad[7^d, 2^d], sign[7^d, 2^d]) on the host; side 0 A, 1 B, 2 C."""
+    P, T = 7 ** depth, 2 ** depth
+    count = np.zeros(P, np.int32)
+    quad = np.zeros((P, T), np.int32)
+    sign = np.zeros((P, T), np.int8)
+    _check(_lib.stark_quadrant_table(int(depth), int(side), count.ctypes.data, quad.ctypes.data,
+                                     sign.ctypes.data), "stark_quadrant_table")
+    return count, quad, sign
+
+
+def selftest_bounded_wait(timeout_ns: int = 20_000_000) -> Status:
+    return Status(_lib.stark_selftest_bounded_wait(int(timeout_ns)))
+
+
+def launch_count() -> int:
+    return int(_lib.stark_launch_count())
+
+
+def strerror(status) -> str:
+    return _lib.stark_strerror(int(status)).decode()

@@ -26,3 +26,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def stark_lib():
+    """The built C-ABI library (builds it in-tree first if it is missing)."""
+    from paper_1811_07325_gb300 import build_lib
+    build_lib.build()
+    from paper_1811_07325_gb300 import stark
+    return stark

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (written here, derived in the comments):
+  * int64: bit-exact (wrapping mod 2^64 on both sides).
+  * divide phase: bit-exact operand sums and splits (every sum is a two-term
+    fp32 addition per level, so the order cannot matter; the splits are
+    round-to-nearest-even on both sides).
+  * fp64: max|dC| <= Higham's first-order Strassen bound (Thm. 23.2,
+    "Accuracy and Stability of Numerical Algorithms", 2nd ed.), and the
+    normwise ratio max|dC| / (||A||_F ||B||_F) <= 1e-12.
+  * split fp32 (3xBF16, 3xTF32): normwise ratio <= 1e-6, and a bug-signal
+    bound on the relative RMS error, rms(dC) / rms(C):
+      3xBF16: operands carry 16 significant bits (8 + 8), products lose
+      ~2^-16 relative, fp32 accumulation adds ~2^-24 sqrt(L); a dropped cross
+      term would leave ~2^-8.  Bound: 2^-12.
+      3xTF32: 22 bits, ~2^-21 relative; a dropped term leaves ~2^-11.
+      Bound: 2^-16.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_07325_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S(stark_lib):
+    return stark_lib
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def higham_bound(n, d, A, B):
+    u = 2.0 ** -53
+    L = -(-n // 2 ** d)
+    return 2 * ((12 ** d * (L * L + 5 * L) - 5 * n) + n) * u * np.abs(A).max() * np.abs(B).max()
+
+
+# ----------------------------------------------------------------- self test
+def test_bounded_wait_reports_timeout_and_context_survives(S):
+    assert S.selftest_bounded_wait(20_000_000) == S.Status.ETIMEOUT
+    with S.Plan(64, 1, S.DType.I64) as p:
+        A = synth.integers(64, 1, 0, -5, 5)
+        B = synth.integers(64, 1, 1, -5, 5)
+        C = p.mul(dev(A), dev(B))
+        p.check()
+        assert np.array_equal(C.cpu().numpy(), oracle.gemm_classical(A, B))
+
+
+# ----------------------------------------------------------------- int64
+@pytest.mark.parametrize("n,depths", [(1, [0, 1]), (63, [0, 1, 2]), (200, [1, 2, 3]), (512, [0, 1, 2, 3]),
+                                      (1000, [2, 3, 4])])
+def test_int64_bit_exact(S, n, depths):
+    A = synth.integers(n, 100 + n, 0, -16, 16)
+    B = synth.integers(n, 100 + n, 1, -16, 16)
+    want = oracle.gemm_classical(A, B)
+    dA, dB = dev(A), dev(B)
+    for d in depths:
+        with S.Plan(n, d, S.DType.I64) as p:
+            C = p.mul(dA, dB)
+            p.check()
+            assert np.array_equal(C.cpu().numpy(), want), d
+
+
+def test_int64_wraps_modulo_2_64(S):
+    n = 130
+    A = synth.integers(n, 5, 0, -2**63, 2**63 - 1)
+    B = synth.integers(n, 5, 1, -2**63, 2**63 - 1)
+    want = oracle.gemm_classical(A, B)
+    for d in (1, 2):
+        with S.Plan(n, d, S.DType.I64) as p:
+            assert np.array_equal(p.mul(dev(A), dev(B)).cpu().numpy(), want)
+
+
+def test_int64_equals_oracle_strassen(S):
+    n = 256
+    A = synth.integers(n, 6, 0, -16, 16)
+    B = synth.integers(n, 6, 1, -16, 16)
+    with S.Plan(n, 3, S.DType.I64) as p:
+        assert np.array_equal(p.mul(dev(A), dev(B)).cpu().numpy(), oracle.strassen(A, B, 3))
+
+
+# ----------------------------------------------------------------- divide phase
+@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
+@pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3)])
+def test_divide_split_bit_exact(S, dtype, n, d):
+    dt = S.DType[dtype]
+    A = synth.normal(n, 7 + d, 0)
+    B = synth.normal(n, 7 + d, 1)
+    split = oracle.split_bf16 if dt == S.DType.F32_SPLIT_BF16 else oracle.split_tf32
+    with S.Plan(n, d, dt) as p:
+        X, Y = p.operands(dev(A), dev(B))
+        torch.cuda.synchronize()
+        P = p.leaves
+        X = X.float().cpu().numpy()
+        Y = Y.float().cpu().numpy()
+        xa = oracle.strassen_operands(A, p.n_pad, d, "A")
+        yb = oracle.strassen_operands(B, p.n_pad, d, "B")
+        xh, xl = split(xa)
+        yh, yl = split(yb)
+        assert np.array_equal(X[:P], xh) and np.array_equal(X[P:], xl)
+        # B planes are stored transposed (N x K) for the K-major tensor-core operand
+        assert np.array_equal(Y[:P].transpose(0, 2, 1), yh) and np.array_equal(Y[P:].transpose(0, 2, 1), yl)
+
+
+@pytest.mark.parametrize("n,d", [(200, 1), (300, 2)])
+def test_divide_plain_f64_matches_oracle_sums(S, n, d):
+    # integer-valued doubles: the oracle's fp32 sums are exact, so they must equal the fp64 planes
+    A = synth.integers(n, 3, 0, -1000, 1000).astype(np.float64)
+    B = synth.integers(n, 3, 1, -1000, 1000).astype(np.float64)
+    with S.Plan(n, d, S.DType.F64) as p:
+        X, Y = p.operands(dev(A), dev(B))
+        torch.cuda.synchronize()
+        xa = oracle.strassen_operands(A.astype(np.float32), p.n_pad, d, "A")
+        yb = oracle.strassen_operands(B.astype(np.float32), p.n_pad, d, "B")
+        assert np.array_equal(X.cpu().numpy(), xa.astype(np.float64))
+        assert np.array_equal(Y.cpu().numpy(), yb.astype(np.float64))
+
+
+# ----------------------------------------------------------------- fp64
+@pytest.mark.parametrize("n,depths", [(129, [0, 1]), (640, [1, 2, 3]), (1024, [3])])
+def test_f64_within_bound(S, n, depths):
+    A = synth.uniform(n, 11, 0)
+    B = synth.uniform(n, 11, 1)
+    want = oracle.gemm_classical(A, B)
+    dA, dB = dev(A), dev(B)
+    for d in depths:
+        with S.Plan(n, d, S.DType.F64) as p:
+            C = p.mul(dA, dB).cpu().numpy()
+            p.check()
+        err = np.abs(C - want).max()
+        assert err <= higham_bound(n, d, A, B), (d, err)
+        assert err / (np.linalg.norm(A) * np.linalg.norm(B)) <= 1e-12
+
+
+# ----------------------------------------------------------------- split fp32
+SPLIT_BOUND = {"F32_SPLIT_BF16": 2.0 ** -12, "F32_SPLIT_TF32": 2.0 ** -16}
+
+
+def check_split(C, want, A64norm, B64norm, dtype):
+    diff = C.astype(np.float64) - want
+    ratio = np.abs(diff).max() / (A64norm * B64norm)
+    rel_rms = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+    assert ratio <= 1e-6, ratio
+    assert rel_rms <= SPLIT_BOUND[dtype], rel_rms
+    return ratio, rel_rms
+
+
+@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
+@pytest.mark.parametrize("n,depths", [(1, [0]), (100, [0, 1]), (384, [0, 1]), (1000, [1, 2, 3]),
+                                      (2048, [0, 2, 3])])
+def test_split_within_bound(S, dtype, n, depths):
+    dt = S.DType[dtype]
+    A = synth.normal(n, 21, 0)
+    B = synth.normal(n, 21, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    for d in depths:
+        with S.Plan(n, d, dt) as p:
+            C = p.mul(dA, dB)
+            p.check()
+            check_split(C.cpu().numpy(), want, an, bn, dtype)
+
+
+def test_split_repeatable_and_stream_ordered(S):
+    n = 1024
+    A = synth.normal(n, 31, 0)
+    B = synth.normal(n, 31, 1)
+    with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
+        s = torch.cuda.Stream()
+        dA, dB = dev(A), dev(B)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            C1 = p.mul(dA, dB, stream=s)
+            C2 = p.mul(dA, dB, stream=s)
+        s.synchronize()
+        want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+        an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+        check_split(C1.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
+        check_split(C2.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
+
+
+# ----------------------------------------------------------------- API paths
+def test_leaf_partition_sums_to_product(S):
+    n, d = 300, 2
+    A = synth.integers(n, 41, 0, -16, 16)
+    B = synth.integers(n, 41, 1, -16, 16)
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType.I64) as p:
+        cuts = [0, 5, 20, 21, 49]
+        total = torch.zeros((n, n), dtype=torch.int64, device="cuda")
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            total += p.mul_leaves(dA, dB, a, b)
+        assert np.array_equal(total.cpu().numpy(), oracle.gemm_classical(A, B))
+
+
+def test_mul_host_matches_device(S):
+    n = 777
+    A = synth.normal(n, 51, 0)
+    B = synth.normal(n, 51, 1)
+    with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
+        Ch = p.mul_host(A, B)
+        Cd = p.mul(dev(A), dev(B)).cpu().numpy()
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    check_split(Ch, want, an, bn, "F32_SPLIT_BF16")
+    check_split(Cd, want, an, bn, "F32_SPLIT_BF16")
+
+
+def test_empty_and_bad_arguments(S):
+    with S.Plan(0, 1, S.DType.F32_SPLIT_BF16) as p:
+        e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
+        p.mul(e, e, e)
+    with pytest.raises(S.StarkError):
+        S.Plan(-1, 1, S.DType.F64)
+    with pytest.raises(S.StarkError):
+        S.Plan(64, 5, S.DType.F64)
+    with S.Plan(64, 1, S.DType.F64) as p:
+        with pytest.raises(TypeError):
+            p.mul(torch.zeros(64, 64, device="cuda"), torch.zeros(64, 64, device="cuda"))
+
+
+def test_auto_depth(S):
+    with S.Plan(16384, -1, S.DType.F32_SPLIT_BF16) as p:
+        assert 1 <= p.depth <= 4
+    with S.Plan(300, -1, S.DType.F32_SPLIT_BF16) as p:
+        assert p.depth == 0
+
+
+# ----------------------------------------------------------------- full size, sampled rows
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype,d", [("F32_SPLIT_BF16", 2), ("F32_SPLIT_BF16", 3), ("F32_SPLIT_TF32", 2)])
+def test_full_size_sampled_rows(S, dtype, d):
+    n = 16384
+    A = synth.normal(n, 2024, 0)
+    B = synth.normal(n, 2024, 1)
+    rows = synth.sample_rows(n, 256, 2024)
+    want = oracle.gemm_rows(A, B, rows)
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        C = p.mul(dA, dB)
+        p.check()
+        got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+    del C, dA, dB
+    torch.cuda.empty_cache()
+    check_split(got, want, an, bn, dtype)
