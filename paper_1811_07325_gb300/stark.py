@@ -117,7 +117,7 @@ class _CudaBuffer:
 
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 2, "strides": None}
+                                         "data": (int(ptr), False), "version": 2, "strides": None}
 
 
 class Plan:

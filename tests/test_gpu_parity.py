@@ -141,19 +141,33 @@ def test_f64_within_bound(S, n, depths):
 
 # ----------------------------------------------------------------- split fp32
 SPLIT_BOUND = {"F32_SPLIT_BF16": 2.0 ** -12, "F32_SPLIT_TF32": 2.0 ** -16}
+# Per-product relative error of the split: |x - hi - lo| <= u^2 |x| with
+# u = 2^-8 (bf16) or 2^-11 (tf32), and the dropped lo*lo term <= u^2 |xy|,
+# so each product is off by at most ~3 u^2 relative.
+SPLIT_U2 = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22}
 
 
-def check_split(C, want, A64norm, B64norm, dtype):
+def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=0):
+    """Normwise bound 1e-6 (the configs' sizes, n >= 64) and the RMS bug
+    signal; tiny n, where averaging cannot bring the 16/22-bit split below
+    1e-6 of ||A|| ||B||, gets the componentwise bound instead:
+    |dC_ij| <= (3 u^2 + n 2^-23) 3^d (|A| |B|)_ij."""
     diff = C.astype(np.float64) - want
     ratio = np.abs(diff).max() / (A64norm * B64norm)
     rel_rms = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
-    assert ratio <= 1e-6, ratio
-    assert rel_rms <= SPLIT_BOUND[dtype], rel_rms
+    n = want.shape[1]
+    if n >= 64:
+        assert ratio <= 1e-6, ratio
+        assert rel_rms <= SPLIT_BOUND[dtype], rel_rms
+    else:
+        absAB = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+        tol = (3 * SPLIT_U2[dtype] + n * 2.0 ** -23) * 3 ** d * absAB
+        assert np.all(np.abs(diff) <= tol), np.max(np.abs(diff) / tol)
     return ratio, rel_rms
 
 
 @pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
-@pytest.mark.parametrize("n,depths", [(1, [0]), (100, [0, 1]), (384, [0, 1]), (1000, [1, 2, 3]),
+@pytest.mark.parametrize("n,depths", [(1, [0, 1]), (37, [0, 1]), (100, [0, 1]), (384, [0, 1]), (1000, [1, 2, 3]),
                                       (2048, [0, 2, 3])])
 def test_split_within_bound(S, dtype, n, depths):
     dt = S.DType[dtype]
@@ -166,7 +180,7 @@ def test_split_within_bound(S, dtype, n, depths):
         with S.Plan(n, d, dt) as p:
             C = p.mul(dA, dB)
             p.check()
-            check_split(C.cpu().numpy(), want, an, bn, dtype)
+            check_split(C.cpu().numpy(), want, an, bn, dtype, A, B, d)
 
 
 def test_split_repeatable_and_stream_ordered(S):
