@@ -121,10 +121,10 @@ STARK_API stark_status stark_mul_leaves(stark_plan_t plan, const void *A, const 
  * the plan's workspace and returns read-only device pointers to it, for
  * inspection by tests.  Layout: split dtypes hold [2*leaves][L][L] planes
  * (hi planes, then lo planes; bf16 values, or TF32 values in fp32
- * containers); F64/I64 hold [leaves][L][L].  A planes are row-major (the
- * leaf's M x K operand); B planes are row-major K x N for F64/I64 and
- * transposed (N x K) for the split dtypes.  The pointers stay valid until the
- * plan is destroyed and are overwritten by the next product. */
+ * containers); F64/I64 hold [leaves][L][L].  Every plane is row-major: A
+ * planes are the leaf's M x K operand, B planes its K x N operand.  The
+ * pointers stay valid until the plan is destroyed and are overwritten by the
+ * next product. */
 STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, const void *B, void *stream, const void **X,
                                  const void **Y);
 

@@ -1,20 +1,22 @@
-// divide.cu -- the divide phase (Alg. 1 / Alg. 3, Sec. III-C): one pass over
-// an operand that writes the operand sums of all 7^depth leaf products.
+// divide.cu -- the divide phase (Alg. 1 / Alg. 3, Sec. III-C): one streaming
+// pass over an operand that writes the operand sums of all 7^depth leaf
+// products.
 //
-// Stark forms these sums level by level with a Spark shuffle per level
-// (replicate A11, A22 four times and A12, A21 twice, group by M-index, add).
-// Here one kernel does every level for a T x T tile position of all leaf
-// planes at once: each element of the input is read from HBM once, and
-// each leaf operand element is written once.
+// Stark forms these sums level by level, with a Spark shuffle per level
+// (replicate A11 and A22 four times and A12, A21 twice, group by M-index,
+// add).  Here one kernel does every level at once.  A thread owns VEC
+// consecutive columns (i, j..j+VEC-1) of the L x L leaf grid; it reads the
+// matching element vector of every quadrant path of the input (each input
+// element is read from HBM once, with vector loads), forms the sums of the
+// recursion tree in registers and stores its VEC values of every leaf plane
+// (one contiguous 8- or 16-byte store per plane, coalesced across the warp).
 //
-// Per block (output tile origin (r0, c0) inside an L x L leaf plane):
-//   for each level-1 product m1 in M1..M7:
-//     stage the level-1 sums  S = sum_q1 coef(m1, q1) * X_{q1, g}  for every
-//     sub-path g of the remaining depth-1 levels into shared memory (two fp32
-//     terms at most, exactly the additions of Alg. 1, so the result does not
-//     depend on summation order), transposed for B when requested;
-//   each thread then walks the remaining levels of the tree in registers and
-//   writes its leaf values (bf16 hi/lo, tf32 hi/lo, or the plain value).
+// For depth <= 2 all 4^depth quadrant vectors sit in registers.  Deeper
+// trees walk the first depth-2 levels as an outer loop: for each prefix of
+// M-indices the 16 sub-quadrant sums are re-evaluated from global memory
+// (L2 hits), in the same level-by-level order, then the last two levels run
+// in registers.  Every sum is a two-term addition per level exactly as in
+// Alg. 1, so results do not depend on evaluation order.
 // Padding to n_pad is virtual: reads beyond n return zero.
 #include <cuda_bf16.h>
 
@@ -37,8 +39,8 @@ struct AccOf<int64_t> {
 
 // The two-term sums of Alg. 1 for product m (0..6 = M1..M7), quadrant values
 // from g(q), q = 0:11, 1:12, 2:21, 3:22.
-template <int SIDE, typename Acc, class Get>
-__device__ __forceinline__ Acc level_sum(int m, const Get& g) {
+template <int SIDE, typename V, class Get>
+__device__ __forceinline__ V level_sum(int m, const Get& g) {
   if constexpr (SIDE == 0) {
     switch (m) {
       case 0: return g(0) + g(3);  // A11 + A22
@@ -74,62 +76,40 @@ __device__ __forceinline__ float rn_tf32(float x) {
   return __uint_as_float(u);
 }
 
-template <typename Acc, int Q, int VEC>
-struct RegSrc {
-  const Acc (&v)[Q][VEC];
-  __device__ __forceinline__ Acc get(int g, int e) const { return v[g][e]; }
-};
-
-template <typename Acc, int T, int VEC>
-struct SmemSrc {
-  const Acc* s;
-  int base;  // cr * LD + cc
-  __device__ __forceinline__ Acc get(int g, int e) const { return s[g * T * (T + 1) + base + e]; }
-};
-
-// Walk LV more recursion levels of product sums, calling emit(leaf, vals)
-// for every leaf below; leaf numbers extend `prefix` in base 7.
-template <typename Acc, int SIDE, int LV, int VEC>
-struct Tree {
-  template <class Src, class Emit>
-  __device__ __forceinline__ static void run(const Src& src, int prefix, Emit& emit) {
-    if constexpr (LV == 0) {
-      Acc v[VEC];
+// A short vector of accumulator values with elementwise + and -.
+template <typename Acc, int VEC>
+struct Vec {
+  Acc v[VEC];
+  __device__ __forceinline__ Vec operator+(const Vec& o) const {
+    Vec r;
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) v[e] = src.get(0, e);
-      emit(prefix, v);
-    } else {
-      constexpr int Q = pow4c(LV - 1);
+    for (int e = 0; e < VEC; ++e) r.v[e] = v[e] + o.v[e];
+    return r;
+  }
+  __device__ __forceinline__ Vec operator-(const Vec& o) const {
+    Vec r;
 #pragma unroll
-      for (int m = 0; m < 7; ++m) {
-        Acc o[Q][VEC];
-#pragma unroll
-        for (int h = 0; h < Q; ++h)
-#pragma unroll
-          for (int e = 0; e < VEC; ++e)
-            o[h][e] = level_sum<SIDE, Acc>(m, [&](int q) { return src.get(q * Q + h, e); });
-        RegSrc<Acc, Q, VEC> rs{o};
-        Tree<Acc, SIDE, LV - 1, VEC>::run(rs, prefix * 7 + m, emit);
-      }
-    }
+    for (int e = 0; e < VEC; ++e) r.v[e] = v[e] - o.v[e];
+    return r;
   }
 };
 
 template <int OUT, typename Tin, int VEC>
 struct Emitter {
+  using Acc = typename AccOf<Tin>::type;
   void* hi;
   void* lo;
   int64_t plane_elems;  // L * L
   int64_t offset;       // row * L + col of this thread's first element
 
-  __device__ __forceinline__ void operator()(int leaf, const typename AccOf<Tin>::type (&v)[VEC]) const {
+  __device__ __forceinline__ void operator()(int leaf, const Vec<Acc, VEC>& x) const {
     const int64_t at = (int64_t)leaf * plane_elems + offset;
     if constexpr (OUT == kOutSplitBf16) {
       __nv_bfloat16 h[VEC], l[VEC];
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
-        h[e] = __float2bfloat16_rn(v[e]);
-        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+        h[e] = __float2bfloat16_rn(x.v[e]);
+        l[e] = __float2bfloat16_rn(x.v[e] - __bfloat162float(h[e]));
       }
       store_vec(reinterpret_cast<__nv_bfloat16*>(hi) + at, h);
       store_vec(reinterpret_cast<__nv_bfloat16*>(lo) + at, l);
@@ -137,15 +117,15 @@ struct Emitter {
       float h[VEC], l[VEC];
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
-        h[e] = rn_tf32(v[e]);
-        l[e] = rn_tf32(v[e] - h[e]);
+        h[e] = rn_tf32(x.v[e]);
+        l[e] = rn_tf32(x.v[e] - h[e]);
       }
       store_vec(reinterpret_cast<float*>(hi) + at, h);
       store_vec(reinterpret_cast<float*>(lo) + at, l);
     } else {
       Tin o[VEC];
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) o[e] = (Tin)v[e];
+      for (int e = 0; e < VEC; ++e) o[e] = (Tin)x.v[e];
       store_vec(reinterpret_cast<Tin*>(hi) + at, o);
     }
   }
@@ -155,11 +135,11 @@ struct Emitter {
     constexpr int bytes = (int)sizeof(E) * VEC;
     if constexpr (bytes % 16 == 0) {
 #pragma unroll
-      for (int k = 0; k < bytes / 16; ++k) reinterpret_cast<int4*>(p)[k] = reinterpret_cast<const int4*>(x)[k];
+      for (int k = 0; k < bytes / 16; ++k) __stcs(reinterpret_cast<int4*>(p) + k, reinterpret_cast<const int4*>(x)[k]);
     } else if constexpr (bytes == 8) {
-      *reinterpret_cast<int2*>(p) = *reinterpret_cast<const int2*>(x);
+      __stcs(reinterpret_cast<int2*>(p), *reinterpret_cast<const int2*>(x));
     } else if constexpr (bytes == 4) {
-      *reinterpret_cast<int*>(p) = *reinterpret_cast<const int*>(x);
+      __stcs(reinterpret_cast<int*>(p), *reinterpret_cast<const int*>(x));
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; ++e) p[e] = x[e];
@@ -167,128 +147,181 @@ struct Emitter {
   }
 };
 
-template <typename Tin, int OUT, int D, int T, int SIDE, bool TRANS>
-__global__ void __launch_bounds__(T * 8) divide_kernel(DivideArgs a) {
+// Register tree over the last LV levels: `in` holds the 4^LV sub-quadrant
+// vectors (base-4 path, top level most significant).
+template <typename Acc, int SIDE, int LV, int VEC>
+struct Tree {
+  template <class Emit>
+  __device__ __forceinline__ static void run(const Vec<Acc, VEC> (&in)[pow4c(LV)], int prefix, const Emit& emit) {
+    if constexpr (LV == 0) {
+      emit(prefix, in[0]);
+    } else {
+      constexpr int Q = pow4c(LV - 1);
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        Vec<Acc, VEC> o[Q];
+#pragma unroll
+        for (int h = 0; h < Q; ++h) o[h] = level_sum<SIDE, Vec<Acc, VEC>>(m, [&](int q) { return in[q * Q + h]; });
+        Tree<Acc, SIDE, LV - 1, VEC>::run(o, prefix * 7 + m, emit);
+      }
+    }
+  }
+};
+
+template <typename Tin, int VEC>
+struct Loader {
   using Acc = typename AccOf<Tin>::type;
-  constexpr int NT = T * 8;
-  constexpr int VEC = T / 8;
-  constexpr int G = (D == 0) ? 1 : pow4c(D - 1);
-  constexpr int LD = T + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc* s = reinterpret_cast<Acc*>(smem_raw);
+  const Tin* __restrict__ X;
+  int64_t n;
+  bool vec_ok;  // rows are VEC-aligned: vector loads allowed where in bounds
 
-  const int t = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.y * T;
-  const int64_t c0 = (int64_t)blockIdx.x * T;
-  const int64_t i0 = TRANS ? c0 : r0;
-  const int64_t j0 = TRANS ? r0 : c0;
-  const Tin* __restrict__ X = static_cast<const Tin*>(a.X);
-  const int64_t n = a.n, npad = a.npad;
+  __device__ __forceinline__ Vec<Acc, VEC> operator()(int64_t row, int64_t col) const {
+    Vec<Acc, VEC> r;
+    if (row < n && col + VEC <= n && vec_ok) {
+      const Tin* p = X + row * n + col;
+      if constexpr (sizeof(Tin) * VEC == 16) {
+        const int4 raw = __ldcs(reinterpret_cast<const int4*>(p));
+        const Tin* t = reinterpret_cast<const Tin*>(&raw);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)t[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)__ldcs(p + e);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e)
+        r.v[e] = (row < n && col + e < n) ? (Acc)__ldcs(X + row * n + col + e) : Acc(0);
+    }
+    return r;
+  }
+};
 
-  const int cr = t / 8;
-  const int cc = (t % 8) * VEC;
-  Emitter<OUT, Tin, VEC> emit{a.out_hi, a.out_lo, a.L * a.L, (r0 + cr) * a.L + c0 + cc};
-  const SmemSrc<Acc, T, VEC> src{s, cr * LD + cc};
+// The same two-term sums for a product index known only at run time:
+// value = x_qa, then (+ or -) x_qb when the product has a second term, in
+// the order written in level_sum (so the rounding is identical).
+struct TermPair {
+  int8_t qa, qb, sb;  // qb < 0: single term
+};
+template <int SIDE>
+__device__ __forceinline__ TermPair terms_of(int m) {
+  // A: M1 11+22, M2 21+22, M3 11, M4 22, M5 11+12, M6 21-11, M7 12-22
+  // B: M1 11+22, M2 11, M3 12-22, M4 21-11, M5 22, M6 11+12, M7 21+22
+  constexpr int8_t ta[7][3] = {{0, 3, 1}, {2, 3, 1}, {0, -1, 0}, {3, -1, 0}, {0, 1, 1}, {2, 0, -1}, {1, 3, -1}};
+  constexpr int8_t tb[7][3] = {{0, 3, 1}, {0, -1, 0}, {1, 3, -1}, {2, 0, -1}, {3, -1, 0}, {0, 1, 1}, {2, 3, 1}};
+  const int8_t* t = SIDE == 0 ? ta[m] : tb[m];
+  return TermPair{t[0], t[1], t[2]};
+}
 
-  auto load = [&](int64_t row, int64_t col) -> Acc {
-    return (row < n && col < n) ? (Acc)__ldg(&X[row * n + col]) : Acc(0);
+// Value at position (row, col) of the level-F operand sum S_F selected by the
+// M-indices dig[0..F) (top level first).  S_k(p) = level_sum(i_k, quadrant q
+// of S_{k-1} at p), S_0 = the input: the outermost sum is the deepest level,
+// so the rounding is exactly that of forming the levels one after another.
+template <int SIDE, typename Acc, int VEC, int F, class Load>
+struct Prefix {
+  __device__ __forceinline__ static Vec<Acc, VEC> eval(const Load& ld, const int* dig, int64_t npad, int64_t row,
+                                                       int64_t col) {
+    if constexpr (F == 0) {
+      return ld(row, col);
+    } else {
+      const int64_t h = npad >> F;  // quadrant side at level F
+      const TermPair t = terms_of<SIDE>(dig[F - 1]);
+      Vec<Acc, VEC> v = Prefix<SIDE, Acc, VEC, F - 1, Load>::eval(ld, dig, npad, row + (t.qa >> 1) * h,
+                                                                   col + (t.qa & 1) * h);
+      if (t.qb >= 0) {
+        const Vec<Acc, VEC> w = Prefix<SIDE, Acc, VEC, F - 1, Load>::eval(ld, dig, npad, row + (t.qb >> 1) * h,
+                                                                         col + (t.qb & 1) * h);
+        v = t.sb > 0 ? v + w : v - w;
+      }
+      return v;
+    }
+  }
+};
+
+template <typename Tin, int OUT, int D, int SIDE, int VEC>
+__global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok) {
+  using Acc = typename AccOf<Tin>::type;
+  constexpr int R = D < 2 ? D : 2;  // levels done in registers
+  constexpr int F = D - R;          // levels walked as an outer loop
+  const int64_t per_row = a.L / VEC;
+  const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= a.L * per_row) return;
+  const int64_t i = pos / per_row;
+  const int64_t j = (pos % per_row) * VEC;
+  const Loader<Tin, VEC> ld{static_cast<const Tin*>(a.X), a.n, vec_ok != 0};
+  const Emitter<OUT, Tin, VEC> emit{a.out_hi, a.out_lo, a.L * a.L, i * a.L + j};
+  const int64_t npad = a.npad;
+
+  auto leaf_block = [&](const int* dig, int prefix) {
+    // the 4^R sub-quadrant vectors below this prefix, then the register tree
+    Vec<Acc, VEC> in[pow4c(R)];
+#pragma unroll
+    for (int g = 0; g < pow4c(R); ++g) {
+      int64_t r = i, c = j;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int digit = (g >> (2 * (R - 1 - k))) & 3;
+        r += (int64_t)(digit >> 1) * (npad >> (F + k + 1));
+        c += (int64_t)(digit & 1) * (npad >> (F + k + 1));
+      }
+      in[g] = Prefix<SIDE, Acc, VEC, F, Loader<Tin, VEC>>::eval(ld, dig, npad, r, c);
+    }
+    Tree<Acc, SIDE, R, VEC>::run(in, prefix, emit);
   };
 
-  if constexpr (D == 0) {
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-      const int idx = t + e * NT;
-      const int ii = idx / T, jj = idx % T;
-      const Acc v = load(i0 + ii, j0 + jj);
-      s[(TRANS ? jj : ii) * LD + (TRANS ? ii : jj)] = v;
-    }
-    __syncthreads();
-    Tree<Acc, SIDE, 0, VEC>::run(src, 0, emit);
+  if constexpr (F == 0) {
+    leaf_block(nullptr, 0);
   } else {
-    const int64_t half = npad >> 1;
-    for (int m1 = 0; m1 < 7; ++m1) {
-      if (m1) __syncthreads();
-#pragma unroll 4
-      for (int g = 0; g < G; ++g) {
-        int64_t sub_r = 0, sub_c = 0;
+#pragma unroll 1
+    for (int p = 0; p < pow7c(F); ++p) {
+      int dig[F > 0 ? F : 1];
+      int x = p;
 #pragma unroll
-        for (int k = 2; k <= D; ++k) {
-          const int digit = (g / pow4c(D - k)) & 3;
-          sub_r += (int64_t)(digit >> 1) * (npad >> k);
-          sub_c += (int64_t)(digit & 1) * (npad >> k);
-        }
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const int idx = t + e * NT;
-          const int ii = idx / T, jj = idx % T;
-          const int64_t row = sub_r + i0 + ii, col = sub_c + j0 + jj;
-          const Acc v = level_sum<SIDE, Acc>(
-              m1, [&](int q1) { return load(row + (q1 >> 1) * half, col + (q1 & 1) * half); });
-          s[(g * T + (TRANS ? jj : ii)) * LD + (TRANS ? ii : jj)] = v;
-        }
+      for (int k = F - 1; k >= 0; --k) {
+        dig[k] = x % 7;
+        x /= 7;
       }
-      __syncthreads();
-      Tree<Acc, SIDE, D - 1, VEC>::run(src, m1, emit);
+      leaf_block(dig, p);
     }
   }
 }
 
-constexpr int pick_tile(int D, int esz) {
-  // largest T in {32, 16, 8} whose staging buffer fits 100 KB
-  return ((D == 0 ? 1 : pow4c(D - 1)) * 32 * 33 * esz <= 100 * 1024)   ? 32
-         : ((D == 0 ? 1 : pow4c(D - 1)) * 16 * 17 * esz <= 100 * 1024) ? 16
-                                                                        : 8;
-}
-
-template <typename Tin, int OUT, int D, int SIDE, bool TRANS>
+template <typename Tin, int OUT, int D, int SIDE>
 cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
-  using Acc = typename AccOf<Tin>::type;
-  constexpr int T = pick_tile(D, (int)sizeof(Acc));
-  constexpr int G = (D == 0) ? 1 : pow4c(D - 1);
-  constexpr int smem = G * T * (T + 1) * (int)sizeof(Acc);
-  auto kern = divide_kernel<Tin, OUT, D, T, SIDE, TRANS>;
-  if (a.L % T != 0) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t tiles = a.L / T;
-  if (tiles > 65535) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)tiles, (unsigned)tiles, 1);
-  kern<<<grid, T * 8, smem, st>>>(a);
+  constexpr int VEC = 16 / (int)sizeof(Tin);  // one 16-byte load per quadrant
+  if (a.L % VEC != 0) return cudaErrorInvalidValue;
+  const int vec_ok = (a.n % VEC == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+  const int64_t threads = a.L * (a.L / VEC);
+  const int64_t blocks = (threads + 255) / 256;
+  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  divide_kernel<Tin, OUT, D, SIDE, VEC><<<(unsigned)blocks, 256, 0, st>>>(a, vec_ok);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename Tin, int OUT, int SIDE, bool TRANS>
+template <typename Tin, int OUT, int SIDE>
 cudaError_t by_depth(const DivideArgs& a, int depth, cudaStream_t st) {
   switch (depth) {
-    case 0: return launch_one<Tin, OUT, 0, SIDE, TRANS>(a, st);
-    case 1: return launch_one<Tin, OUT, 1, SIDE, TRANS>(a, st);
-    case 2: return launch_one<Tin, OUT, 2, SIDE, TRANS>(a, st);
-    case 3: return launch_one<Tin, OUT, 3, SIDE, TRANS>(a, st);
-    case 4: return launch_one<Tin, OUT, 4, SIDE, TRANS>(a, st);
+    case 0: return launch_one<Tin, OUT, 0, SIDE>(a, st);
+    case 1: return launch_one<Tin, OUT, 1, SIDE>(a, st);
+    case 2: return launch_one<Tin, OUT, 2, SIDE>(a, st);
+    case 3: return launch_one<Tin, OUT, 3, SIDE>(a, st);
+    case 4: return launch_one<Tin, OUT, 4, SIDE>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, bool trans,
-                          cudaStream_t st) {
-  if (in == kInF32 && out == kOutSplitBf16) {
-    if (side == 0 && !trans) return by_depth<float, kOutSplitBf16, 0, false>(a, depth, st);
-    if (side == 1 && trans) return by_depth<float, kOutSplitBf16, 1, true>(a, depth, st);
-  } else if (in == kInF32 && out == kOutSplitTf32) {
-    if (side == 0 && !trans) return by_depth<float, kOutSplitTf32, 0, false>(a, depth, st);
-    if (side == 1 && trans) return by_depth<float, kOutSplitTf32, 1, true>(a, depth, st);
-  } else if (in == kInF64 && out == kOutPlain && !trans) {
-    return side == 0 ? by_depth<double, kOutPlain, 0, false>(a, depth, st)
-                     : by_depth<double, kOutPlain, 1, false>(a, depth, st);
-  } else if (in == kInI64 && out == kOutPlain && !trans) {
-    return side == 0 ? by_depth<int64_t, kOutPlain, 0, false>(a, depth, st)
-                     : by_depth<int64_t, kOutPlain, 1, false>(a, depth, st);
-  }
+cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t st) {
+  if (in == kInF32 && out == kOutSplitBf16)
+    return side == 0 ? by_depth<float, kOutSplitBf16, 0>(a, depth, st) : by_depth<float, kOutSplitBf16, 1>(a, depth, st);
+  if (in == kInF32 && out == kOutSplitTf32)
+    return side == 0 ? by_depth<float, kOutSplitTf32, 0>(a, depth, st) : by_depth<float, kOutSplitTf32, 1>(a, depth, st);
+  if (in == kInF64 && out == kOutPlain)
+    return side == 0 ? by_depth<double, kOutPlain, 0>(a, depth, st) : by_depth<double, kOutPlain, 1>(a, depth, st);
+  if (in == kInI64 && out == kOutPlain)
+    return side == 0 ? by_depth<int64_t, kOutPlain, 0>(a, depth, st) : by_depth<int64_t, kOutPlain, 1>(a, depth, st);
   return cudaErrorInvalidValue;
 }
 

@@ -8,9 +8,9 @@
 // Y = Y_hi + Y_lo (bf16 halves, or tf32 halves in fp32 containers), and
 //   M ~= X_lo Y_hi + X_hi Y_lo + X_hi Y_hi
 // accumulates in fp32 in tensor memory (the lo*lo term is below fp32
-// resolution of the result and is dropped).  Both operands are K-major: the
-// X planes are row-major (M x K) and the Y planes are stored transposed
-// (N x K) by the divide kernel.
+// resolution of the result and is dropped).  Both operand planes are
+// row-major as the divide kernel writes them: X (M x K) is a K-major
+// operand, Y (K x N) an MN-major one, loaded in 128-byte-wide N chunks.
 //
 // Persistent kernel, one CTA per SM, warp-specialised:
 //   warp 0      TMA producer: per k-block, 4 tiles (X_hi, X_lo, Y_hi, Y_lo)
@@ -32,16 +32,22 @@ constexpr int kThreads = 192;
 
 template <int BN, int STAGES, bool TF32>
 struct TcCfg {
-  static constexpr int BK = TF32 ? 32 : 64;         // elements per 128-byte row
-  static constexpr int A_BYTES = kBM * 128;          // one operand half tile
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int ESZ = TF32 ? 4 : 2;
+  static constexpr int BK = 128 / ESZ;               // K per stage: one 128-byte A row
+  static constexpr int A_BYTES = kBM * 128;          // one operand half tile (K-major)
+  static constexpr int W = 128 / ESZ;                // N elements per 128-byte B chunk
+  static constexpr int NCHUNK = BN / W;              // B chunks per half tile (MN-major)
+  static constexpr int CH_BYTES = BK * 128;          // one B chunk: BK rows of 128 bytes
+  static constexpr int B_BYTES = NCHUNK * CH_BYTES;  // == BN * 128
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int KSTEP_BYTES = 32;             // one MMA's K slice (16 bf16 / 8 tf32)
-  static constexpr int KSTEPS = 128 / KSTEP_BYTES;   // 4 MMAs (x3) per stage
+  static constexpr int MMA_K = 32 / ESZ;             // K of one MMA (16 bf16 / 8 tf32)
+  static constexpr int KSTEPS = BK / MMA_K;          // 4 MMAs (x3) per stage
+  static constexpr int A_KSTEP = 32;                 // bytes along a K-major row
+  static constexpr int B_KSTEP = MMA_K * 128;        // bytes down an MN-major chunk
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
   static constexpr int BAR_BYTES = 8 * (2 * STAGES + 4) + 16;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
-  static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32>();
+  static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, true>();
 };
 
 template <int BN, int STAGES, bool TF32>
@@ -115,8 +121,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = kb * Cfg::BK;
           tma_load_3d(st, &tmA, k0, m0, leaf, full_bar(s), pol);
           tma_load_3d(st + Cfg::A_BYTES, &tmA, k0, m0, p.P + leaf, full_bar(s), pol);
-          tma_load_3d(st + 2 * Cfg::A_BYTES, &tmB, k0, n0, leaf, full_bar(s), pol);
-          tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB, k0, n0, p.P + leaf, full_bar(s), pol);
+#pragma unroll
+          for (int c = 0; c < Cfg::NCHUNK; ++c) {
+            tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0, leaf, full_bar(s), pol);
+            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0,
+                        p.P + leaf, full_bar(s), pol);
+          }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
           if (++s == STAGES) {
@@ -156,11 +166,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
 #pragma unroll
           for (int k = 0; k < Cfg::KSTEPS; ++k) {
-            const uint32_t off = k * Cfg::KSTEP_BYTES;
-            const uint64_t a_hi = smem_desc_k_sw128(st + off);
-            const uint64_t a_lo = smem_desc_k_sw128(st + Cfg::A_BYTES + off);
-            const uint64_t b_hi = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + off);
-            const uint64_t b_lo = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + off);
+            const uint32_t aoff = k * Cfg::A_KSTEP, boff = k * Cfg::B_KSTEP;
+            const uint64_t a_hi = smem_desc_k_sw128(st + aoff);
+            const uint64_t a_lo = smem_desc_k_sw128(st + Cfg::A_BYTES + aoff);
+            const uint64_t b_hi = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+            const uint64_t b_lo = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
             const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
             if constexpr (TF32) {
               mma_tf32(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
@@ -257,6 +267,7 @@ template <int BN, int STAGES, bool TF32>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int num_sms,
                        cudaStream_t st) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
+  static_assert(Cfg::B_BYTES == BN * 128, "B tile size");
   if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
   auto kern = leaf_tc_kernel<BN, STAGES, TF32>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);

@@ -97,8 +97,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// planes [planes][L][L] of bf16 (or fp32 holding tf32), K innermost; box =
-// one 128-byte K slice x box_rows rows of one plane, 128-byte swizzle.
+// planes [planes][L][L] of bf16 (or fp32 holding tf32), row-major; box =
+// 128 bytes of a row x box_rows rows of one plane, 128-byte swizzle.  For
+// the K-major X planes a box is a 128-byte K slice of box_rows M rows; for
+// the MN-major Y planes it is a 128-byte N chunk of box_rows K rows.
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -418,7 +420,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
   if (p->is_tc) {
     const bool tf32 = dt == STARK_F32_SPLIT_TF32;
     if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * p->P, 128) ||
-        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, p->bn))
+        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, tf32 ? 32 : 64))
       return STARK_EUNSUPPORTED;
   }
   return STARK_OK;
@@ -456,9 +458,9 @@ stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStre
     da.out_lo = static_cast<char*>(p->X) + half;
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
-  stark_status st = to_status(launch_divide(da, p->depth, 0, in, om, false, s));
+  stark_status st = to_status(launch_divide(da, p->depth, 0, in, om, s));
   if (st != STARK_OK) return st;
-  return to_status(launch_divide(db, p->depth, 1, in, om, p->is_tc, s));
+  return to_status(launch_divide(db, p->depth, 1, in, om, s));
 }
 
 stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,

@@ -228,15 +228,31 @@ __device__ __forceinline__ uint64_t smem_desc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand tile with the
+// 128-byte swizzle: each 128-byte row holds 128 bytes of consecutive M/N
+// elements at one k; 8 consecutive k rows form a 1024-byte swizzle atom.
+//   leading-dimension byte offset = distance between consecutive 128-byte
+//   M/N chunks; stride-dimension byte offset = distance between consecutive
+//   8-row groups along K (1024 when the k rows of a chunk are contiguous).
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr, uint32_t chunk_stride_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((chunk_stride_bytes >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor for tcgen05.mma kind::f16 / kind::tf32 with fp32
-// accumulation, both operands K-major, dense, no negation.
+// accumulation, dense, no negation; A K-major, B K-major or MN-major.
 //   bits 4-5 D format (1 = f32); bits 7-9 A format, 10-12 B format
-//   (kind::f16: 1 = bf16; kind::tf32: 2 = tf32); bit 15/16 A/B major (0 = K);
-//   bits 17-22 N >> 3; bits 24-28 M >> 4.
-template <int M, int N, bool TF32>
+//   (kind::f16: 1 = bf16; kind::tf32: 2 = tf32); bit 15/16 A/B major
+//   (0 = K-major, 1 = MN-major); bits 17-22 N >> 3; bits 24-28 M >> 4.
+template <int M, int N, bool TF32, bool B_MN_MAJOR>
 __host__ __device__ constexpr uint32_t make_idesc() {
-  return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((B_MN_MAJOR ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 }  // namespace stark

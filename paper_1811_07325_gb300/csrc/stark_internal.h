@@ -65,11 +65,9 @@ struct DivideArgs {
   void* out_lo;       // planes [P][L][L] (split: lo part; plain: unused)
 };
 
-// Divide phase for one operand: writes the 7^depth leaf operand sums.
-// side 0 = A (row-major planes), side 1 = B; `trans` stores each B plane
-// transposed (N x K, K contiguous) for K-major tensor-core operands.
-cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, bool trans,
-                          cudaStream_t s);
+// Divide phase for one operand: writes the 7^depth leaf operand sums as
+// row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
+cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 
 struct LeafTcArgs {
   int32_t P;           // leaves per operand side (planes 0..P-1 hi, P..2P-1 lo)

@@ -9,12 +9,15 @@ Bars (written here, derived in the comments):
     "Accuracy and Stability of Numerical Algorithms", 2nd ed.), and the
     normwise ratio max|dC| / (||A||_F ||B||_F) <= 1e-12.
   * split fp32 (3xBF16, 3xTF32): normwise ratio <= 1e-6, and a bug-signal
-    bound on the relative RMS error, rms(dC) / rms(C):
-      3xBF16: operands carry 16 significant bits (8 + 8), products lose
-      ~2^-16 relative, fp32 accumulation adds ~2^-24 sqrt(L); a dropped cross
-      term would leave ~2^-8.  Bound: 2^-12.
-      3xTF32: 22 bits, ~2^-21 relative; a dropped term leaves ~2^-11.
-      Bound: 2^-16.
+    bound on the relative RMS error, rms(dC) / rms(C) <= s + 3 (L / k) 2^-24:
+      s: the split.  3xBF16 operands carry 16 significant bits (8 + 8), each
+      product is off by ~2^-16 relative, a dropped cross term would leave
+      ~2^-8: s = 2^-12.  3xTF32 carries 22 bits: s = 2^-16 (a dropped term
+      leaves ~2^-11).
+      3 (L / k) 2^-24: the tensor-core accumulation, up to one fp32 ulp per
+      accumulating MMA (k = 16 bf16 / 8 tf32 per MMA, 3 MMAs per K step,
+      L = leaf side): at L = 4096 this term, not the split, dominates, which
+      is why 3xTF32 is measured no more accurate than 3xBF16 there.
 """
 import numpy as np
 import pytest
@@ -88,7 +91,7 @@ def test_int64_equals_oracle_strassen(S):
 
 # ----------------------------------------------------------------- divide phase
 @pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
-@pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3)])
+@pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3), (1001, 4)])
 def test_divide_split_bit_exact(S, dtype, n, d):
     dt = S.DType[dtype]
     A = synth.normal(n, 7 + d, 0)
@@ -105,11 +108,10 @@ def test_divide_split_bit_exact(S, dtype, n, d):
         xh, xl = split(xa)
         yh, yl = split(yb)
         assert np.array_equal(X[:P], xh) and np.array_equal(X[P:], xl)
-        # B planes are stored transposed (N x K) for the K-major tensor-core operand
-        assert np.array_equal(Y[:P].transpose(0, 2, 1), yh) and np.array_equal(Y[P:].transpose(0, 2, 1), yl)
+        assert np.array_equal(Y[:P], yh) and np.array_equal(Y[P:], yl)
 
 
-@pytest.mark.parametrize("n,d", [(200, 1), (300, 2)])
+@pytest.mark.parametrize("n,d", [(200, 1), (300, 2), (513, 3), (999, 4)])
 def test_divide_plain_f64_matches_oracle_sums(S, n, d):
     # integer-valued doubles: the oracle's fp32 sums are exact, so they must equal the fp64 planes
     A = synth.integers(n, 3, 0, -1000, 1000).astype(np.float64)
@@ -147,7 +149,10 @@ SPLIT_BOUND = {"F32_SPLIT_BF16": 2.0 ** -12, "F32_SPLIT_TF32": 2.0 ** -16}
 SPLIT_U2 = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22}
 
 
-def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=0):
+MMA_K = {"F32_SPLIT_BF16": 16, "F32_SPLIT_TF32": 8}
+
+
+def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=0, L=None):
     """Normwise bound 1e-6 (the configs' sizes, n >= 64) and the RMS bug
     signal; tiny n, where averaging cannot bring the 16/22-bit split below
     1e-6 of ||A|| ||B||, gets the componentwise bound instead:
@@ -157,8 +162,9 @@ def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=0):
     rel_rms = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
     n = want.shape[1]
     if n >= 64:
+        L = n if L is None else L
         assert ratio <= 1e-6, ratio
-        assert rel_rms <= SPLIT_BOUND[dtype], rel_rms
+        assert rel_rms <= SPLIT_BOUND[dtype] + 3 * (L / MMA_K[dtype]) * 2.0 ** -24, rel_rms
     else:
         absAB = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
         tol = (3 * SPLIT_U2[dtype] + n * 2.0 ** -23) * 3 ** d * absAB
@@ -180,7 +186,7 @@ def test_split_within_bound(S, dtype, n, depths):
         with S.Plan(n, d, dt) as p:
             C = p.mul(dA, dB)
             p.check()
-            check_split(C.cpu().numpy(), want, an, bn, dtype, A, B, d)
+            check_split(C.cpu().numpy(), want, an, bn, dtype, A, B, d, L=p.leaf)
 
 
 def test_split_repeatable_and_stream_ordered(S):
@@ -250,7 +256,8 @@ def test_auto_depth(S):
 
 # ----------------------------------------------------------------- full size, sampled rows
 @pytest.mark.slow
-@pytest.mark.parametrize("dtype,d", [("F32_SPLIT_BF16", 2), ("F32_SPLIT_BF16", 3), ("F32_SPLIT_TF32", 2)])
+@pytest.mark.parametrize("dtype,d", [("F32_SPLIT_BF16", 2), ("F32_SPLIT_BF16", 3), ("F32_SPLIT_TF32", 2),
+                                     ("F32_SPLIT_TF32", 3)])
 def test_full_size_sampled_rows(S, dtype, d):
     n = 16384
     A = synth.normal(n, 2024, 0)
@@ -263,6 +270,7 @@ def test_full_size_sampled_rows(S, dtype, d):
         C = p.mul(dA, dB)
         p.check()
         got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+        L = p.leaf
     del C, dA, dB
     torch.cuda.empty_cache()
-    check_split(got, want, an, bn, dtype)
+    check_split(got, want, an, bn, dtype, L=L)
