@@ -122,11 +122,19 @@ STARK_API stark_status stark_mul_leaves(stark_plan_t plan, const void *A, const 
  * inspection by tests.  Layout: split dtypes hold [2*leaves][L][L] planes
  * (hi planes, then lo planes; bf16 values, or TF32 values in fp32
  * containers); F64/I64 hold [leaves][L][L].  Every plane is row-major: A
- * planes are the leaf's M x K operand, B planes its K x N operand.  The
+ * planes are the leaf's M x K operand, B planes its K x N operand, except
+ * for F32_SPLIT_TF32 whose B planes are stored transposed (N x K).  The
  * pointers stay valid until the plan is destroyed and are overwritten by the
  * next product. */
 STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, const void *B, void *stream, const void **X,
                                  const void **Y);
+
+/* How the fused combine adds leaf tiles into C on the tensor-core dtypes:
+ * mode 0 (default) uses TMA bulk add-reductions of 32 x 32 boxes whenever C
+ * is addressable by TMA (16-byte aligned, n a multiple of 4) and signed
+ * vector atomics otherwise; mode 1 always uses the atomics.  Results agree
+ * within fp32 rounding (the order of the additions into C differs). */
+STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
 /* Synchronise the plan's last stream and report any device-side error
  * (STARK_ETIMEOUT) recorded by its kernels since the previous check; the

@@ -8,9 +8,10 @@
 // Y = Y_hi + Y_lo (bf16 halves, or tf32 halves in fp32 containers), and
 //   M ~= X_lo Y_hi + X_hi Y_lo + X_hi Y_hi
 // accumulates in fp32 in tensor memory (the lo*lo term is below fp32
-// resolution of the result and is dropped).  Both operand planes are
-// row-major as the divide kernel writes them: X (M x K) is a K-major
-// operand, Y (K x N) an MN-major one, loaded in 128-byte-wide N chunks.
+// resolution of the result and is dropped).  X planes (M x K, row-major) are
+// a K-major operand.  For bf16 the Y planes stay row-major (K x N) and are an
+// MN-major operand, loaded in 128-byte-wide N chunks; for tf32 they are
+// transposed in place to N x K beforehand and read K-major.
 //
 // Persistent kernel, one CTA per SM, warp-specialised:
 //   warp 0      TMA producer: per k-block, 4 tiles (X_hi, X_lo, Y_hi, Y_lo)
@@ -35,37 +36,41 @@ struct TcCfg {
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int BK = 128 / ESZ;               // K per stage: one 128-byte A row
   static constexpr int A_BYTES = kBM * 128;          // one operand half tile (K-major)
-  static constexpr int W = 128 / ESZ;                // N elements per 128-byte B chunk
-  static constexpr int NCHUNK = BN / W;              // B chunks per half tile (MN-major)
-  static constexpr int CH_BYTES = BK * 128;          // one B chunk: BK rows of 128 bytes
+  static constexpr bool B_MN = !TF32;                // B operand MN-major (bf16) or K-major (tf32)
+  static constexpr int W = B_MN ? 128 / ESZ : BN;    // N elements per B TMA box
+  static constexpr int NCHUNK = BN / W;              // B boxes per half tile
+  static constexpr int CH_BYTES = B_MN ? BK * 128 : BN * 128;  // bytes per B box
   static constexpr int B_BYTES = NCHUNK * CH_BYTES;  // == BN * 128
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int MMA_K = 32 / ESZ;             // K of one MMA (16 bf16 / 8 tf32)
   static constexpr int KSTEPS = BK / MMA_K;          // 4 MMAs (x3) per stage
   static constexpr int A_KSTEP = 32;                 // bytes along a K-major row
-  static constexpr int B_KSTEP = MMA_K * 128;        // bytes down an MN-major chunk
+  static constexpr int B_KSTEP = B_MN ? MMA_K * 128 : 32;  // bytes per MMA K step in a B box
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
+  static constexpr int EPI_BYTES = 4 * 2 * 4096;     // per epilogue warp: a +/- pair of 32x32 fp32 boxes
   static constexpr int BAR_BYTES = 8 * (2 * STAGES + 4) + 16;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
-  static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, true>();
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + BAR_BYTES;
+  static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, B_MN>();
 };
 
 template <int BN, int STAGES, bool TF32>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const LeafTcArgs p) {
+                   const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bar_base = sbase + STAGES * Cfg::STAGE_BYTES;
+  const uint32_t epi_base = sbase + STAGES * Cfg::STAGE_BYTES;
+  const uint32_t bar_base = epi_base + Cfg::EPI_BYTES;
   auto full_bar = [&](int s) { return bar_base + 8 * s; };
   auto empty_bar = [&](int s) { return bar_base + 8 * (STAGES + s); };
   auto accf_bar = [&](int a) { return bar_base + 8 * (2 * STAGES + a); };
   auto acce_bar = [&](int a) { return bar_base + 8 * (2 * STAGES + 2 + a); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * Cfg::STAGE_BYTES + 8 * (2 * STAGES + 4));
+  uint32_t* tmem_slot =
+      reinterpret_cast<uint32_t*>(smem + STAGES * Cfg::STAGE_BYTES + Cfg::EPI_BYTES + 8 * (2 * STAGES + 4));
 
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
@@ -88,6 +93,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
+    if (p.use_tma_c) prefetch_tmap(&tmC);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
@@ -121,11 +127,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = kb * Cfg::BK;
           tma_load_3d(st, &tmA, k0, m0, leaf, full_bar(s), pol);
           tma_load_3d(st + Cfg::A_BYTES, &tmA, k0, m0, p.P + leaf, full_bar(s), pol);
+          if constexpr (Cfg::B_MN) {
 #pragma unroll
-          for (int c = 0; c < Cfg::NCHUNK; ++c) {
-            tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0, leaf, full_bar(s), pol);
-            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0,
-                        p.P + leaf, full_bar(s), pol);
+            for (int c = 0; c < Cfg::NCHUNK; ++c) {
+              tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
+                          pol);
+              tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0,
+                          p.P + leaf, full_bar(s), pol);
+            }
+          } else {
+            tma_load_3d(st + 2 * Cfg::A_BYTES, &tmB, k0, n0, leaf, full_bar(s), pol);
+            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB, k0, n0, p.P + leaf, full_bar(s), pol);
           }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
@@ -169,8 +181,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t aoff = k * Cfg::A_KSTEP, boff = k * Cfg::B_KSTEP;
             const uint64_t a_hi = smem_desc_k_sw128(st + aoff);
             const uint64_t a_lo = smem_desc_k_sw128(st + Cfg::A_BYTES + aoff);
-            const uint64_t b_hi = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
-            const uint64_t b_lo = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+            uint64_t b_hi, b_lo;
+            if constexpr (Cfg::B_MN) {
+              b_hi = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+              b_lo = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+            } else {
+              b_hi = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + boff);
+              b_lo = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
+            }
             const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
             if constexpr (TF32) {
               mma_tf32(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
@@ -206,8 +224,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // Combine (Alg. 5) fused here: the accumulator tile of leaf l is added,
+    // with its sign, into every C target of l.  Fast path: each warp stages
+    // its 32 x 32 fp32 box (and its negation when a target needs it) in
+    // shared memory with the 128-byte swizzle and issues one TMA bulk
+    // add-reduction per target (the add happens at L2).  Fallback (C not
+    // 16-byte addressable by TMA): signed vector atomics from registers.
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     const int row_in_tile = quarter * 32 + lane;
+    const uint32_t ebuf = epi_base + (uint32_t)(warp - 2) * 8192u;  // [+ box][- box]
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int item = blockIdx.x; item < num_items; item += gridDim.x) {
@@ -219,32 +244,66 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int n0 = (rem % tiles_n) * BN;
       const int nt = p.ccount[leaf];
       const CTarget* tg = p.ctab + (int64_t)leaf * p.maxT;
+      bool has_pos = false, has_neg = false;
+      for (int t = 0; t < nt; ++t) (tg[t].sign > 0 ? has_pos : has_neg) = true;
       const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) && ((p.ldc & 3) == 0);
 #pragma unroll 1
       for (int chunk = 0; chunk < BN / 32; ++chunk) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + chunk * 32), r);
         tmem_ld_wait();
-#pragma unroll 1
-        for (int t = 0; t < nt; ++t) {
-          const CTarget c = tg[t];
-          const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
-          const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
-          if (grow >= p.n || gcol >= p.n) continue;
-          float* dst = p.C + grow * p.ldc + gcol;
-          const float sg = (float)c.sign;
-          if (vec_ok && gcol + 32 <= p.n) {
+        if (p.use_tma_c) {
+          if (lane == 0) bulk_wait_group_read<0>();  // the previous boxes have been read
+          __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
-                                     sg * __uint_as_float(r[4 * j + 2]), sg * __uint_as_float(r[4 * j + 3]));
-              atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
+          for (int sg = 0; sg < 2; ++sg) {
+            if (sg == 0 ? !has_pos : !has_neg) continue;
+            const uint32_t row_addr = ebuf + (uint32_t)sg * 4096u + (uint32_t)lane * 128u;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float4 v = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                     __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+              if (sg == 1) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+              const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
+              asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                           "f"(v.w)
+                           : "memory");
             }
-          } else {
-            const int64_t lim = p.n - gcol;
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            for (int t = 0; t < nt; ++t) {
+              const CTarget c = tg[t];
+              const int64_t y = (int64_t)c.row_off + m0 + quarter * 32;
+              const int64_t x = (int64_t)c.col_off + n0 + chunk * 32;
+              if (y >= p.n || x >= p.n) continue;
+              tma_reduce_add_2d(&tmC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u));
+            }
+            bulk_commit_group();
+          }
+        } else {
+#pragma unroll 1
+          for (int t = 0; t < nt; ++t) {
+            const CTarget c = tg[t];
+            const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
+            const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
+            if (grow >= p.n || gcol >= p.n) continue;
+            float* dst = p.C + grow * p.ldc + gcol;
+            const float sg = (float)c.sign;
+            if (vec_ok && gcol + 32 <= p.n) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
+              for (int j = 0; j < 8; ++j) {
+                float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
+                                       sg * __uint_as_float(r[4 * j + 2]), sg * __uint_as_float(r[4 * j + 3]));
+                atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
+              }
+            } else {
+              const int64_t lim = p.n - gcol;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
+            }
           }
         }
       }
@@ -255,6 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         acc_phase ^= 1;
       }
     }
+    // every bulk reduction issued by this warp completes before the CTA exits
+    if (p.use_tma_c && lane == 0) bulk_wait_group<0>();
   }
 
   tc_fence_before();
@@ -264,8 +325,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int BN, int STAGES, bool TF32>
-cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int num_sms,
-                       cudaStream_t st) {
+cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
+                       int num_sms, cudaStream_t st) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
   static_assert(Cfg::B_BYTES == BN * 128, "B tile size");
   if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
@@ -276,7 +337,7 @@ cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtens
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
   const int grid = (int)(items < num_sms ? items : num_sms);
-  kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, a);
+  kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, *tmC, a);
   count_launch();
   return cudaGetLastError();
 }
@@ -288,15 +349,15 @@ int leaf_tc_smem_bytes(bool tf32, int bn) {
   return tf32 ? TcCfg<128, 3, true>::SMEM : TcCfg<128, 3, false>::SMEM;
 }
 
-cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, bool tf32, int bn,
-                           int num_sms, cudaStream_t st) {
+cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                           const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
   if (bn == 256) {
-    return tf32 ? launch_cfg<256, 2, true>(a, tmA, tmB, num_sms, st)
-                : launch_cfg<256, 2, false>(a, tmA, tmB, num_sms, st);
+    return tf32 ? launch_cfg<256, 2, true>(a, tmA, tmB, tmC, num_sms, st)
+                : launch_cfg<256, 2, false>(a, tmA, tmB, tmC, num_sms, st);
   }
   if (bn == 128) {
-    return tf32 ? launch_cfg<128, 3, true>(a, tmA, tmB, num_sms, st)
-                : launch_cfg<128, 3, false>(a, tmA, tmB, num_sms, st);
+    return tf32 ? launch_cfg<128, 3, true>(a, tmA, tmB, tmC, num_sms, st)
+                : launch_cfg<128, 3, false>(a, tmA, tmB, tmC, num_sms, st);
   }
   return cudaErrorInvalidValue;
 }

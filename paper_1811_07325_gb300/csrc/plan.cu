@@ -115,6 +115,18 @@ bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t 
   return r == CUDA_SUCCESS;
 }
 
+bool make_tmap_c(CUtensorMap* m, void* C, int64_t n) {
+  auto fn = encode_fn();
+  if (!fn || n <= 0 || (n % 4) != 0 || (reinterpret_cast<uintptr_t>(C) & 15) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(n * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------ self test
 
 __global__ void wait_selftest_kernel(const int* flag, int* err, uint64_t timeout_ns) {
@@ -306,6 +318,12 @@ stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* 
   return stark_plan_check(p, stream);
 }
 
+stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
+  if (!p || mode < 0 || mode > 1) return STARK_EINVAL;
+  p->combine_mode = mode;
+  return STARK_OK;
+}
+
 stark_status stark_plan_check(stark_plan_t p, void* stream) {
   if (!p) return STARK_EINVAL;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
@@ -420,7 +438,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
   if (p->is_tc) {
     const bool tf32 = dt == STARK_F32_SPLIT_TF32;
     if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * p->P, 128) ||
-        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, tf32 ? 32 : 64))
+        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, tf32 ? p->bn : 64))
       return STARK_EUNSUPPORTED;
   }
   return STARK_OK;
@@ -460,7 +478,11 @@ stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStre
   }
   stark_status st = to_status(launch_divide(da, p->depth, 0, in, om, s));
   if (st != STARK_OK) return st;
-  return to_status(launch_divide(db, p->depth, 1, in, om, s));
+  st = to_status(launch_divide(db, p->depth, 1, in, om, s));
+  if (st != STARK_OK) return st;
+  if (p->dt == STARK_F32_SPLIT_TF32)  // the 3xTF32 leaf GEMM takes B K-major (N x K planes)
+    st = to_status(launch_transpose_planes(static_cast<float*>(p->Y), p->L, 2 * p->P, s));
+  return st;
 }
 
 stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
@@ -489,7 +511,10 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     a.n = p->n;
     a.err = p->d_err;
     a.timeout_ns = p->timeout_ns;
-    st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
+    CUtensorMap tmC;
+    std::memset(&tmC, 0, sizeof(tmC));
+    a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, C, p->n)) ? 1 : 0;
+    st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
   } else {
     LeafCcArgs a{};
     a.P = (int32_t)p->P;

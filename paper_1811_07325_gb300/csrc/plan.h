@@ -44,6 +44,7 @@ struct stark_plan_s {
   int32_t maxT = 1;
   int* d_err = nullptr;
   uint64_t timeout_ns = stark::kDefaultTimeoutNs;
+  int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics
   CUtensorMap tmA;
   CUtensorMap tmB;
   // end-to-end staging (stark_mul_host), allocated on first use

@@ -68,6 +68,8 @@ struct DivideArgs {
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
+// In-place transpose of `count` square L x L fp32 planes.
+cudaError_t launch_transpose_planes(float* planes, int64_t L, int64_t count, cudaStream_t s);
 
 struct LeafTcArgs {
   int32_t P;           // leaves per operand side (planes 0..P-1 hi, P..2P-1 lo)
@@ -82,11 +84,12 @@ struct LeafTcArgs {
   int64_t n;
   int* err;
   uint64_t timeout_ns;
+  int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
 };
 
 // 3xBF16 / 3xTF32 leaf GEMMs with the combine fused in the epilogue.
-cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, bool tf32, int bn,
-                           int num_sms, cudaStream_t s);
+cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                           const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t s);
 int leaf_tc_smem_bytes(bool tf32, int bn);
 
 struct LeafCcArgs {
@@ -109,5 +112,7 @@ void count_launch(int k = 1);
 int device_sm_count();
 bool device_is_sm100_family();
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows);
+// n x n fp32 row-major C, 32 x 32 boxes, 128-byte swizzle (reduction target).
+bool make_tmap_c(CUtensorMap* m, void* C, int64_t n);
 
 }  // namespace stark

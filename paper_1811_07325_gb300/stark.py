@@ -62,6 +62,7 @@ _SIGS = {
     "stark_mul_leaves": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _ci),
     "stark_plan_operands": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _ci),
     "stark_plan_check": ([_vp, _vp], _ci),
+    "stark_plan_set_combine": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
@@ -216,6 +217,10 @@ class Plan:
         if view is not None:
             X, Y = X.view(view), Y.view(view)
         return X, Y
+
+    def set_combine(self, mode: int):
+        """0: TMA bulk reductions where possible (default), 1: vector atomics."""
+        _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
 
     def check(self, stream=None):
         """Synchronise and raise on a device-side timeout."""

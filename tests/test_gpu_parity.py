@@ -108,6 +108,8 @@ def test_divide_split_bit_exact(S, dtype, n, d):
         xh, xl = split(xa)
         yh, yl = split(yb)
         assert np.array_equal(X[:P], xh) and np.array_equal(X[P:], xl)
+        if dt == S.DType.F32_SPLIT_TF32:  # stored N x K for the K-major TF32 operand
+            Y = Y.transpose(0, 2, 1)
         assert np.array_equal(Y[:P], yh) and np.array_equal(Y[P:], yl)
 
 
@@ -205,6 +207,25 @@ def test_split_repeatable_and_stream_ordered(S):
         an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
         check_split(C1.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
         check_split(C2.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
+
+
+@pytest.mark.parametrize("n,d", [(1024, 2), (1000, 3), (1004, 1)])
+def test_split_combine_modes_agree(S, n, d):
+    # TMA bulk reductions and the vector-atomic fallback give the same product
+    A = synth.normal(n, 61, 0)
+    B = synth.normal(n, 61, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    out = []
+    for mode in (0, 1):
+        with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
+            p.set_combine(mode)
+            C = p.mul(dev(A), dev(B))
+            p.check()
+            out.append(C.cpu().numpy())
+            check_split(out[-1], want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+    # same products, different addition order into C: fp32-level agreement
+    assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
 
 # ----------------------------------------------------------------- API paths
