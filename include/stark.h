@@ -151,6 +151,34 @@ STARK_API stark_status stark_plan_check(stark_plan_t plan, void *stream);
 STARK_API stark_status stark_plan_set_timing(stark_plan_t plan, int records);
 STARK_API stark_status stark_plan_phase_ms(stark_plan_t plan, float out_ms[3]);
 
+/* ----------------------------------------------------------------- no allocation */
+
+/* Size of the fixed device scratch array behind stark_mul_noalloc. */
+#define STARK_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* C = A * B for fp32 matrices with 3xBF16 leaves, like stark_mul on a plan of
+ * dtype STARK_F32_SPLIT_BF16, but without allocating any device memory: for
+ * callers that cannot call cudaMalloc (code that may not enter a memory
+ * allocator, or that runs inside a fixed device-memory budget it may not
+ * grow).  The paper has no counterpart; this is a deployment variant.
+ *
+ * The workspace is a file-scope device array of STARK_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) that every GPU which loads it keeps until the process exits.
+ * Problems whose workspace does not fit are rejected with STARK_ENOMEM
+ * (e.g. n <= 2048 fits at depth 0 or 1, n <= 1024 at depth 2).
+ * A, B, C: device pointers to n x n row-major fp32 matrices; C is
+ * overwritten.  depth: 0..3 (no automatic choice).  Asynchronous on
+ * `stream`; nothing is allocated, and no device-side timeout is reported
+ * (the error word lives in the shared scratch).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and must come before any stream capture.  Every
+ * call reuses the same array: calls that overlap on the GPU (other streams
+ * or threads) race and must be ordered by the caller.
+ * Errors: EINVAL (bad n or depth, null pointer), ENOMEM (over the scratch
+ * size), EUNSUPPORTED (not a GB300), ECUDA. */
+STARK_API stark_status stark_mul_noalloc(int64_t n, int depth, const void *A, const void *B, void *C,
+                                         void *stream);
+
 /* ----------------------------------------------------------------- tables */
 
 /* The quadrant-index table ("block tags", Sec. III-B) for `depth` levels,
