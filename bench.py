@@ -119,6 +119,117 @@ def cpu_baseline(n, seed, budget_s=12.0, rows_cap=256):
                       f"{t:.1f} s on {threads} OpenMP threads"}
 
 
+def run_batch(args, stark, synth, torch):
+    """Batched form: 64 products, n drawn from {512, ..., 4096}, FP32 U[-1,1],
+    3xBF16, autotuned depth; one grouped graph-replayed launch per step,
+    compared with the same products issued one by one."""
+    sizes = synth.batch_sizes(args.batch_count, args.seed + 11)
+    As = [torch.from_numpy(synth.uniform(n, args.seed + 100 + i, 0, dtype=np.float32)).cuda()
+          for i, n in enumerate(sizes)]
+    Bs = [torch.from_numpy(synth.uniform(n, args.seed + 100 + i, 1, dtype=np.float32)).cuda()
+          for i, n in enumerate(sizes)]
+    Cs = [torch.empty((n, n), device="cuda") for n in sizes]
+    flops = sum(2.0 * n ** 3 for n in sizes)
+    t_create = time.perf_counter()
+    bt = stark.Batch(sizes, -1, stark.DType.F32_SPLIT_BF16)
+    t_create = time.perf_counter() - t_create
+    for _ in range(3):
+        bt.mul(As, Bs, Cs)
+    bt.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        bt.mul(As, Bs, Cs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    info = bt.info()
+    depths = bt.depths()
+    bt.close()
+    # the same products one plan at a time (no grouping, no graph)
+    plans = {}
+    for n, d in zip(sizes, depths):
+        if n not in plans:
+            plans[n] = stark.Plan(n, d, stark.DType.F32_SPLIT_BF16)
+    for i, n in enumerate(sizes):
+        plans[n].mul(As[i], Bs[i], Cs[i])
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        for i, n in enumerate(sizes):
+            plans[n].mul(As[i], Bs[i], Cs[i])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / 3
+    for p in plans.values():
+        p.close()
+    return {"workload": f"{len(sizes)} products, n in {{512..4096}} (seeded), fp32 U[-1,1], 3xbf16, autotuned depth",
+            "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_batch": ms,
+            "one_by_one_tflops": flops / (ms_seq * 1e-3) / 1e12, "depths": depths, "tile_n": info["tile_n"],
+            "work_items": info["work_items"], "create_and_autotune_s": t_create,
+            "graph_replays": info["graph_replays"]}
+
+
+def run_serve(args, stark, synth, torch):
+    """Served form: Poisson arrivals (200/s), n log-uniform in [256, 8192],
+    FP32 N(0,1), 3xBF16, device budget 150 GB; latency from submission to
+    observed completion.  A first pass over the same sizes warms the
+    workspace cache (not measured)."""
+    import threading as th
+    count = args.serve_requests
+    sizes = synth.loguniform_sizes(count, args.seed + 21, 256, 8192)
+    nmax = max(sizes)
+    poolA = torch.from_numpy(synth.normal(nmax, args.seed + 22, 0)).cuda().reshape(-1)
+    poolB = torch.from_numpy(synth.normal(nmax, args.seed + 22, 1)).cuda().reshape(-1)
+    srv = stark.Server(150 * 10 ** 9, slots=4)
+
+    def one_pass(gaps):
+        Cs, ids, lock = {}, [], th.Lock()
+        start = time.perf_counter()
+
+        def producer():
+            t = start
+            for n, g in zip(sizes, gaps):
+                t += g
+                while True:
+                    now = time.perf_counter()
+                    if now >= t:
+                        break
+                    time.sleep(min(t - now, 0.0005))
+                C = torch.empty((n, n), device="cuda")
+                rid = srv.submit(poolA[:n * n].view(n, n), poolB[:n * n].view(n, n), C)
+                with lock:
+                    Cs[rid] = C
+                    ids.append(rid)
+
+        thr = th.Thread(target=producer)
+        thr.start()
+        thr.join()
+        srv.drain()
+        end = time.perf_counter()
+        lat = []
+        for rid in ids:
+            done, st = srv.poll(rid)
+            assert done and st == stark.Status.OK, st
+            lat.append(srv.latency(rid))
+        return np.array(lat), end - start
+
+    rate = 200.0
+    torch.cuda.synchronize()
+    one_pass(synth.exponential_gaps(count, args.seed + 23, rate))           # warm the workspace cache
+    lat, wall = one_pass(synth.exponential_gaps(count, args.seed + 24, rate))
+    stats = srv.stats()
+    srv.close()
+    flops = sum(2.0 * n ** 3 for n in sizes)
+    return {"workload": f"Poisson 200 req/s, {count} requests, n log-uniform [256, 8192], fp32 N(0,1), 3xbf16, "
+                        f"budget 150 GB, 4 slots",
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "aggregate_tflops": flops / wall / 1e12,
+            "offered_tflops": flops / (count / rate) / 1e12, "wall_s": wall,
+            "cached_workspaces": stats["cached_workspaces"], "workspace_bytes": stats["owned_bytes"]}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle, timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -166,6 +277,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=600)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -275,6 +390,7 @@ def main():
                 "launch_ms": phases["leaf_combine"]}
     divide_bytes = 2 * (n * n * 4) + plan.workspace_bytes  # read A, B; write every leaf operand (hi+lo)
 
+    plan_tmp_holder = []
     comparators = None
     if not args.no_comparators and rank == 0:
         comparators = {}
@@ -318,6 +434,13 @@ def main():
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
 
+    batch = serve = None
+    if rank == 0 and not args.no_batch:
+        del plan_tmp_holder[:]
+        batch = run_batch(args, stark, synth, torch)
+    if rank == 0 and not args.no_serve:
+        serve = run_serve(args, stark, synth, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, args.seed)
@@ -335,7 +458,8 @@ def main():
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
-               "error_vs_fp64": error, "comparators": comparators, "cpu_baseline": cpu}
+               "error_vs_fp64": error, "comparators": comparators, "batch": batch, "serve": serve,
+               "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     plan.close()
     if dist is not None:

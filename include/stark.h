@@ -151,6 +151,92 @@ STARK_API stark_status stark_plan_check(stark_plan_t plan, void *stream);
 STARK_API stark_status stark_plan_set_timing(stark_plan_t plan, int records);
 STARK_API stark_status stark_plan_phase_ms(stark_plan_t plan, float out_ms[3]);
 
+/* ----------------------------------------------------------------- batches */
+
+typedef struct stark_batch_s *stark_batch_t;
+
+/* A batch of `count` independent products C_i = A_i * B_i of sizes n[i] (any
+ * mix), one tensor-core dtype (F32_SPLIT_BF16 or F32_SPLIT_TF32).  Every leaf
+ * product of every member (Alg. 4) is a work item of ONE persistent grouped
+ * leaf launch, whose epilogue combines (Alg. 5) into each member's own C;
+ * the member divides (Alg. 3) precede it.  The launch sequence is recorded
+ * in a CUDA graph on first use and replayed while the pointers stay the
+ * same.  depth = -1: each member's depth is chosen by the autotuner, which
+ * times the candidate depths on the device (cached per (n, dtype) for the
+ * process); the leaf tile width is 256 when every member allows it, else
+ * 128.  Allocates every member's workspace.
+ * Errors: EINVAL (count <= 0 or > 4096, n[i] <= 0, depth out of range),
+ * EUNSUPPORTED (other dtypes, not a GB300), ENOMEM, ECUDA. */
+STARK_API stark_status stark_batch_create(int32_t count, const int64_t *n, int depth, stark_dtype dtype,
+                                          stark_batch_t *out);
+
+/* Waits for the device, then frees everything the batch owns.  NULL is ignored. */
+STARK_API stark_status stark_batch_destroy(stark_batch_t batch);
+
+/* C[i] = A[i] * B[i] for every member.  A, B, C: host arrays of `count`
+ * device pointers (member i is n[i] x n[i], row-major fp32).  Asynchronous
+ * on `stream` (one graph launch); when any pointer differs from the previous
+ * call the graph is re-recorded first, which waits for the device. */
+STARK_API stark_status stark_batch_mul(stark_batch_t batch, const void *const *A, const void *const *B,
+                                       void *const *C, void *stream);
+
+/* Depth chosen for member `index`. */
+STARK_API stark_status stark_batch_depth(stark_batch_t batch, int32_t index, int32_t *depth);
+
+/* Leaf tile width, number of grouped work items, device workspace bytes,
+ * and graph replays so far (any pointer may be NULL). */
+STARK_API stark_status stark_batch_info(stark_batch_t batch, int32_t *tile_n, int64_t *work_items,
+                                        int64_t *workspace_bytes, int64_t *graph_replays);
+
+/* Synchronise `stream` and report a device-side timeout of the batch's
+ * kernels (STARK_ETIMEOUT), clearing it. */
+STARK_API stark_status stark_batch_check(stark_batch_t batch, void *stream);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct stark_server_s *stark_server_t;
+
+/* Continuous-batching request server on the current device (the serving
+ * form of the benchmark spec; the paper has no serving layer).  One dispatcher
+ * thread admits queued requests in arrival order while a stream slot is free
+ * and their workspace fits `hbm_budget_bytes` (device bytes the server may
+ * own for workspaces; idle workspaces are evicted least recently used first
+ * to make room).  Each free slot takes a micro-batch of up to 16 admitted
+ * requests and runs their divides plus ONE grouped leaf launch (as
+ * stark_batch_mul), so requests arriving while others run overlap with them
+ * on the device.  Workspaces are cached per padded size and stay resident.
+ * Thread-safe.  Errors: EINVAL (budget 0, slots outside 1..64),
+ * EUNSUPPORTED, ENOMEM. */
+STARK_API stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_server_t *out);
+
+/* Queue C = A*B (device pointers, n x n row-major, element type of dtype)
+ * and return its id at once.  A, B, C must stay valid and unmodified until
+ * stark_poll reports the request done.  ENOMEM: the request alone does not
+ * fit the budget (it could never be admitted); EINVAL: bad arguments. */
+STARK_API stark_status stark_submit(stark_server_t server, int64_t n, stark_dtype dtype, const void *A,
+                                    const void *B, void *C, uint64_t *req_id);
+
+/* Non-blocking: *done = 1 once the request finished (its status in
+ * *req_status, if not NULL), else 0.  The poll that reports a request done
+ * reaps it; later polls of that id return ENOTFOUND, as do unknown ids. */
+STARK_API stark_status stark_poll(stark_server_t server, uint64_t req_id, int *done, stark_status *req_status);
+
+/* Blocks until every submitted request finished (reaped or not). */
+STARK_API stark_status stark_server_drain(stark_server_t server);
+
+/* Latency of a finished request, in seconds from stark_submit until the
+ * dispatcher observed its completion event.  EBUSY while it is pending,
+ * ENOTFOUND for an unknown id. */
+STARK_API stark_status stark_request_latency(stark_server_t server, uint64_t req_id, double *seconds);
+
+/* Cached workspaces, device bytes they own, and requests waiting (any
+ * pointer may be NULL). */
+STARK_API stark_status stark_server_stats(stark_server_t server, int64_t *cached_workspaces, int64_t *owned_bytes,
+                                          int64_t *queued);
+
+/* Drains, stops the dispatcher and frees everything the server owns. */
+STARK_API stark_status stark_server_destroy(stark_server_t server);
+
 /* ----------------------------------------------------------------- no allocation */
 
 /* Size of the fixed device scratch array behind stark_mul_noalloc. */

@@ -1,0 +1,325 @@
+// batch.cu -- many independent products in one grouped, graph-captured pass.
+//
+// Each member keeps its own plan (operand planes, C-target table, operand
+// tensor maps).  One stark_batch_mul enqueues, for every member, the zeroing
+// of C and the divide of A and B, then ONE persistent grouped leaf launch
+// whose work items are all (member, leaf, tile) triples: the 7^d leaf
+// products of every member share the GPU in a single launch, and each
+// item's epilogue combines into its own member's C.  The whole sequence is
+// captured once in a CUDA graph and replayed while the pointers are
+// unchanged.
+//
+// Depth per member: given, or chosen by the autotuner, which times the
+// candidate depths on the device (one warm-up and three timed products per
+// candidate on scratch inputs) and caches the winner per (n, dtype) for the
+// process.  The leaf tile width of the grouped launch is 256 when every
+// member's leaf side allows it, else 128.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "plan.h"
+#include "stark_internal.h"
+
+namespace stark {
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::pair<int64_t, int>, int> g_tuned;  // (n, dtype) -> depth
+
+// Device time (ms) of one product of side n at `depth`, averaged over 3.
+float time_depth(int64_t n, int depth, stark_dtype dt, void* A, void* B, void* C, cudaStream_t s) {
+  stark_plan_s p;
+  if (plan_init(&p, n, depth, dt) != STARK_OK) {
+    plan_release(&p);
+    return -1.f;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = -1.f;
+  if (plan_run(&p, A, B, C, 0, p.P, s) == STARK_OK) {
+    cudaEventRecord(e0, s);
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) ok = plan_run(&p, A, B, C, 0, p.P, s) == STARK_OK;
+    cudaEventRecord(e1, s);
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= 3;
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan_release(&p);
+  cudaGetLastError();
+  return ms;
+}
+
+}  // namespace
+
+// Measured depth choice for n x n products (cached per process).
+int autotune_depth(int64_t n, stark_dtype dt) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find({n, (int)dt});
+    if (it != g_tuned.end()) return it->second;
+  }
+  int best = choose_depth(n, dt);
+  const size_t bytes = (size_t)n * n * element_size(dt);
+  void *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaStream_t s = nullptr;
+  if (n > 0 && cudaMalloc(&A, bytes) == cudaSuccess && cudaMalloc(&B, bytes) == cudaSuccess &&
+      cudaMalloc(&C, bytes) == cudaSuccess && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) {
+    cudaMemsetAsync(A, 0x3c, bytes, s);  // bounded, nonzero values
+    cudaMemsetAsync(B, 0x3c, bytes, s);
+    float best_ms = 1e30f;
+    for (int d = 0; d <= 3; ++d) {
+      if ((padded_side(n, d, dt) >> d) < tile_granularity(dt)) continue;
+      if (d > 0 && (n >> d) < 128) break;
+      const float ms = time_depth(n, d, dt, A, B, C, s);
+      if (ms > 0 && ms < best_ms) {
+        best_ms = ms;
+        best = d;
+      }
+    }
+  }
+  if (s) cudaStreamDestroy(s);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[{n, (int)dt}] = best;
+  return best;
+}
+
+}  // namespace stark
+
+struct stark_batch_s {
+  stark_dtype dt = STARK_F32_SPLIT_BF16;
+  int bn = 128;
+  std::vector<stark_plan_s*> plans;
+  std::vector<stark::GroupDesc> host_desc;
+  stark::GroupDesc* d_desc = nullptr;
+  int total_items = 0;
+  int* d_err = nullptr;
+  cudaStream_t cap = nullptr;  // private capture stream
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> caller_index;  // caller's index of each (size-sorted) member
+  std::vector<const void*> last;  // pointers the graph was captured with
+  int64_t replays = 0;
+};
+
+using namespace stark;
+
+static void batch_free(stark_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto* p : b->plans) {
+    plan_release(p);
+    delete p;
+  }
+  cudaFree(b->d_desc);
+  cudaFree(b->d_err);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaGetLastError();
+  delete b;
+}
+
+extern "C" {
+
+stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, stark_dtype dt, stark_batch_t* out) {
+  if (!out || !n || count <= 0 || count > 4096 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;
+  *out = nullptr;
+  if (dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32) return STARK_EUNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (n[i] <= 0 || n[i] > (int64_t)1 << 20) return STARK_EINVAL;
+  if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
+  auto* b = new (std::nothrow) stark_batch_s();
+  if (!b) return STARK_ENOMEM;
+  b->dt = dt;
+  stark_status st = STARK_OK;
+  // members in order of decreasing size so the big tiles start first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  b->plans.assign(count, nullptr);
+  for (int i = 0; i < count && st == STARK_OK; ++i) {
+    const int d = depth >= 0 ? depth : autotune_depth(n[i], dt);
+    auto* p = new (std::nothrow) stark_plan_s();
+    if (!p) {
+      st = STARK_ENOMEM;
+      break;
+    }
+    b->plans[i] = p;
+    st = plan_init(p, n[i], d, dt);
+  }
+  if (st != STARK_OK) {
+    batch_free(b);
+    return st;
+  }
+  b->bn = 256;
+  for (auto* p : b->plans)
+    if (p->L % 256 != 0) b->bn = 128;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return b->plans[x]->n > b->plans[y]->n; });
+  // descriptors: work items of member order[0] first
+  b->host_desc.resize(count);
+  int64_t items = 0;
+  for (int k = 0; k < count; ++k) {
+    stark_plan_s* p = b->plans[order[k]];
+    GroupDesc& g = b->host_desc[k];
+    std::memset(&g, 0, sizeof(g));
+    g.tmA = p->tmA;
+    if (dt == STARK_F32_SPLIT_TF32) {
+      if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, b->bn)) st = STARK_EUNSUPPORTED;
+    } else {
+      g.tmB = p->tmB;
+    }
+    g.item_base = (int32_t)items;
+    g.P = (int32_t)p->P;
+    g.L = (int32_t)p->L;
+    g.ctab = p->d_ctab;
+    g.ccount = p->d_ccount;
+    g.maxT = p->maxT;
+    g.n = p->n;
+    items += p->P * (p->L / 128) * (p->L / b->bn);
+  }
+  if (items > 0x7FFFFFFF) st = STARK_EINVAL;
+  b->total_items = (int)items;
+  // keep the member order used by the descriptors
+  std::vector<stark_plan_s*> sorted(count);
+  for (int k = 0; k < count; ++k) sorted[k] = b->plans[order[k]];
+  b->last.clear();
+  if (st == STARK_OK && (cudaMalloc(&b->d_desc, sizeof(GroupDesc) * count) != cudaSuccess ||
+                         cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess ||
+                         cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess))
+    st = STARK_ENOMEM;
+  if (st != STARK_OK) {
+    batch_free(b);
+    return st;
+  }
+  // members are kept in the descriptor order; remember the caller's index
+  b->plans = sorted;
+  b->caller_index = order;
+  *out = b;
+  return STARK_OK;
+}
+
+stark_status stark_batch_destroy(stark_batch_t b) {
+  if (!b) return STARK_OK;
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return STARK_OK;
+}
+
+stark_status stark_batch_depth(stark_batch_t b, int32_t index, int32_t* depth) {
+  if (!b || !depth || index < 0 || index >= (int32_t)b->plans.size()) return STARK_EINVAL;
+  for (size_t k = 0; k < b->plans.size(); ++k)
+    if (b->caller_index[k] == index) {
+      *depth = b->plans[k]->depth;
+      return STARK_OK;
+    }
+  return STARK_EINVAL;
+}
+
+stark_status stark_batch_info(stark_batch_t b, int32_t* tile_n, int64_t* work_items, int64_t* workspace_bytes,
+                              int64_t* graph_replays) {
+  if (!b) return STARK_EINVAL;
+  if (tile_n) *tile_n = b->bn;
+  if (work_items) *work_items = b->total_items;
+  if (workspace_bytes) {
+    int64_t w = 0;
+    for (auto* p : b->plans) w += p->ws_bytes;
+    *workspace_bytes = w;
+  }
+  if (graph_replays) *graph_replays = b->replays;
+  return STARK_OK;
+}
+
+stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* const* B, void* const* C,
+                             void* stream) {
+  if (!b || !A || !B || !C) return STARK_EINVAL;
+  const int count = (int)b->plans.size();
+  std::vector<const void*> ptrs((size_t)count * 3);
+  for (int k = 0; k < count; ++k) {
+    const int i = b->caller_index[k];
+    if (!A[i] || !B[i] || !C[i]) return STARK_EINVAL;
+    ptrs[3 * k] = A[i];
+    ptrs[3 * k + 1] = B[i];
+    ptrs[3 * k + 2] = C[i];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ptrs != b->last || !b->exec) {
+    // new pointers: refresh the C maps and re-record the graph (the device
+    // descriptors may be read by a replay still in flight, so wait first)
+    if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
+    for (int k = 0; k < count; ++k) {
+      GroupDesc& g = b->host_desc[k];
+      g.C = static_cast<float*>(const_cast<void*>(ptrs[3 * k + 2]));
+      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n) ? 1 : 0;
+    }
+    if (cudaMemcpy(b->d_desc, b->host_desc.data(), sizeof(GroupDesc) * count, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return STARK_ECUDA;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return STARK_ECUDA;
+    stark_status st = STARK_OK;
+    for (int k = 0; k < count && st == STARK_OK; ++k) {
+      stark_plan_s* p = b->plans[k];
+      if (cudaMemsetAsync(const_cast<void*>(ptrs[3 * k + 2]), 0, (size_t)p->n * p->n * p->esz, b->cap) !=
+          cudaSuccess)
+        st = STARK_ECUDA;
+      else
+        st = plan_divide(p, ptrs[3 * k], ptrs[3 * k + 1], b->cap);
+    }
+    if (st == STARK_OK) {
+      LeafTcArgs a{};
+      a.err = b->d_err;
+      a.timeout_ns = kDefaultTimeoutNs;
+      a.groups = b->d_desc;
+      a.ngroups = count;
+      a.total_items = b->total_items;
+      if (launch_leaf_tc_grouped(a, b->dt == STARK_F32_SPLIT_TF32, b->bn, device_sm_count(), b->cap) !=
+          cudaSuccess)
+        st = STARK_ECUDA;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+    if (st != STARK_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != STARK_OK ? st : STARK_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      b->exec = nullptr;
+      cudaGetLastError();
+      return STARK_ECUDA;
+    }
+    b->last = ptrs;
+  }
+  if (cudaGraphLaunch(b->exec, s) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ECUDA;
+  }
+  ++b->replays;
+  return STARK_OK;
+}
+
+stark_status stark_batch_check(stark_batch_t b, void* stream) {
+  if (!b) return STARK_EINVAL;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STARK_ECUDA;
+  if (e != 0) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return STARK_ETIMEOUT;
+  }
+  return STARK_OK;
+}
+
+}  // extern "C"

@@ -22,6 +22,8 @@
 //               into C for every target of the leaf
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // drains its in-flight copies and MMAs, frees TMEM and returns.
+#include <cstring>
+
 #include "ptx.cuh"
 #include "stark_internal.h"
 
@@ -53,7 +55,72 @@ struct TcCfg {
   static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, B_MN>();
 };
 
-template <int BN, int STAGES, bool TF32>
+// Everything one work item (a BM x BN tile of one leaf product) needs.
+struct ItemInfo {
+  const CUtensorMap* tA;
+  const CUtensorMap* tB;
+  const CUtensorMap* tC;
+  int leaf, P, m0, n0, kblocks;
+  const CTarget* tg;
+  int nt;
+  float* C;
+  int64_t n, ldc;
+  int use_tma_c;
+};
+
+template <int BN, int BK, bool GROUPED>
+__device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, const CUtensorMap* tmA,
+                                                const CUtensorMap* tmB, const CUtensorMap* tmC) {
+  ItemInfo it;
+  if constexpr (GROUPED) {
+    // member owning this item: the last one whose item_base <= item
+    int lo = 0, hi = p.ngroups - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.groups[mid].item_base <= item) lo = mid; else hi = mid - 1;
+    }
+    const GroupDesc* g = p.groups + lo;
+    const int L = g->L;
+    const int tiles_n = L / BN;
+    const int per_leaf = (L / kBM) * tiles_n;
+    const int rem = item - g->item_base;
+    it.tA = &g->tmA;
+    it.tB = &g->tmB;
+    it.tC = &g->tmC;
+    it.leaf = rem / per_leaf;
+    it.P = g->P;
+    it.m0 = ((rem % per_leaf) / tiles_n) * kBM;
+    it.n0 = ((rem % per_leaf) % tiles_n) * BN;
+    it.kblocks = L / BK;
+    it.tg = g->ctab + (int64_t)it.leaf * g->maxT;
+    it.nt = g->ccount[it.leaf];
+    it.C = g->C;
+    it.n = g->n;
+    it.ldc = g->n;
+    it.use_tma_c = g->use_tma_c;
+  } else {
+    const int tiles_n = p.L / BN;
+    const int per_leaf = (p.L / kBM) * tiles_n;
+    const int rem = item % per_leaf;
+    it.tA = tmA;
+    it.tB = tmB;
+    it.tC = tmC;
+    it.leaf = p.leaf_begin + item / per_leaf;
+    it.P = p.P;
+    it.m0 = (rem / tiles_n) * kBM;
+    it.n0 = (rem % tiles_n) * BN;
+    it.kblocks = p.L / BK;
+    it.tg = p.ctab + (int64_t)it.leaf * p.maxT;
+    it.nt = p.ccount[it.leaf];
+    it.C = p.C;
+    it.n = p.n;
+    it.ldc = p.ldc;
+    it.use_tma_c = p.use_tma_c;
+  }
+  return it;
+}
+
+template <int BN, int STAGES, bool TF32, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
@@ -75,11 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
 
-  const int tiles_m = p.L / kBM;
-  const int tiles_n = p.L / BN;
-  const int per_leaf = tiles_m * tiles_n;
-  const int num_items = (p.leaf_end - p.leaf_begin) * per_leaf;
-  const int kblocks = p.L / Cfg::BK;
+  const int num_items = GROUPED ? p.total_items : (p.leaf_end - p.leaf_begin) * (p.L / kBM) * (p.L / BN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -91,9 +154,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(acce_bar(a), 128);
     }
     fence_mbar_init();
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    if (p.use_tma_c) prefetch_tmap(&tmC);
+    if (!GROUPED) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      if (p.use_tma_c) prefetch_tmap(&tmC);
+    }
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
@@ -113,11 +178,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t armed = 0, armed_phase = 0;  // per-stage: ever armed / parity of last arming
       bool ok = true;
       for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
-        const int leaf = p.leaf_begin + item / per_leaf;
-        const int rem = item % per_leaf;
-        const int m0 = (rem / tiles_n) * kBM;
-        const int n0 = (rem % tiles_n) * BN;
-        for (int kb = 0; kb < kblocks; ++kb) {
+        const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC);
+        const int leaf = it.leaf, m0 = it.m0, n0 = it.n0;
+        for (int kb = 0; kb < it.kblocks; ++kb) {
           if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) {
             ok = false;
             break;
@@ -125,19 +188,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
           mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
           const int k0 = kb * Cfg::BK;
-          tma_load_3d(st, &tmA, k0, m0, leaf, full_bar(s), pol);
-          tma_load_3d(st + Cfg::A_BYTES, &tmA, k0, m0, p.P + leaf, full_bar(s), pol);
+          tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol);
+          tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol);
           if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
-              tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
+              tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
                           pol);
-              tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, &tmB, n0 + c * Cfg::W, k0,
-                          p.P + leaf, full_bar(s), pol);
+              tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
+                          it.P + leaf, full_bar(s), pol);
             }
           } else {
-            tma_load_3d(st + 2 * Cfg::A_BYTES, &tmB, k0, n0, leaf, full_bar(s), pol);
-            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB, k0, n0, p.P + leaf, full_bar(s), pol);
+            tma_load_3d(st + 2 * Cfg::A_BYTES, it.tB, k0, n0, leaf, full_bar(s), pol);
+            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, n0, it.P + leaf, full_bar(s), pol);
           }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
@@ -163,6 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       bool issued = false;
       for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
+        const int kblocks = GROUPED ? decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC).kblocks
+                                    : p.L / Cfg::BK;
         if (!mbar_wait_bounded(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
           ok = false;
           break;
@@ -238,21 +303,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int item = blockIdx.x; item < num_items; item += gridDim.x) {
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
-      const int leaf = p.leaf_begin + item / per_leaf;
-      const int rem = item % per_leaf;
-      const int m0 = (rem / tiles_n) * kBM;
-      const int n0 = (rem % tiles_n) * BN;
-      const int nt = p.ccount[leaf];
-      const CTarget* tg = p.ctab + (int64_t)leaf * p.maxT;
+      const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC);
+      const int m0 = it.m0, n0 = it.n0, nt = it.nt;
+      const CTarget* tg = it.tg;
       bool has_pos = false, has_neg = false;
       for (int t = 0; t < nt; ++t) (tg[t].sign > 0 ? has_pos : has_neg) = true;
-      const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) && ((p.ldc & 3) == 0);
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(it.C) & 15) == 0) && ((it.ldc & 3) == 0);
 #pragma unroll 1
       for (int chunk = 0; chunk < BN / 32; ++chunk) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + chunk * 32), r);
         tmem_ld_wait();
-        if (p.use_tma_c) {
+        if (it.use_tma_c) {
           if (lane == 0) bulk_wait_group_read<0>();  // the previous boxes have been read
           __syncwarp();
 #pragma unroll
@@ -277,8 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const CTarget c = tg[t];
               const int64_t y = (int64_t)c.row_off + m0 + quarter * 32;
               const int64_t x = (int64_t)c.col_off + n0 + chunk * 32;
-              if (y >= p.n || x >= p.n) continue;
-              tma_reduce_add_2d(&tmC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u));
+              if (y >= it.n || x >= it.n) continue;
+              tma_reduce_add_2d(it.tC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u));
             }
             bulk_commit_group();
           }
@@ -288,10 +350,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const CTarget c = tg[t];
             const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
             const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
-            if (grow >= p.n || gcol >= p.n) continue;
-            float* dst = p.C + grow * p.ldc + gcol;
+            if (grow >= it.n || gcol >= it.n) continue;
+            float* dst = it.C + grow * it.ldc + gcol;
             const float sg = (float)c.sign;
-            if (vec_ok && gcol + 32 <= p.n) {
+            if (vec_ok && gcol + 32 <= it.n) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
@@ -299,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
               }
             } else {
-              const int64_t lim = p.n - gcol;
+              const int64_t lim = it.n - gcol;
 #pragma unroll
               for (int j = 0; j < 32; ++j)
                 if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
@@ -315,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     // every bulk reduction issued by this warp completes before the CTA exits
-    if (p.use_tma_c && lane == 0) bulk_wait_group<0>();
+    if (lane == 0) bulk_wait_group<0>();
   }
 
   tc_fence_before();
@@ -324,16 +386,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
 }
 
-template <int BN, int STAGES, bool TF32>
+template <int BN, int STAGES, bool TF32, bool GROUPED>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
   static_assert(Cfg::B_BYTES == BN * 128, "B tile size");
-  if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32>;
+  int64_t items;
+  if constexpr (GROUPED) {
+    items = a.total_items;
+    if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
+  } else {
+    if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
+    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM) * (a.L / BN);
+  }
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  const int64_t items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM) * (a.L / BN);
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
   const int grid = (int)(items < num_sms ? items : num_sms);
@@ -352,12 +420,26 @@ int leaf_tc_smem_bytes(bool tf32, int bn) {
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
   if (bn == 256) {
-    return tf32 ? launch_cfg<256, 2, true>(a, tmA, tmB, tmC, num_sms, st)
-                : launch_cfg<256, 2, false>(a, tmA, tmB, tmC, num_sms, st);
+    return tf32 ? launch_cfg<256, 2, true, false>(a, tmA, tmB, tmC, num_sms, st)
+                : launch_cfg<256, 2, false, false>(a, tmA, tmB, tmC, num_sms, st);
   }
   if (bn == 128) {
-    return tf32 ? launch_cfg<128, 3, true>(a, tmA, tmB, tmC, num_sms, st)
-                : launch_cfg<128, 3, false>(a, tmA, tmB, tmC, num_sms, st);
+    return tf32 ? launch_cfg<128, 3, true, false>(a, tmA, tmB, tmC, num_sms, st)
+                : launch_cfg<128, 3, false, false>(a, tmA, tmB, tmC, num_sms, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t st) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  if (bn == 256) {
+    return tf32 ? launch_cfg<256, 2, true, true>(a, &none, &none, &none, num_sms, st)
+                : launch_cfg<256, 2, false, true>(a, &none, &none, &none, num_sms, st);
+  }
+  if (bn == 128) {
+    return tf32 ? launch_cfg<128, 3, true, true>(a, &none, &none, &none, num_sms, st)
+                : launch_cfg<128, 3, false, true>(a, &none, &none, &none, num_sms, st);
   }
   return cudaErrorInvalidValue;
 }

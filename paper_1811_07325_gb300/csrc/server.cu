@@ -1,0 +1,449 @@
+// server.cu -- continuous-batching request server (stark_server_*).
+//
+// Requests (C = A*B on device pointers, any n) are queued by stark_submit
+// and served by one dispatcher thread:
+//   * admission in arrival order: the head request is admitted when a
+//     workspace for its (n_pad, depth, dtype) bucket is idle in the cache, or
+//     a new one fits the device-memory budget (idle workspaces of other
+//     buckets are evicted, least recently used first, to make room);
+//   * every free stream slot takes a micro-batch of the admitted requests:
+//     their C zeroing and divides, then ONE grouped leaf launch over all
+//     their leaf products (the same kernel as stark_batch_mul), then an
+//     event; requests that arrive while others run are admitted as slots and
+//     memory free up, so their work overlaps on the device;
+//   * completion is observed by polling the slot events; the request's
+//     latency runs from stark_submit to that observation.
+// Workspaces are plans keyed by padded size, so one workspace serves every
+// n that pads to the same n_pad; they stay resident until evicted.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.h"
+#include "stark_internal.h"
+
+namespace stark {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr int kMaxMicroBatch = 16;
+
+struct Request {
+  uint64_t id;
+  int64_t n;
+  stark_dtype dt;
+  const void* A;
+  const void* B;
+  void* C;
+  Clock::time_point t_submit;
+  stark_plan_s* ws = nullptr;  // workspace while running
+  stark_status status = STARK_OK;
+};
+
+struct Workspace {
+  stark_plan_s* plan;
+  bool busy;
+  Clock::time_point last_used;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  GroupDesc* d_desc = nullptr;  // device descriptors of the running micro-batch
+  GroupDesc* h_desc = nullptr;  // pinned host staging
+  std::vector<Request*> running;
+};
+
+}  // namespace
+}  // namespace stark
+
+struct stark_server_s {
+  int device = 0;
+  size_t budget = 0;
+  size_t owned = 0;  // bytes of all cached workspaces
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<stark::Request*> queue;
+  std::unordered_map<uint64_t, stark::Request*> live;  // queued or running
+  std::unordered_map<uint64_t, std::pair<stark_status, double>> finished;  // not yet reaped
+  std::unordered_map<uint64_t, double> latency;                          // every finished request
+  std::map<std::tuple<int64_t, int, int>, std::vector<stark::Workspace>> cache;  // (npad, depth, dt)
+  std::vector<stark::Slot> slots;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  int* d_err = nullptr;
+  int num_sms = 1;
+};
+
+using namespace stark;
+
+namespace {
+
+int depth_for(int64_t n, stark_dtype dt) { return choose_depth(n, dt); }
+
+// Find or make an idle workspace for request r (server mutex held).
+stark_plan_s* acquire_workspace(stark_server_s* s, const Request& r, stark_status* err) {
+  const int d = depth_for(r.n, r.dt);
+  const int64_t npad = padded_side(r.n, d, r.dt);
+  auto key = std::make_tuple(npad, d, (int)r.dt);
+  auto& pool = s->cache[key];
+  for (auto& w : pool)
+    if (!w.busy) {
+      w.busy = true;
+      w.last_used = Clock::now();
+      return w.plan;
+    }
+  // a new workspace: how big, and does it fit once idle ones are evicted?
+  const size_t need = (size_t)operand_bytes(npad, d, r.dt) + (1u << 20);
+  while (s->owned + need > s->budget) {
+    // evict the least recently used idle workspace of any bucket
+    Workspace* victim = nullptr;
+    std::vector<Workspace>* vpool = nullptr;
+    for (auto& kv : s->cache)
+      for (auto& w : kv.second)
+        if (!w.busy && (!victim || w.last_used < victim->last_used)) {
+          victim = &w;
+          vpool = &kv.second;
+        }
+    if (!victim) {
+      *err = STARK_EBUSY;  // wait for running requests to free memory
+      return nullptr;
+    }
+    s->owned -= (size_t)victim->plan->ws_bytes;
+    plan_release(victim->plan);
+    delete victim->plan;
+    vpool->erase(vpool->begin() + (victim - vpool->data()));
+  }
+  auto* p = new (std::nothrow) stark_plan_s();
+  if (!p) {
+    *err = STARK_ENOMEM;
+    return nullptr;
+  }
+  stark_status st = plan_init(p, npad, d, r.dt);  // sized for the whole bucket
+  if (st != STARK_OK) {
+    plan_release(p);
+    delete p;
+    *err = st;
+    return nullptr;
+  }
+  s->owned += (size_t)p->ws_bytes;
+  s->cache[key].push_back(Workspace{p, true, Clock::now()});
+  return p;
+}
+
+void release_workspace(stark_server_s* s, stark_plan_s* p) {
+  for (auto& kv : s->cache)
+    for (auto& w : kv.second)
+      if (w.plan == p) {
+        w.busy = false;
+        w.last_used = Clock::now();
+        return;
+      }
+}
+
+void finish(stark_server_s* s, Request* r, stark_status st) {
+  const double lat = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
+  s->finished[r->id] = {st, lat};
+  s->latency[r->id] = lat;
+  s->live.erase(r->id);
+  if (r->ws) release_workspace(s, r->ws);
+  delete r;
+}
+
+// Enqueue one micro-batch on a slot (server mutex held).
+stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Request*>& reqs) {
+  cudaStream_t st = slot.stream;
+  std::vector<Request*> tc;
+  for (Request* r : reqs) {
+    stark_plan_s view = *r->ws;  // the bucket workspace, bounds of this request
+    view.n = r->n;
+    view.ev.clear();
+    view.timing_cap = 0;
+    stark_status e;
+    if (r->dt == STARK_F32_SPLIT_BF16 || r->dt == STARK_F32_SPLIT_TF32) {
+      if (cudaMemsetAsync(r->C, 0, (size_t)r->n * r->n * view.esz, st) != cudaSuccess) return STARK_ECUDA;
+      e = plan_divide(&view, r->A, r->B, st);
+      tc.push_back(r);
+    } else {
+      e = plan_run(&view, r->A, r->B, r->C, 0, view.P, st);
+    }
+    if (e != STARK_OK) return e;
+  }
+  if (!tc.empty()) {
+    int bn = 256;
+    for (Request* r : tc)
+      if (r->ws->L % 256 != 0) bn = 128;
+    int64_t items = 0;
+    const bool tf32 = tc[0]->dt == STARK_F32_SPLIT_TF32;
+    for (size_t k = 0; k < tc.size(); ++k) {
+      stark_plan_s* p = tc[k]->ws;
+      GroupDesc& g = slot.h_desc[k];
+      std::memset(&g, 0, sizeof(g));
+      g.tmA = p->tmA;
+      if (tf32) {
+        if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn)) return STARK_EUNSUPPORTED;
+      } else {
+        g.tmB = p->tmB;
+      }
+      g.item_base = (int32_t)items;
+      g.P = (int32_t)p->P;
+      g.L = (int32_t)p->L;
+      g.ctab = p->d_ctab;
+      g.ccount = p->d_ccount;
+      g.maxT = p->maxT;
+      g.C = static_cast<float*>(tc[k]->C);
+      g.n = tc[k]->n;
+      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n) ? 1 : 0;
+      items += p->P * (p->L / 128) * (p->L / bn);
+    }
+    if (cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(GroupDesc) * tc.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return STARK_ECUDA;
+    LeafTcArgs a{};
+    a.err = s->d_err;
+    a.timeout_ns = kDefaultTimeoutNs;
+    a.groups = slot.d_desc;
+    a.ngroups = (int32_t)tc.size();
+    a.total_items = (int32_t)items;
+    if (launch_leaf_tc_grouped(a, tf32, bn, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+  }
+  if (cudaEventRecord(slot.done, st) != cudaSuccess) return STARK_ECUDA;
+  return STARK_OK;
+}
+
+void worker_loop(stark_server_s* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // 1. completions
+    bool any_running = false;
+    for (Slot& slot : s->slots) {
+      if (slot.running.empty()) continue;
+      const cudaError_t q = cudaEventQuery(slot.done);
+      if (q == cudaErrorNotReady) {
+        any_running = true;
+        continue;
+      }
+      stark_status st = q == cudaSuccess ? STARK_OK : STARK_ECUDA;
+      int e = 0;
+      if (st == STARK_OK && cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && e) {
+        st = STARK_ETIMEOUT;
+        cudaMemset(s->d_err, 0, sizeof(int));
+      }
+      cudaGetLastError();
+      for (Request* r : slot.running) finish(s, r, st);
+      slot.running.clear();
+    }
+    if (s->stop && s->queue.empty() && !any_running) {
+      bool idle = true;
+      for (Slot& slot : s->slots) idle = idle && slot.running.empty();
+      if (idle) break;
+    }
+    // 2. admission into free slots, arrival order
+    for (Slot& slot : s->slots) {
+      if (!slot.running.empty() || s->queue.empty()) continue;
+      std::vector<Request*> batch;
+      while (!s->queue.empty() && (int)batch.size() < kMaxMicroBatch) {
+        Request* r = s->queue.front();
+        if (!batch.empty() && (r->dt != batch[0]->dt)) break;  // one dtype per grouped launch
+        stark_status err = STARK_OK;
+        r->ws = acquire_workspace(s, *r, &err);
+        if (!r->ws) {
+          if (err == STARK_EBUSY) {
+            bool running = false;
+            for (Slot& o : s->slots) running = running || !o.running.empty();
+            if (running || !batch.empty()) break;  // memory frees up when those finish
+            err = STARK_ENOMEM;                    // cannot ever fit
+          }
+          s->queue.pop_front();
+          finish(s, r, err);
+          continue;
+        }
+        s->queue.pop_front();
+        batch.push_back(r);
+      }
+      if (batch.empty()) continue;
+      const stark_status st = launch_micro_batch(s, slot, batch);
+      if (st != STARK_OK) {
+        cudaStreamSynchronize(slot.stream);
+        cudaGetLastError();
+        for (Request* r : batch) finish(s, r, st);
+      } else {
+        slot.running = batch;
+        any_running = true;
+      }
+    }
+    // 3. wait: briefly while work runs (poll events), else for a submission
+    if (any_running) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    } else if (!s->stop && s->queue.empty()) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(50));
+    } else if (!s->queue.empty()) {
+      // queued but not admissible right now and nothing runs: retry shortly
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+      lk.lock();
+    }
+  }
+}
+
+void server_free(stark_server_s* s) {
+  for (auto& kv : s->cache)
+    for (auto& w : kv.second) {
+      plan_release(w.plan);
+      delete w.plan;
+    }
+  for (Slot& slot : s->slots) {
+    if (slot.stream) cudaStreamDestroy(slot.stream);
+    if (slot.done) cudaEventDestroy(slot.done);
+    cudaFree(slot.d_desc);
+    cudaFreeHost(slot.h_desc);
+  }
+  for (auto& kv : s->live) delete kv.second;
+  cudaFree(s->d_err);
+  cudaGetLastError();
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_server_t* out) {
+  if (!out || hbm_budget_bytes == 0 || slots <= 0 || slots > 64) return STARK_EINVAL;
+  *out = nullptr;
+  if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
+  auto* s = new (std::nothrow) stark_server_s();
+  if (!s) return STARK_ENOMEM;
+  cudaGetDevice(&s->device);
+  s->budget = hbm_budget_bytes;
+  s->num_sms = device_sm_count();
+  s->slots.resize((size_t)slots);
+  bool ok = cudaMalloc(&s->d_err, sizeof(int)) == cudaSuccess && cudaMemset(s->d_err, 0, sizeof(int)) == cudaSuccess;
+  for (Slot& slot : s->slots) {
+    ok = ok && cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&slot.d_desc, sizeof(GroupDesc) * kMaxMicroBatch) == cudaSuccess;
+    ok = ok && cudaMallocHost(&slot.h_desc, sizeof(GroupDesc) * kMaxMicroBatch) == cudaSuccess;
+  }
+  if (!ok) {
+    server_free(s);
+    return STARK_ENOMEM;
+  }
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return STARK_OK;
+}
+
+stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const void* A, const void* B, void* C,
+                          uint64_t* req_id) {
+  if (!s || !req_id || n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
+  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
+    return STARK_EINVAL;
+  if (n > 0 && (!A || !B || !C)) return STARK_EINVAL;
+  const int d = choose_depth(n, dt);
+  if ((size_t)operand_bytes(padded_side(n, d, dt), d, dt) + (1u << 20) > s->budget) return STARK_ENOMEM;
+  auto* r = new (std::nothrow) Request();
+  if (!r) return STARK_ENOMEM;
+  r->n = n;
+  r->dt = dt;
+  r->A = A;
+  r->B = B;
+  r->C = C;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      delete r;
+      return STARK_EINVAL;
+    }
+    r->id = s->next_id++;
+    *req_id = r->id;
+    if (n == 0) {
+      s->live[r->id] = r;
+      finish(s, r, STARK_OK);
+      return STARK_OK;
+    }
+    s->live[r->id] = r;
+    s->queue.push_back(r);
+  }
+  s->cv.notify_one();
+  return STARK_OK;
+}
+
+stark_status stark_poll(stark_server_t s, uint64_t id, int* done, stark_status* req_status) {
+  if (!s || !done) return STARK_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto f = s->finished.find(id);
+  if (f != s->finished.end()) {
+    *done = 1;
+    if (req_status) *req_status = f->second.first;
+    s->finished.erase(f);
+    return STARK_OK;
+  }
+  if (s->live.count(id)) {
+    *done = 0;
+    return STARK_OK;
+  }
+  return STARK_ENOTFOUND;
+}
+
+stark_status stark_server_drain(stark_server_t s) {
+  if (!s) return STARK_EINVAL;
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->live.empty()) return STARK_OK;
+    }
+    s->cv.notify_one();
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+}
+
+stark_status stark_request_latency(stark_server_t s, uint64_t id, double* seconds) {
+  if (!s || !seconds) return STARK_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->latency.find(id);
+  if (it == s->latency.end()) return s->live.count(id) ? STARK_EBUSY : STARK_ENOTFOUND;
+  *seconds = it->second;
+  return STARK_OK;
+}
+
+stark_status stark_server_stats(stark_server_t s, int64_t* cached_workspaces, int64_t* owned_bytes,
+                                int64_t* queued) {
+  if (!s) return STARK_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int64_t w = 0;
+  for (auto& kv : s->cache) w += (int64_t)kv.second.size();
+  if (cached_workspaces) *cached_workspaces = w;
+  if (owned_bytes) *owned_bytes = (int64_t)s->owned;
+  if (queued) *queued = (int64_t)s->queue.size();
+  return STARK_OK;
+}
+
+stark_status stark_server_destroy(stark_server_t s) {
+  if (!s) return STARK_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_one();
+  if (s->worker.joinable()) s->worker.join();
+  cudaDeviceSynchronize();
+  server_free(s);
+  return STARK_OK;
+}
+
+}  // extern "C"

@@ -71,6 +71,21 @@ cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, O
 // In-place transpose of `count` square L x L fp32 planes.
 cudaError_t launch_transpose_planes(float* planes, int64_t L, int64_t count, cudaStream_t s);
 
+// One member of a grouped leaf launch (a batch): its operand and C tensor
+// maps, where its work items start, and its combine table.  Lives in device
+// memory; 128-byte aligned for the tensor maps.
+struct alignas(128) GroupDesc {
+  CUtensorMap tmA, tmB, tmC;
+  int32_t item_base;   // first work item of this member
+  int32_t P, L;        // leaves, leaf side
+  int32_t use_tma_c;
+  const CTarget* ctab;
+  const int32_t* ccount;
+  int32_t maxT, pad;
+  float* C;
+  int64_t n;
+};
+
 struct LeafTcArgs {
   int32_t P;           // leaves per operand side (planes 0..P-1 hi, P..2P-1 lo)
   int32_t L;           // leaf side
@@ -85,11 +100,18 @@ struct LeafTcArgs {
   int* err;
   uint64_t timeout_ns;
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
+  // grouped launch (batch): when groups != nullptr the fields above that
+  // describe one problem are ignored and every item is looked up here
+  const GroupDesc* groups;
+  int32_t ngroups;
+  int32_t total_items;
 };
 
 // 3xBF16 / 3xTF32 leaf GEMMs with the combine fused in the epilogue.
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t s);
+// Grouped launch over a.groups (tensor maps taken from the descriptors).
+cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t s);
 int leaf_tc_smem_bytes(bool tf32, int bn);
 
 struct LeafCcArgs {

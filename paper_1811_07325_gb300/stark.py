@@ -69,6 +69,20 @@ _SIGS = {
     "stark_strerror": ([_ci], ctypes.c_char_p),
     "stark_selftest_bounded_wait": ([ctypes.c_uint64], _ci),
     "stark_launch_count": ([], _i64),
+    "stark_batch_create": ([_i32, _vp, _ci, _ci, ctypes.POINTER(_vp)], _ci),
+    "stark_batch_destroy": ([_vp], _ci),
+    "stark_batch_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
+    "stark_batch_depth": ([_vp, _i32, ctypes.POINTER(_i32)], _ci),
+    "stark_batch_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                          ctypes.POINTER(_i64)], _ci),
+    "stark_batch_check": ([_vp, _vp], _ci),
+    "stark_server_create": ([ctypes.c_size_t, _i32, ctypes.POINTER(_vp)], _ci),
+    "stark_submit": ([_vp, _i64, _ci, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _ci),
+    "stark_poll": ([_vp, ctypes.c_uint64, ctypes.POINTER(_ci), ctypes.POINTER(_ci)], _ci),
+    "stark_server_drain": ([_vp], _ci),
+    "stark_request_latency": ([_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], _ci),
+    "stark_server_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
+    "stark_server_destroy": ([_vp], _ci),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -235,6 +249,122 @@ class Plan:
         out = (ctypes.c_float * 3)()
         _check(_lib.stark_plan_phase_ms(self._h, out), "stark_plan_phase_ms")
         return {"zero_c": out[0], "divide": out[1], "leaf_combine": out[2]}
+
+
+class Batch:
+    """Independent products of mixed sizes in one grouped, graph-replayed pass
+    (``stark_batch_create``)."""
+
+    def __init__(self, sizes, depth: int = -1, dtype: DType = DType.F32_SPLIT_BF16):
+        self.sizes = [int(x) for x in sizes]
+        arr = (ctypes.c_int64 * len(self.sizes))(*self.sizes)
+        h = _vp()
+        _check(_lib.stark_batch_create(len(self.sizes), ctypes.cast(arr, _vp), int(depth), int(dtype),
+                                       ctypes.byref(h)), "stark_batch_create")
+        self._h = h
+        self.dtype = DType(dtype)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.stark_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def depths(self):
+        out = []
+        for i in range(len(self.sizes)):
+            d = _i32()
+            _check(_lib.stark_batch_depth(self._h, i, ctypes.byref(d)), "stark_batch_depth")
+            out.append(d.value)
+        return out
+
+    def info(self):
+        t, w, b, r = _i32(), _i64(), _i64(), _i64()
+        _check(_lib.stark_batch_info(self._h, ctypes.byref(t), ctypes.byref(w), ctypes.byref(b), ctypes.byref(r)),
+               "stark_batch_info")
+        return {"tile_n": t.value, "work_items": w.value, "workspace_bytes": b.value, "graph_replays": r.value}
+
+    def mul(self, As, Bs, Cs, stream=None):
+        """Cs[i] = As[i] @ Bs[i] (device fp32 tensors)."""
+        import torch
+        k = len(self.sizes)
+        if not (len(As) == len(Bs) == len(Cs) == k):
+            raise ValueError("one A, B and C per member")
+        pa, pb, pc = (_vp * k)(), (_vp * k)(), (_vp * k)()
+        for i, n in enumerate(self.sizes):
+            for t, name in ((As[i], "A"), (Bs[i], "B"), (Cs[i], "C")):
+                if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 \
+                        or tuple(t.shape) != (n, n) or not t.is_contiguous():
+                    raise ValueError(f"{name}[{i}] must be a contiguous fp32 CUDA {n}x{n} tensor")
+            pa[i], pb[i], pc[i] = As[i].data_ptr(), Bs[i].data_ptr(), Cs[i].data_ptr()
+        _check(_lib.stark_batch_mul(self._h, ctypes.cast(pa, _vp), ctypes.cast(pb, _vp), ctypes.cast(pc, _vp),
+                                    _stream_handle(stream)), "stark_batch_mul")
+        return Cs
+
+    def check(self, stream=None):
+        _check(_lib.stark_batch_check(self._h, _stream_handle(stream)), "stark_batch_check")
+
+
+class Server:
+    """Continuous-batching request server (``stark_server_create``)."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int = 4):
+        h = _vp()
+        _check(_lib.stark_server_create(int(hbm_budget_bytes), int(slots), ctypes.byref(h)), "stark_server_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.stark_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, A, B, C, dtype: DType = DType.F32_SPLIT_BF16) -> int:
+        """Queue C = A @ B (device tensors kept alive by the caller); returns the id."""
+        import torch
+        n = A.shape[0]
+        for t, name in ((A, "A"), (B, "B"), (C, "C")):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != _torch_dtype(dtype) \
+                    or tuple(t.shape) != (n, n) or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {n}x{n} CUDA tensor of the dtype's type")
+        rid = ctypes.c_uint64()
+        _check(_lib.stark_submit(self._h, n, int(dtype), A.data_ptr(), B.data_ptr(), C.data_ptr(), ctypes.byref(rid)),
+               "stark_submit")
+        return rid.value
+
+    def poll(self, rid: int):
+        """(done, status) without blocking."""
+        done, st = _ci(), _ci()
+        _check(_lib.stark_poll(self._h, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(st)), "stark_poll")
+        return bool(done.value), Status(st.value) if done.value else None
+
+    def drain(self):
+        _check(_lib.stark_server_drain(self._h), "stark_server_drain")
+
+    def latency(self, rid: int) -> float:
+        x = ctypes.c_double()
+        _check(_lib.stark_request_latency(self._h, ctypes.c_uint64(rid), ctypes.byref(x)), "stark_request_latency")
+        return x.value
+
+    def stats(self):
+        w, b, q = _i64(), _i64(), _i64()
+        _check(_lib.stark_server_stats(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(q)),
+               "stark_server_stats")
+        return {"cached_workspaces": w.value, "owned_bytes": b.value, "queued": q.value}
 
 
 def quadrant_table(depth: int, side: int):

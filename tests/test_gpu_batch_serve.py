@@ -1,0 +1,151 @@
+"""GPU tests of the batched form (one grouped, graph-replayed leaf launch for
+many products) and of the continuous-batching server, against the oracle and
+against the same products computed alone."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_07325_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check(C, A, B, L, dtype="F32_SPLIT_BF16"):
+    """Same bars as the single-product split tests: 1e-6 normwise (n >= 64)
+    and the relative-RMS bug signal s + 3 (L/k) 2^-24."""
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    want = oracle.gemm_classical(A64, B64)
+    diff = C.astype(np.float64) - want
+    ratio = np.abs(diff).max() / (np.linalg.norm(A64) * np.linalg.norm(B64))
+    s, k = (2.0 ** -12, 16) if dtype == "F32_SPLIT_BF16" else (2.0 ** -16, 8)
+    rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+    assert ratio <= 1e-6, ratio
+    assert rel <= s + 3 * (L / k) * 2.0 ** -24, rel
+    return want
+
+
+@pytest.mark.parametrize("sizes,depth,dtype", [([512, 768, 1000, 300, 1536], -1, "F32_SPLIT_BF16"),
+                                               ([1024, 2048, 512, 1536], 1, "F32_SPLIT_BF16"),
+                                               ([640, 384, 1100], -1, "F32_SPLIT_TF32")])
+def test_batch_matches_oracle_and_replays(stark_lib, sizes, depth, dtype):
+    S = stark_lib
+    dt = S.DType[dtype]
+    As = [synth.uniform(n, 300 + i, 0, dtype=np.float32) for i, n in enumerate(sizes)]
+    Bs = [synth.uniform(n, 300 + i, 1, dtype=np.float32) for i, n in enumerate(sizes)]
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    dC = [torch.full((n, n), float("nan"), device="cuda") for n in sizes]
+    with S.Batch(sizes, depth, dt) as bt:
+        depths = bt.depths()
+        assert all(0 <= d <= 3 for d in depths)
+        if depth >= 0:
+            assert depths == [depth] * len(sizes)
+        for rep in range(2):  # first call records the graph, second replays it
+            bt.mul(dA, dB, dC)
+            bt.check()
+            for i, n in enumerate(sizes):
+                L = (n + (128 << depths[i]) - 1) // (128 << depths[i]) * 128
+                check(dC[i].cpu().numpy(), As[i], Bs[i], L, dtype)
+            for c in dC:
+                c.fill_(float("nan"))
+        info = bt.info()
+        assert info["graph_replays"] == 2 and info["work_items"] > 0
+        # new C pointers: the graph is recorded again and stays correct
+        dC2 = [torch.empty((n, n), device="cuda") for n in sizes]
+        bt.mul(dA, dB, dC2)
+        bt.check()
+        for i, n in enumerate(sizes):
+            L = (n + (128 << depths[i]) - 1) // (128 << depths[i]) * 128
+            check(dC2[i].cpu().numpy(), As[i], Bs[i], L, dtype)
+
+
+def test_batch_rejects_bad_arguments(stark_lib):
+    S = stark_lib
+    with pytest.raises(S.StarkError):
+        S.Batch([], -1)
+    with pytest.raises(S.StarkError):
+        S.Batch([0, 64], -1)
+    with pytest.raises(S.StarkError):
+        S.Batch([64], -1, S.DType.F64)
+
+
+def wait_all(srv, ids, timeout=120.0):
+    pending, status = set(ids), {}
+    t0 = time.time()
+    while pending:
+        for rid in list(pending):
+            done, st = srv.poll(rid)
+            if done:
+                status[rid] = st
+                pending.discard(rid)
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.0005)
+    return status
+
+
+def test_server_results_equal_solo_and_oracle(stark_lib):
+    S = stark_lib
+    sizes = [256, 1200, 300, 777, 2048, 513, 1024, 4096, 260, 1500]
+    As = [synth.normal(n, 400 + i, 0) for i, n in enumerate(sizes)]
+    Bs = [synth.normal(n, 400 + i, 1) for i, n in enumerate(sizes)]
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    dC = [torch.empty((n, n), device="cuda") for n in sizes]
+    torch.cuda.synchronize()
+    with S.Server(16 << 30, slots=3) as srv:
+        ids = [srv.submit(dA[i], dB[i], dC[i]) for i in range(len(sizes))]  # arrive while others run
+        status = wait_all(srv, ids)
+        assert all(st == S.Status.OK for st in status.values())
+        lat = [srv.latency(r) for r in ids]
+        assert all(x > 0 for x in lat)
+        with pytest.raises(S.StarkError):  # reaped
+            srv.poll(ids[0])
+        st = srv.stats()
+        assert st["owned_bytes"] <= 16 << 30 and st["queued"] == 0
+    for i, n in enumerate(sizes):
+        with S.Plan(n, -1, S.DType.F32_SPLIT_BF16) as p:
+            solo = p.mul(dA[i], dB[i])
+            p.check()
+            L = p.leaf
+        # the same product alone and in the mix: same kernels, only the
+        # order of the combine's additions into C differs
+        assert (dC[i] - solo).abs().max().item() <= 1e-5 * solo.abs().max().item(), n
+        if n <= 2048:
+            check(dC[i].cpu().numpy(), As[i], Bs[i], L)
+
+
+def test_server_admission_under_small_budget(stark_lib):
+    S = stark_lib
+    # budget for about one n=1024 workspace at a time: requests queue and are
+    # admitted as memory frees up; each still completes correctly
+    sizes = [1024, 1000, 1024, 900, 1024, 1010]
+    As = [synth.integers(n, 500 + i, 0, -16, 16) for i, n in enumerate(sizes)]
+    Bs = [synth.integers(n, 500 + i, 1, -16, 16) for i, n in enumerate(sizes)]
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    dC = [torch.empty((n, n), dtype=torch.int64, device="cuda") for n in sizes]
+    torch.cuda.synchronize()
+    budget = 200 << 20
+    with S.Server(budget, slots=4) as srv:
+        ids = [srv.submit(dA[i], dB[i], dC[i], S.DType.I64) for i in range(len(sizes))]
+        status = wait_all(srv, ids)
+        assert all(st == S.Status.OK for st in status.values())
+        assert srv.stats()["owned_bytes"] <= budget
+        big = torch.zeros((8192, 8192), dtype=torch.int64, device="cuda")
+        with pytest.raises(S.StarkError) as e:
+            srv.submit(big, big, big, S.DType.I64)
+        assert e.value.status == S.Status.ENOMEM
+    for i, n in enumerate(sizes):
+        assert np.array_equal(dC[i].cpu().numpy(), oracle.gemm_classical(As[i], Bs[i])), n
+
+
+def test_server_unknown_id(stark_lib):
+    S = stark_lib
+    with S.Server(1 << 30, slots=1) as srv:
+        with pytest.raises(S.StarkError) as e:
+            srv.poll(12345)
+        assert e.value.status == S.Status.ENOTFOUND
