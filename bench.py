@@ -390,7 +390,6 @@ def main():
                 "launch_ms": phases["leaf_combine"]}
     divide_bytes = 2 * (n * n * 4) + plan.workspace_bytes  # read A, B; write every leaf operand (hi+lo)
 
-    plan_tmp_holder = []
     comparators = None
     if not args.no_comparators and rank == 0:
         comparators = {}
@@ -436,7 +435,6 @@ def main():
 
     batch = serve = None
     if rank == 0 and not args.no_batch:
-        del plan_tmp_holder[:]
         batch = run_batch(args, stark, synth, torch)
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, stark, synth, torch)

@@ -129,7 +129,7 @@ def test_server_admission_under_small_budget(stark_lib):
     dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
     dC = [torch.empty((n, n), dtype=torch.int64, device="cuda") for n in sizes]
     torch.cuda.synchronize()
-    budget = 200 << 20
+    budget = 60 << 20
     with S.Server(budget, slots=4) as srv:
         ids = [srv.submit(dA[i], dB[i], dC[i], S.DType.I64) for i in range(len(sizes))]
         status = wait_all(srv, ids)
