@@ -82,8 +82,12 @@ typedef struct {
 
 /* Build a plan for n x n products with `depth` recursion levels (Alg. 1 /
  * Alg. 2: depth = log2 of the number of partitions per side, the paper's
- * p - q).  depth = -1 lets the library choose (cost model over the leaf
- * GEMM and divide traffic).  depth 0 multiplies classically (one leaf).
+ * p - q).  depth = -1 lets the library choose: for the tensor-core dtypes a
+ * measured autotuner times the candidate depths on the device once per size
+ * class (n rounded up to 256) and caches the winner for the process (the
+ * paper's U-shaped optimum over the partition count, Sec. V-C, found by
+ * measurement); for F64/I64 a cost model over leaf work and divide traffic.
+ * depth 0 multiplies classically (one leaf).
  * Allocates the plan's device workspace on the current device.
  * Errors: EINVAL (n < 0 or > 2^20, depth < -1 or > 4, unknown dtype, out == NULL),
  * ENOMEM, ECUDA, EUNSUPPORTED (current device is not a GB300 / sm_103). */

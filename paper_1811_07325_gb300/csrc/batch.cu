@@ -59,7 +59,8 @@ float time_depth(int64_t n, int depth, stark_dtype dt, void* A, void* B, void* C
 }  // namespace
 
 // Measured depth choice for n x n products (cached per process).
-int autotune_depth(int64_t n, stark_dtype dt) {
+int autotune_depth(int64_t n_req, stark_dtype dt) {
+  const int64_t n = n_req <= 256 ? n_req : (n_req + 255) / 256 * 256;  // size class
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find({n, (int)dt});
@@ -255,8 +256,11 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
     if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
     for (int k = 0; k < count; ++k) {
       GroupDesc& g = b->host_desc[k];
-      g.C = static_cast<float*>(const_cast<void*>(ptrs[3 * k + 2]));
-      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n) ? 1 : 0;
+      void* Cuser = const_cast<void*>(ptrs[3 * k + 2]);
+      const bool staged = plan_uses_cstage(b->plans[k], Cuser);
+      g.C = static_cast<float*>(staged ? b->plans[k]->cstage : Cuser);
+      g.ldc = staged ? staged_ld(g.n) : g.n;
+      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n, g.ldc) ? 1 : 0;
     }
     if (cudaMemcpy(b->d_desc, b->host_desc.data(), sizeof(GroupDesc) * count, cudaMemcpyHostToDevice) !=
         cudaSuccess)
@@ -270,8 +274,8 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
     stark_status st = STARK_OK;
     for (int k = 0; k < count && st == STARK_OK; ++k) {
       stark_plan_s* p = b->plans[k];
-      if (cudaMemsetAsync(const_cast<void*>(ptrs[3 * k + 2]), 0, (size_t)p->n * p->n * p->esz, b->cap) !=
-          cudaSuccess)
+      const GroupDesc& g = b->host_desc[k];
+      if (cudaMemsetAsync(g.C, 0, (size_t)p->n * g.ldc * sizeof(float), b->cap) != cudaSuccess)
         st = STARK_ECUDA;
       else
         st = plan_divide(p, ptrs[3 * k], ptrs[3 * k + 1], b->cap);
@@ -286,6 +290,10 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
       if (launch_leaf_tc_grouped(a, b->dt == STARK_F32_SPLIT_TF32, b->bn, device_sm_count(), b->cap) !=
           cudaSuccess)
         st = STARK_ECUDA;
+      // members combined into a staging copy: move the result into C
+      for (int k = 0; k < count && st == STARK_OK; ++k)
+        if (b->host_desc[k].C != ptrs[3 * k + 2])
+          st = plan_copy_cstage(b->plans[k], const_cast<void*>(ptrs[3 * k + 2]), b->cap);
     }
     const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
     if (st != STARK_OK || ec != cudaSuccess) {

@@ -96,7 +96,7 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     it.nt = g->ccount[it.leaf];
     it.C = g->C;
     it.n = g->n;
-    it.ldc = g->n;
+    it.ldc = g->ldc;
     it.use_tma_c = g->use_tma_c;
   } else {
     const int tiles_n = p.L / BN;
@@ -172,7 +172,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      const uint64_t pol = policy_evict_normal();
+      // L2 priorities: a leaf's B panels are re-read by every row of tiles,
+      // so they should stay; A panels stream through once per row of tiles
+      const uint64_t pol_a = policy_evict_first();
+      const uint64_t pol_b = policy_evict_last();
       int s = 0;
       uint32_t phase = 0;
       uint32_t armed = 0, armed_phase = 0;  // per-stage: ever armed / parity of last arming
@@ -188,19 +191,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
           mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
           const int k0 = kb * Cfg::BK;
-          tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol);
-          tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol);
+          tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol_a);
+          tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol_a);
           if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
               tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
-                          pol);
+                          pol_b);
               tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
-                          it.P + leaf, full_bar(s), pol);
+                          it.P + leaf, full_bar(s), pol_b);
             }
           } else {
-            tma_load_3d(st + 2 * Cfg::A_BYTES, it.tB, k0, n0, leaf, full_bar(s), pol);
-            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, n0, it.P + leaf, full_bar(s), pol);
+            tma_load_3d(st + 2 * Cfg::A_BYTES, it.tB, k0, n0, leaf, full_bar(s), pol_b);
+            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, n0, it.P + leaf, full_bar(s), pol_b);
           }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
@@ -298,6 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t ebuf = epi_base + (uint32_t)(warp - 2) * 8192u;  // [+ box][- box]
+    const uint64_t pol_c = policy_evict_first();  // C lines: add and move on
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int item = blockIdx.x; item < num_items; item += gridDim.x) {
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int64_t y = (int64_t)c.row_off + m0 + quarter * 32;
               const int64_t x = (int64_t)c.col_off + n0 + chunk * 32;
               if (y >= it.n || x >= it.n) continue;
-              tma_reduce_add_2d(it.tC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u));
+              tma_reduce_add_2d(it.tC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u), pol_c);
             }
             bulk_commit_group();
           }

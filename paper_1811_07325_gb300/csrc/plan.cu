@@ -115,11 +115,11 @@ bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t 
   return r == CUDA_SUCCESS;
 }
 
-bool make_tmap_c(CUtensorMap* m, void* C, int64_t n) {
+bool make_tmap_c(CUtensorMap* m, void* C, int64_t n, int64_t ld) {
   auto fn = encode_fn();
-  if (!fn || n <= 0 || (n % 4) != 0 || (reinterpret_cast<uintptr_t>(C) & 15) != 0) return false;
+  if (!fn || n <= 0 || ld < n || (ld % 4) != 0 || (reinterpret_cast<uintptr_t>(C) & 15) != 0) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)(n * 4)};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
   cuuint32_t box[2] = {32, 32};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -251,7 +251,8 @@ stark_status stark_plan_create(int64_t n, int depth, stark_dtype dt, stark_plan_
     return STARK_EINVAL;
   if (n > (int64_t)1 << 20) return STARK_EINVAL;
   if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
-  if (depth < 0) depth = choose_depth(n, dt);
+  if (depth < 0)
+    depth = (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
   auto* p = new (std::nothrow) stark_plan_s();
   if (!p) return STARK_ENOMEM;
   stark_status st = plan_init(p, n, depth, dt);
@@ -435,6 +436,10 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
       cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
     return STARK_ECUDA;
 
+  if (p->is_tc && n > 0 && n % 4 != 0) {
+    // C cannot be a TMA target: combine into a staging copy with an aligned pitch
+    if (stark_status e = plan_ensure_cstage(p); e != STARK_OK) return e;
+  }
   if (p->is_tc) {
     const bool tf32 = dt == STARK_F32_SPLIT_TF32;
     if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * p->P, 128) ||
@@ -453,6 +458,7 @@ void plan_release(stark_plan_s* p) {
   cudaFree(p->stage_A);
   cudaFree(p->stage_B);
   cudaFree(p->stage_C);
+  cudaFree(p->cstage);
   for (auto e : p->ev)
     if (e) cudaEventDestroy(e);
   p->ev.clear();
@@ -506,15 +512,17 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     a.ctab = p->d_ctab;
     a.ccount = p->d_ccount;
     a.maxT = p->maxT;
-    a.C = static_cast<float*>(C);
-    a.ldc = p->n;
+    const bool staged = plan_uses_cstage(p, C);
+    a.C = static_cast<float*>(staged ? p->cstage : C);
+    a.ldc = staged ? staged_ld(p->n) : p->n;
     a.n = p->n;
     a.err = p->d_err;
     a.timeout_ns = p->timeout_ns;
     CUtensorMap tmC;
     std::memset(&tmC, 0, sizeof(tmC));
-    a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, C, p->n)) ? 1 : 0;
+    a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
     st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
+    if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   } else {
     LeafCcArgs a{};
     a.P = (int32_t)p->P;
@@ -545,8 +553,35 @@ stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, in
     ++p->timing_used;
     p->timing_active = true;
   }
-  if (cudaMemsetAsync(C, 0, (size_t)p->n * p->n * p->esz, s) != cudaSuccess) return to_status(cudaGetLastError());
+  if (p->is_tc && plan_uses_cstage(p, C)) {
+    if (cudaMemsetAsync(p->cstage, 0, (size_t)p->n * staged_ld(p->n) * 4, s) != cudaSuccess)
+      return to_status(cudaGetLastError());
+  } else if (cudaMemsetAsync(C, 0, (size_t)p->n * p->n * p->esz, s) != cudaSuccess) {
+    return to_status(cudaGetLastError());
+  }
   return plan_run_accumulate(p, A, B, C, lb, le, s);
+}
+
+stark_status plan_ensure_cstage(stark_plan_s* p) {
+  if (p->cstage) return STARK_OK;
+  const size_t bytes = (size_t)p->n * staged_ld(p->n) * 4;
+  if (cudaMalloc(&p->cstage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p->cstage = nullptr;
+    return STARK_ENOMEM;
+  }
+  p->ws_bytes += (int64_t)bytes;
+  return STARK_OK;
+}
+
+bool plan_uses_cstage(const stark_plan_s* p, const void* C) {
+  return p->is_tc && p->combine_mode != 1 && p->cstage != nullptr && !c_is_tma_target(C, p->n);
+}
+
+stark_status plan_copy_cstage(const stark_plan_s* p, void* C, cudaStream_t s) {
+  const size_t w = (size_t)p->n * 4;
+  return to_status(cudaMemcpy2DAsync(C, w, p->cstage, (size_t)staged_ld(p->n) * 4, w, (size_t)p->n,
+                                     cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace stark

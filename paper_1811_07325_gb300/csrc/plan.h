@@ -21,6 +21,10 @@ size_t element_size(stark_dtype dt);
 int64_t operand_bytes(int64_t n, int depth, stark_dtype dt);
 double model_seconds(int64_t n, int depth, stark_dtype dt);
 int choose_depth(int64_t n, stark_dtype dt);
+// Measured depth choice: times the candidate depths on the current device for
+// the size class of n (n rounded up to a multiple of 256) and caches the
+// winner per (class, dtype) for the process.  Tensor-core dtypes.
+int autotune_depth(int64_t n, stark_dtype dt);
 
 }  // namespace stark
 
@@ -51,6 +55,9 @@ struct stark_plan_s {
   void* stage_A = nullptr;
   void* stage_B = nullptr;
   void* stage_C = nullptr;
+  // staging copy of C (row pitch staged_ld(n)) for the tensor-core combine
+  // when C cannot be a TMA target (n not a multiple of 4)
+  void* cstage = nullptr;
   // optional phase timing: event sets for up to timing_cap products
   int timing_cap = 0;
   int timing_used = 0;
@@ -64,6 +71,10 @@ void plan_release(stark_plan_s* p);
 // Enqueue C = sum over leaves [lb, le) of their combine contributions.
 stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
                       cudaStream_t s);
+// Staging copy of C for the combine (allocated once; see stark_plan_s::cstage).
+stark_status plan_ensure_cstage(stark_plan_s* p);
+bool plan_uses_cstage(const stark_plan_s* p, const void* C);
+stark_status plan_copy_cstage(const stark_plan_s* p, void* C, cudaStream_t s);
 // Divide phase only: all leaf operands of A and B into the workspace.
 stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s);
 // The same without zeroing C first (C accumulates).

@@ -46,6 +46,8 @@ struct Request {
   void* C;
   Clock::time_point t_submit;
   stark_plan_s* ws = nullptr;  // workspace while running
+  void* target = nullptr;      // combine target: C, or the workspace's staging copy
+  int64_t ld = 0;              // its row pitch
   stark_status status = STARK_OK;
 };
 
@@ -89,7 +91,11 @@ using namespace stark;
 
 namespace {
 
-int depth_for(int64_t n, stark_dtype dt) { return choose_depth(n, dt); }
+// Tensor-core dtypes: the measured autotuner (per size class, cached);
+// fp64/int64: the cost model.
+int depth_for(int64_t n, stark_dtype dt) {
+  return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
+}
 
 // Find or make an idle workspace for request r (server mutex held).
 stark_plan_s* acquire_workspace(stark_server_s* s, const Request& r, stark_status* err) {
@@ -171,7 +177,18 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
     view.timing_cap = 0;
     stark_status e;
     if (r->dt == STARK_F32_SPLIT_BF16 || r->dt == STARK_F32_SPLIT_TF32) {
-      if (cudaMemsetAsync(r->C, 0, (size_t)r->n * r->n * view.esz, st) != cudaSuccess) return STARK_ECUDA;
+      // C that TMA cannot address (n % 4 != 0) is combined in the bucket's staging copy
+      if (!c_is_tma_target(r->C, r->n)) {
+        const int64_t before = r->ws->ws_bytes;
+        if (plan_ensure_cstage(r->ws) != STARK_OK) return STARK_ENOMEM;
+        s->owned += (size_t)(r->ws->ws_bytes - before);
+        r->target = r->ws->cstage;
+        r->ld = staged_ld(r->n);
+      } else {
+        r->target = r->C;
+        r->ld = r->n;
+      }
+      if (cudaMemsetAsync(r->target, 0, (size_t)r->n * r->ld * sizeof(float), st) != cudaSuccess) return STARK_ECUDA;
       e = plan_divide(&view, r->A, r->B, st);
       tc.push_back(r);
     } else {
@@ -201,9 +218,10 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       g.ctab = p->d_ctab;
       g.ccount = p->d_ccount;
       g.maxT = p->maxT;
-      g.C = static_cast<float*>(tc[k]->C);
+      g.C = static_cast<float*>(tc[k]->target);
       g.n = tc[k]->n;
-      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n) ? 1 : 0;
+      g.ldc = tc[k]->ld;
+      g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n, g.ldc) ? 1 : 0;
       items += p->P * (p->L / 128) * (p->L / bn);
     }
     if (cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(GroupDesc) * tc.size(), cudaMemcpyHostToDevice, st) !=
@@ -216,6 +234,13 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
     a.ngroups = (int32_t)tc.size();
     a.total_items = (int32_t)items;
     if (launch_leaf_tc_grouped(a, tf32, bn, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+    for (Request* r : tc)
+      if (r->target != r->C) {
+        const size_t w = (size_t)r->n * sizeof(float);
+        if (cudaMemcpy2DAsync(r->C, w, r->target, (size_t)r->ld * sizeof(float), w, (size_t)r->n,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          return STARK_ECUDA;
+      }
   }
   if (cudaEventRecord(slot.done, st) != cudaSuccess) return STARK_ECUDA;
   return STARK_OK;

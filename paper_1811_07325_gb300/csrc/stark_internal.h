@@ -82,8 +82,9 @@ struct alignas(128) GroupDesc {
   const CTarget* ctab;
   const int32_t* ccount;
   int32_t maxT, pad;
-  float* C;
-  int64_t n;
+  float* C;     // combine target (the caller's C, or a staging copy)
+  int64_t n;    // problem side (rows and columns of C)
+  int64_t ldc;  // row pitch of the combine target in elements
 };
 
 struct LeafTcArgs {
@@ -134,7 +135,16 @@ void count_launch(int k = 1);
 int device_sm_count();
 bool device_is_sm100_family();
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows);
-// n x n fp32 row-major C, 32 x 32 boxes, 128-byte swizzle (reduction target).
-bool make_tmap_c(CUtensorMap* m, void* C, int64_t n);
+// n x n fp32 row-major C with row pitch ld elements, 32 x 32 boxes,
+// 128-byte swizzle (reduction target).  Needs ld % 4 == 0 and a 16-byte
+// aligned base.
+bool make_tmap_c(CUtensorMap* m, void* C, int64_t n, int64_t ld);
+// Row pitch of the staging copy of C used when C itself cannot be a TMA
+// target (n not a multiple of 4): n rounded up to a multiple of 4.
+inline int64_t staged_ld(int64_t n) { return (n + 3) / 4 * 4; }
+// True when the caller's C can take the TMA bulk reductions directly.
+inline bool c_is_tma_target(const void* C, int64_t n) {
+  return n > 0 && (n % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+}
 
 }  // namespace stark

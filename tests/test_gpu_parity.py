@@ -209,7 +209,7 @@ def test_split_repeatable_and_stream_ordered(S):
         check_split(C2.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
 
 
-@pytest.mark.parametrize("n,d", [(1024, 2), (1000, 3), (1004, 1)])
+@pytest.mark.parametrize("n,d", [(1024, 2), (1000, 3), (1004, 1), (1001, 2), (777, 1)])
 def test_split_combine_modes_agree(S, n, d):
     # TMA bulk reductions and the vector-atomic fallback give the same product
     A = synth.normal(n, 61, 0)
