@@ -84,7 +84,7 @@ typedef struct {
  * Alg. 2: depth = log2 of the number of partitions per side, the paper's
  * p - q).  depth = -1 lets the library choose: for the tensor-core dtypes a
  * measured autotuner times the candidate depths on the device once per size
- * class (n rounded up to 256) and caches the winner for the process (the
+ * class (n rounded up to 64, 128 or 256) and caches the winner for the process (the
  * paper's U-shaped optimum over the partition count, Sec. V-C, found by
  * measurement); for F64/I64 a cost model over leaf work and divide traffic.
  * depth 0 multiplies classically (one leaf).

@@ -60,7 +60,9 @@ float time_depth(int64_t n, int depth, stark_dtype dt, void* A, void* B, void* C
 
 // Measured depth choice for n x n products (cached per process).
 int autotune_depth(int64_t n_req, stark_dtype dt) {
-  const int64_t n = n_req <= 256 ? n_req : (n_req + 255) / 256 * 256;  // size class
+  // size class: n rounded up to 64 (n <= 1024), 128 (n <= 2048), else 256
+  const int64_t q = n_req <= 1024 ? 64 : n_req <= 2048 ? 128 : 256;
+  const int64_t n = (n_req + q - 1) / q * q;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find({n, (int)dt});

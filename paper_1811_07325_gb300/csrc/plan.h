@@ -22,8 +22,9 @@ int64_t operand_bytes(int64_t n, int depth, stark_dtype dt);
 double model_seconds(int64_t n, int depth, stark_dtype dt);
 int choose_depth(int64_t n, stark_dtype dt);
 // Measured depth choice: times the candidate depths on the current device for
-// the size class of n (n rounded up to a multiple of 256) and caches the
-// winner per (class, dtype) for the process.  Tensor-core dtypes.
+// the size class of n (n rounded up to 64 / 128 / 256 for n up to 1024 /
+// 2048 / beyond) and caches the winner per (class, dtype) for the process.
+// Tensor-core dtypes.
 int autotune_depth(int64_t n, stark_dtype dt);
 
 }  // namespace stark
