@@ -301,3 +301,27 @@ def test_full_size_sampled_rows(S, dtype, d):
     del C, dA, dB
     torch.cuda.empty_cache()
     check_split(got, want, an, bn, dtype, L=L)
+
+
+def test_mul_sharded_single_rank_nccl(S, tmp_path):
+    # the sharding path end to end on one GPU: local leaves + NCCL all-reduce
+    import datetime
+    import socket
+    import torch.distributed as dist
+    from paper_1811_07325_gb300 import shard
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        n = 500
+        A = synth.integers(n, 91, 0, -16, 16)
+        B = synth.integers(n, 91, 1, -16, 16)
+        with S.Plan(n, 2, S.DType.I64) as p:
+            C = torch.empty((n, n), dtype=torch.int64, device="cuda")
+            shard.mul_sharded(p, dev(A), dev(B), C)
+            torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy(), oracle.gemm_classical(A, B))
+    finally:
+        dist.destroy_process_group()
