@@ -36,6 +36,39 @@ sys.path.insert(0, ROOT)
 METRIC = "effective TFLOP/s (2n³/t) at n=16384, stated error vs FP64; p50/p99 serve latency"
 
 
+LEAF_SOURCES = ["paper_1811_07325_gb300/csrc/leaf_tc.cu", "paper_1811_07325_gb300/csrc/ptx.cuh",
+                "paper_1811_07325_gb300/csrc/stark_internal.h"]
+TRAFFIC_PROFILE = "profiles/leaf_tc_traffic_n16384_d2_bf16.md"
+
+
+def leaf_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in LEAF_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(n, depth):
+    """DRAM bytes per leaf launch from the committed ncu summary, if it was
+    taken on this exact kernel source and workload; else None."""
+    try:
+        kv = {}
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_source_sha256") != leaf_source_hash():
+            return None
+        if int(kv.get("n", -1)) != n or int(kv.get("depth", -1)) != depth:
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -230,6 +263,13 @@ def run_serve(args, stark, synth, torch):
             "cached_workspaces": stats["cached_workspaces"], "workspace_bytes": stats["owned_bytes"]}
 
 
+def workload_config(args, depth):
+    n = args.n
+    return {"workload": f"strassen n={n} depth={depth} fp32 N(0,1) split-{args.dtype}", "n": n, "depth": depth,
+            "per_rank": "one independent product per rank",
+            "l2": "inputs (2 x 1 GiB) and workspace larger than L2; no flush needed"}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle, timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -255,7 +295,8 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"strassen n={n} (CPU oracle, row-sampled)", "n": n},
+            "config": dict(workload_config(args, args.depth), reference_arm="CPU oracle (classical FP64), "
+                           "row-sampled: each step computes a bounded sample of rows of this product"),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
@@ -265,7 +306,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
@@ -278,6 +319,7 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tf32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=600)
@@ -384,7 +426,7 @@ def main():
     achieved = leaf_flops / (phases["leaf_combine"] * 1e-3) / 1e12
     roofline = {"kernel": "leaf_tc_kernel (3xBF16 leaf GEMMs + fused combine)", "bound": "tensor",
                 "achieved": achieved, "peak": pk["bf16_sustained"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_sustained"], "traffic": None,
+                "frac": achieved / pk["bf16_sustained"], "traffic": measured_traffic(n, plan.depth),
                 "peak_source": f"{pk['source']} bf16 sustained",
                 "algorithmic_flops_per_launch": leaf_flops,
                 "launch_ms": phases["leaf_combine"]}
@@ -433,6 +475,40 @@ def main():
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
 
+    tf32 = None
+    if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
+        # the same product with 3xTF32 leaves, for comparison
+        del C
+        torch.cuda.empty_cache()
+        p32 = stark.Plan(n, d, stark.DType.F32_SPLIT_TF32)
+        C32 = torch.empty_like(A)
+        for _ in range(2):
+            p32.mul(A, B, C32)
+        p32.check()
+        p32.set_timing(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            p32.mul(A, B, C32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / 5
+        ph32 = p32.phase_ms()
+        tf32 = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32, "phases_ms": ph32}
+        if not args.no_check:
+            import oracle
+            rows = synth.sample_rows(n, 256, args.seed + 5)
+            want = oracle.gemm_rows(A_h.numpy(), B_h.numpy(), rows)
+            got = C32[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+            an = float(torch.linalg.vector_norm(A.double()).item())
+            bn = float(torch.linalg.vector_norm(B.double()).item())
+            diff = got - want
+            tf32["error_vs_fp64"] = {"max_abs_over_normA_normB": float(np.abs(diff).max() / (an * bn)),
+                                     "rel_rms": float(np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2)))}
+        p32.close()
+        del C32
+        torch.cuda.empty_cache()
+
     batch = serve = None
     if rank == 0 and not args.no_batch:
         batch = run_batch(args, stark, synth, torch)
@@ -449,14 +525,12 @@ def main():
                "vs_baseline": None, "dtype": "f32 in/out, 3xbf16 tensor-core leaves, fp32 accumulate"
                if args.dtype == "bf16" else "f32 in/out, 3xtf32 tensor-core leaves, fp32 accumulate",
                "data": "synthetic",
-               "config": {"workload": f"strassen n={n} depth={plan.depth} fp32 N(0,1) split-{args.dtype}",
-                          "n": n, "depth": plan.depth, "leaves": plan.leaves, "leaf": plan.leaf,
-                          "tile": list(plan.tile), "per_rank": "one independent product per rank",
-                          "l2": "inputs (2 x 1 GiB) and workspace larger than L2; no flush needed"},
+               "config": dict(workload_config(args, plan.depth), leaves=plan.leaves, leaf=plan.leaf,
+                              tile=list(plan.tile)),
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
-               "error_vs_fp64": error, "comparators": comparators, "batch": batch, "serve": serve,
+               "error_vs_fp64": error, "comparators": comparators, "tf32": tf32, "batch": batch, "serve": serve,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     plan.close()

@@ -91,7 +91,7 @@ typedef struct {
  * Allocates the plan's device workspace on the current device.
  * Errors: EINVAL (n < 0 or > 2^20, depth < -1 or > 4, unknown dtype, out == NULL),
  * ENOMEM, ECUDA, EUNSUPPORTED (current device is not a GB300 / sm_103). */
-STARK_API stark_status stark_plan_create(int64_t n, int depth, stark_dtype dtype, stark_plan_t *out);
+STARK_API stark_status stark_plan(int64_t n, int depth, stark_dtype dtype, stark_plan_t *out);
 
 /* Release a plan and its workspace (waits for the device to finish using it).
  * NULL is accepted and ignored. */

@@ -243,7 +243,7 @@ stark_status stark_quadrant_table(int depth, int side, int32_t* count, int32_t* 
   return STARK_OK;
 }
 
-stark_status stark_plan_create(int64_t n, int depth, stark_dtype dt, stark_plan_t* out) {
+stark_status stark_plan(int64_t n, int depth, stark_dtype dt, stark_plan_t* out) {
   if (!out) return STARK_EINVAL;
   *out = nullptr;
   if (n < 0 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;

@@ -54,7 +54,7 @@ class PlanInfo(ctypes.Structure):
 
 _i64, _i32, _vp, _ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int
 _SIGS = {
-    "stark_plan_create": ([_i64, _ci, _ci, ctypes.POINTER(_vp)], _ci),
+    "stark_plan": ([_i64, _ci, _ci, ctypes.POINTER(_vp)], _ci),
     "stark_plan_destroy": ([_vp], _ci),
     "stark_plan_get_info": ([_vp, ctypes.POINTER(PlanInfo)], _ci),
     "stark_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
@@ -136,11 +136,11 @@ class _CudaBuffer:
 
 
 class Plan:
-    """A plan for n x n products (``stark_plan_create``)."""
+    """A plan for n x n products (``stark_plan``)."""
 
     def __init__(self, n: int, depth: int = -1, dtype: DType = DType.F32_SPLIT_BF16):
         h = _vp()
-        _check(_lib.stark_plan_create(int(n), int(depth), int(dtype), ctypes.byref(h)), "stark_plan_create")
+        _check(_lib.stark_plan(int(n), int(depth), int(dtype), ctypes.byref(h)), "stark_plan")
         self._h = h
         info = PlanInfo()
         _check(_lib.stark_plan_get_info(h, ctypes.byref(info)), "stark_plan_get_info")

@@ -20,7 +20,7 @@ def declared_in_header():
 
 def test_header_declares_entry_points():
     names = declared_in_header()
-    assert "stark_plan_create" in names and "stark_mul" in names and len(names) >= 10
+    assert "stark_plan" in names and "stark_mul" in names and len(names) >= 10
 
 
 def test_library_exports_every_declared_symbol(stark_lib):

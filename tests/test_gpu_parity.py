@@ -127,6 +127,35 @@ def test_divide_plain_f64_matches_oracle_sums(S, n, d):
         assert np.array_equal(Y.cpu().numpy(), yb.astype(np.float64))
 
 
+# ----------------------------------------------------------------- n = 4096 depth sweep (fp64, int64)
+@pytest.mark.slow
+def test_n4096_depth_sweep_int64_and_f64(S):
+    n = 4096
+    Ai = synth.integers(n, 4096, 0, -16, 16)
+    Bi = synth.integers(n, 4096, 1, -16, 16)
+    want_i = oracle.gemm_classical(Ai, Bi)
+    dA, dB = dev(Ai), dev(Bi)
+    for d in (1, 2, 3, 4):
+        with S.Plan(n, d, S.DType.I64) as p:
+            C = p.mul(dA, dB)
+            p.check()
+            assert np.array_equal(C.cpu().numpy(), want_i), d
+    del dA, dB
+    Af = synth.uniform(n, 4096, 2)
+    Bf = synth.uniform(n, 4096, 3)
+    rows = synth.sample_rows(n, 64, 4096)
+    want_f = oracle.gemm_rows(Af, Bf, rows)
+    dA, dB = dev(Af), dev(Bf)
+    for d in (1, 2, 3, 4):
+        with S.Plan(n, d, S.DType.F64) as p:
+            C = p.mul(dA, dB)
+            p.check()
+            got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+        err = np.abs(got - want_f).max()
+        assert err <= higham_bound(n, d, Af, Bf), (d, err)
+        assert err / (np.linalg.norm(Af) * np.linalg.norm(Bf)) <= 1e-12
+
+
 # ----------------------------------------------------------------- fp64
 @pytest.mark.parametrize("n,depths", [(129, [0, 1]), (640, [1, 2, 3]), (1024, [3])])
 def test_f64_within_bound(S, n, depths):
