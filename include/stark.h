@@ -109,9 +109,20 @@ STARK_API stark_status stark_mul(stark_plan_t plan, const void *A, const void *B
 
 /* The same product, end to end from host memory: copies A and B host->device
  * into plan-owned buffers, runs stark_mul, copies C device->host and waits
- * for completion.  A, B, C: host pointers (pinned memory gives full copy
- * bandwidth).  Synchronous. */
+ * for completion (then reports device-side errors like stark_plan_check).
+ * A, B, C: host pointers (pinned memory gives full copy bandwidth).
+ * Synchronous.  Allocates two staging sets (6 n^2 elements) on first use. */
 STARK_API stark_status stark_mul_host(stark_plan_t plan, const void *A, const void *B, void *C, void *stream);
+
+/* Asynchronous form of stark_mul_host for streams of products: enqueues the
+ * host->device copies, the product and the device->host copy on three
+ * plan-owned streams with alternating staging sets, so the copies of one
+ * call overlap the product of the previous one, and makes `stream` wait for
+ * this product's result.  The host buffers must stay valid and unmodified
+ * (C unread) until `stream` has passed that point; consecutive calls may not
+ * reuse a C buffer before the earlier call completed.  Errors as stark_mul. */
+STARK_API stark_status stark_mul_host_async(stark_plan_t plan, const void *A, const void *B, void *C,
+                                            void *stream);
 
 /* Partial product for sharding the leaves across devices (the independent
  * products of one recursion tree, Sec. III-C): C = sum over leaves l in

@@ -299,23 +299,59 @@ stark_status stark_mul_leaves(stark_plan_t p, const void* A, const void* B, void
   return plan_run(p, A, B, C, leaf_begin, leaf_end, (cudaStream_t)stream);
 }
 
-stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
-  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
-  if (p->n == 0) return STARK_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+// Staging buffers and pipeline streams for the host entry points.
+static stark_status ensure_host_pipeline(stark_plan_t p) {
+  if (p->s_in) return STARK_OK;
   const size_t bytes = (size_t)p->n * p->n * p->esz;
-  if (!p->stage_A) {
-    if (cudaMalloc(&p->stage_A, bytes) != cudaSuccess || cudaMalloc(&p->stage_B, bytes) != cudaSuccess ||
-        cudaMalloc(&p->stage_C, bytes) != cudaSuccess) {
+  void** bufs[6] = {&p->stage_A, &p->stage_B, &p->stage_C, &p->stage2[0], &p->stage2[1], &p->stage2[2]};
+  for (void** b : bufs)
+    if (cudaMalloc(b, bytes) != cudaSuccess) {
       cudaGetLastError();
       return STARK_ENOMEM;
     }
-  }
-  if (cudaMemcpyAsync(p->stage_A, A, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STARK_ECUDA;
-  if (cudaMemcpyAsync(p->stage_B, B, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STARK_ECUDA;
-  stark_status st = plan_run(p, p->stage_A, p->stage_B, p->stage_C, 0, p->P, s);
+  for (cudaStream_t* st : {&p->s_in, &p->s_comp, &p->s_out})
+    if (cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) return STARK_ECUDA;
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t* e : {&p->ev_in[i], &p->ev_comp[i], &p->ev_out[i]})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return STARK_ECUDA;
+  return STARK_OK;
+}
+
+stark_status stark_mul_host_async(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
+  if (p->n == 0) return STARK_OK;
+  if (stark_status st = ensure_host_pipeline(p); st != STARK_OK) return st;
+  const size_t bytes = (size_t)p->n * p->n * p->esz;
+  const int k = p->host_calls++ & 1;  // buffer set of this call
+  void* dA = k ? p->stage2[0] : p->stage_A;
+  void* dB = k ? p->stage2[1] : p->stage_B;
+  void* dC = k ? p->stage2[2] : p->stage_C;
+  cudaStream_t user = (cudaStream_t)stream;
+  bool ok = true;
+  // inputs of this set may be overwritten once the product two calls ago has
+  // read them; its C once that C has been copied out
+  ok = ok && cudaStreamWaitEvent(p->s_in, p->ev_comp[k], 0) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(dA, A, bytes, cudaMemcpyHostToDevice, p->s_in) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(dB, B, bytes, cudaMemcpyHostToDevice, p->s_in) == cudaSuccess;
+  ok = ok && cudaEventRecord(p->ev_in[k], p->s_in) == cudaSuccess;
+  ok = ok && cudaStreamWaitEvent(p->s_comp, p->ev_in[k], 0) == cudaSuccess;
+  ok = ok && cudaStreamWaitEvent(p->s_comp, p->ev_out[k], 0) == cudaSuccess;
+  if (!ok) return STARK_ECUDA;
+  stark_status st = plan_run(p, dA, dB, dC, 0, p->P, p->s_comp);
   if (st != STARK_OK) return st;
-  if (cudaMemcpyAsync(C, p->stage_C, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return STARK_ECUDA;
+  ok = ok && cudaEventRecord(p->ev_comp[k], p->s_comp) == cudaSuccess;
+  ok = ok && cudaStreamWaitEvent(p->s_out, p->ev_comp[k], 0) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(C, dC, bytes, cudaMemcpyDeviceToHost, p->s_out) == cudaSuccess;
+  ok = ok && cudaEventRecord(p->ev_out[k], p->s_out) == cudaSuccess;
+  // the caller's stream observes completion of this product
+  ok = ok && cudaStreamWaitEvent(user, p->ev_out[k], 0) == cudaSuccess;
+  return ok ? STARK_OK : STARK_ECUDA;
+}
+
+stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  stark_status st = stark_mul_host_async(p, A, B, C, stream);
+  if (st != STARK_OK) return st;
+  if (p->n == 0) return STARK_OK;
   return stark_plan_check(p, stream);
 }
 
@@ -458,6 +494,12 @@ void plan_release(stark_plan_s* p) {
   cudaFree(p->stage_A);
   cudaFree(p->stage_B);
   cudaFree(p->stage_C);
+  for (void* b : p->stage2) cudaFree(b);
+  for (cudaStream_t st : {p->s_in, p->s_comp, p->s_out})
+    if (st) cudaStreamDestroy(st);
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t e : {p->ev_in[i], p->ev_comp[i], p->ev_out[i]})
+      if (e) cudaEventDestroy(e);
   cudaFree(p->cstage);
   for (auto e : p->ev)
     if (e) cudaEventDestroy(e);

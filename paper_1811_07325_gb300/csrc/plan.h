@@ -52,10 +52,15 @@ struct stark_plan_s {
   int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics
   CUtensorMap tmA;
   CUtensorMap tmB;
-  // end-to-end staging (stark_mul_host), allocated on first use
+  // end-to-end staging (stark_mul_host / _async), allocated on first use:
+  // two buffer sets so consecutive products overlap copies with compute
   void* stage_A = nullptr;
   void* stage_B = nullptr;
   void* stage_C = nullptr;
+  void* stage2[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  int host_calls = 0;
   // staging copy of C (row pitch staged_ld(n)) for the tensor-core combine
   // when C cannot be a TMA target (n not a multiple of 4)
   void* cstage = nullptr;

@@ -59,6 +59,7 @@ _SIGS = {
     "stark_plan_get_info": ([_vp, ctypes.POINTER(PlanInfo)], _ci),
     "stark_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
     "stark_mul_host": ([_vp, _vp, _vp, _vp, _vp], _ci),
+    "stark_mul_host_async": ([_vp, _vp, _vp, _vp, _vp], _ci),
     "stark_mul_leaves": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _ci),
     "stark_plan_operands": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _ci),
     "stark_plan_check": ([_vp, _vp], _ci),
@@ -193,8 +194,9 @@ class Plan:
                "stark_mul_leaves")
         return C
 
-    def mul_host(self, A, B, C=None, stream=None):
-        """End to end from host memory (numpy arrays or CPU tensors, pinned is best)."""
+    def mul_host(self, A, B, C=None, stream=None, asynchronous=False):
+        """End to end from host memory (numpy arrays or CPU tensors, pinned is
+        best).  ``asynchronous=True``: pipelined form, completion on ``stream``."""
         def ptr(x, name):
             if hasattr(x, "data_ptr"):
                 if x.is_cuda or tuple(x.shape) != (self.n, self.n) or not x.is_contiguous():
@@ -206,8 +208,8 @@ class Plan:
             return ctypes.c_void_p(x.ctypes.data)
         if C is None:
             C = np.empty((self.n, self.n), dtype=_numpy_dtype(self.dtype))
-        _check(_lib.stark_mul_host(self._h, ptr(A, "A"), ptr(B, "B"), ptr(C, "C"), _stream_handle(stream)),
-               "stark_mul_host")
+        fn = _lib.stark_mul_host_async if asynchronous else _lib.stark_mul_host
+        _check(fn(self._h, ptr(A, "A"), ptr(B, "B"), ptr(C, "C"), _stream_handle(stream)), "stark_mul_host")
         return C
 
     def operands(self, A, B, stream=None):

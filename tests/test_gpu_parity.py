@@ -284,6 +284,25 @@ def test_mul_host_matches_device(S):
     check_split(Cd, want, an, bn, "F32_SPLIT_BF16")
 
 
+def test_mul_host_async_pipeline(S):
+    # consecutive asynchronous host products with different inputs, results
+    # read after one synchronisation: each equals its own product
+    n = 640
+    pairs = [(synth.normal(n, 80 + k, 0), synth.normal(n, 80 + k, 1)) for k in range(4)]
+    As = [torch.from_numpy(a).pin_memory() for a, _ in pairs]
+    Bs = [torch.from_numpy(b).pin_memory() for _, b in pairs]
+    Cs = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in pairs]
+    with S.Plan(n, 1, S.DType.F32_SPLIT_BF16) as p:
+        for k in range(4):
+            p.mul_host(As[k], Bs[k], Cs[k], asynchronous=True)
+        torch.cuda.synchronize()
+        p.check()
+    for k, (a, b) in enumerate(pairs):
+        want = oracle.gemm_classical(a.astype(np.float64), b.astype(np.float64))
+        an, bn = np.linalg.norm(a.astype(np.float64)), np.linalg.norm(b.astype(np.float64))
+        check_split(Cs[k].numpy(), want, an, bn, "F32_SPLIT_BF16")
+
+
 def test_empty_and_bad_arguments(S):
     with S.Plan(0, 1, S.DType.F32_SPLIT_BF16) as p:
         e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
