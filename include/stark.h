@@ -151,6 +151,13 @@ STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, con
  * within fp32 rounding (the order of the additions into C differs). */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
+/* Leaf launch schedule on the 3xBF16 path: enable = 1 (default) runs CTA
+ * pairs (thread-block clusters of 2) on vertically adjacent tiles that share
+ * one B tile, fetched once and multicast to both, whenever the leaf side
+ * allows (256-wide tiles, an even number of 128-row tiles); 0 runs single
+ * CTAs.  Results agree within fp32 rounding of the combine's order. */
+STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
+
 /* Synchronise the plan's last stream and report any device-side error
  * (STARK_ETIMEOUT) recorded by its kernels since the previous check; the
  * error word is cleared. */

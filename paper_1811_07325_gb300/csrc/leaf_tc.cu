@@ -68,9 +68,9 @@ struct ItemInfo {
   int use_tma_c;
 };
 
-template <int BN, int BK, bool GROUPED>
+template <int BN, int BK, bool GROUPED, bool PAIR>
 __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, const CUtensorMap* tmA,
-                                                const CUtensorMap* tmB, const CUtensorMap* tmC) {
+                                                const CUtensorMap* tmB, const CUtensorMap* tmC, uint32_t rank) {
   ItemInfo it;
   if constexpr (GROUPED) {
     // member owning this item: the last one whose item_base <= item
@@ -99,15 +99,17 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     it.ldc = g->ldc;
     it.use_tma_c = g->use_tma_c;
   } else {
+    // PAIR: an item is a pair of vertically adjacent tiles sharing one B
+    // tile; this CTA (cluster rank 0 or 1) computes the upper or lower one
     const int tiles_n = p.L / BN;
-    const int per_leaf = (p.L / kBM) * tiles_n;
+    const int per_leaf = (p.L / kBM / (PAIR ? 2 : 1)) * tiles_n;
     const int rem = item % per_leaf;
     it.tA = tmA;
     it.tB = tmB;
     it.tC = tmC;
     it.leaf = p.leaf_begin + item / per_leaf;
     it.P = p.P;
-    it.m0 = (rem / tiles_n) * kBM;
+    it.m0 = PAIR ? ((rem / tiles_n) * 2 + (int)rank) * kBM : (rem / tiles_n) * kBM;
     it.n0 = (rem % tiles_n) * BN;
     it.kblocks = p.L / BK;
     it.tg = p.ctab + (int64_t)it.leaf * p.maxT;
@@ -120,7 +122,7 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
   return it;
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
@@ -142,12 +144,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
 
-  const int num_items = GROUPED ? p.total_items : (p.leaf_end - p.leaf_begin) * (p.L / kBM) * (p.L / BN);
+  // PAIR: clusters of two CTAs; each B tile is fetched once, multicast to both
+  const uint32_t cta_rank = PAIR ? cluster_ctarank() : 0u;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int num_items = GROUPED ? p.total_items
+                                : (p.leaf_end - p.leaf_begin) * (p.L / kBM / (PAIR ? 2 : 1)) * (p.L / BN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), PAIR ? 2 : 1);  // PAIR: both CTAs' MMAs must be done with it
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(accf_bar(a), 1);
@@ -160,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (p.use_tma_c) prefetch_tmap(&tmC);
     }
   }
+  if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before any multicast lands
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
     tmem_relinquish();
@@ -180,8 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t armed = 0, armed_phase = 0;  // per-stage: ever armed / parity of last arming
       bool ok = true;
-      for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
-        const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC);
+      for (int item = unit; ok && item < num_items; item += units) {
+        const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
         const int leaf = it.leaf, m0 = it.m0, n0 = it.n0;
         for (int kb = 0; kb < it.kblocks; ++kb) {
           if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) {
@@ -193,7 +201,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = kb * Cfg::BK;
           tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol_a);
           tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol_a);
-          if constexpr (Cfg::B_MN) {
+          if constexpr (PAIR) {
+            // this CTA fetches its half of the B chunks for both CTAs
+#pragma unroll
+            for (int c = (int)cta_rank * (Cfg::NCHUNK / 2); c < ((int)cta_rank + 1) * (Cfg::NCHUNK / 2); ++c) {
+              tma_load_3d_mc(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf,
+                             full_bar(s), 0x3, pol_b);
+              tma_load_3d_mc(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
+                             it.P + leaf, full_bar(s), 0x3, pol_b);
+            }
+          } else if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
               tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
@@ -217,6 +234,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let every copy already issued land before the CTA can exit
         for (int t = 0; t < STAGES; ++t)
           if (armed & (1u << t)) mbar_wait_bounded(full_bar(t), (armed_phase >> t) & 1, nullptr, 0, 200000000ull);
+      } else if constexpr (PAIR) {
+        // every arrival the peer owes our empty barriers has landed before exit
+        for (int t = 0; t < STAGES; ++t) {
+          if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) break;
+          if (++s == STAGES) {
+            s = 0;
+            phase ^= 1;
+          }
+        }
       }
     }
   } else if (warp == 1) {
@@ -228,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t acc_phase = 0;
       bool ok = true;
       bool issued = false;
-      for (int item = blockIdx.x; ok && item < num_items; item += gridDim.x) {
-        const int kblocks = GROUPED ? decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC).kblocks
+      for (int item = unit; ok && item < num_items; item += units) {
+        const int kblocks = GROUPED ? decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank).kblocks
                                     : p.L / Cfg::BK;
         if (!mbar_wait_bounded(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
           ok = false;
@@ -269,7 +295,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           issued = true;
-          mma_commit(empty_bar(s));  // stage free once these MMAs have read it
+          if constexpr (PAIR)
+            mma_commit_mc(empty_bar(s), 0x3);  // both CTAs' producers learn the stage is read here
+          else
+            mma_commit(empty_bar(s));  // stage free once these MMAs have read it
           if (++s == STAGES) {
             s = 0;
             phase ^= 1;
@@ -304,10 +333,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t pol_c = policy_evict_first();  // C lines: add and move on
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int item = blockIdx.x; item < num_items; item += gridDim.x) {
+    for (int item = unit; item < num_items; item += units) {
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
-      const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED>(item, p, &tmA, &tmB, &tmC);
+      const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
       const int m0 = it.m0, n0 = it.n0, nt = it.nt;
       const CTarget* tg = it.tg;
       bool has_pos = false, has_neg = false;
@@ -388,30 +417,60 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+  if constexpr (PAIR) cluster_sync();  // no CTA leaves while its peer may still write to it
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
   static_assert(Cfg::B_BYTES == BN * 128, "B tile size");
+  static_assert(!PAIR || (!GROUPED && Cfg::B_MN && Cfg::NCHUNK % 2 == 0), "paired mode: bf16, single problem");
   int64_t items;
   if constexpr (GROUPED) {
     items = a.total_items;
     if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
   } else {
     if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
-    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM) * (a.L / BN);
+    if (PAIR && (a.L / kBM) % 2 != 0) return cudaErrorInvalidValue;
+    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM / (PAIR ? 2 : 1)) * (a.L / BN);
   }
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED>;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  const int grid = (int)(items < num_sms ? items : num_sms);
-  kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, *tmC, a);
-  count_launch();
-  return cudaGetLastError();
+  if constexpr (PAIR) {
+    if (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0); e != cudaSuccess)
+      cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = num_sms / 2;
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && active < clusters)
+      clusters = active;
+    cudaGetLastError();
+    if (items < clusters) clusters = (int)items;
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, kern, *tmA, *tmB, *tmC, a);
+    count_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+  } else {
+    const int grid = (int)(items < num_sms ? items : num_sms);
+    kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, *tmC, a);
+    count_launch();
+    return cudaGetLastError();
+  }
 }
 
 }  // namespace
@@ -423,6 +482,10 @@ int leaf_tc_smem_bytes(bool tf32, int bn) {
 
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
+  // bf16 with 256-wide tiles and an even number of tile rows: paired CTAs
+  // sharing each B tile through TMA multicast (unless disabled by the plan)
+  if (bn == 256 && !tf32 && a.pair && (a.L / kBM) % 2 == 0)
+    return launch_cfg<256, 2, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
   if (bn == 256) {
     return tf32 ? launch_cfg<256, 2, true, false>(a, tmA, tmB, tmC, num_sms, st)
                 : launch_cfg<256, 2, false, false>(a, tmA, tmB, tmC, num_sms, st);

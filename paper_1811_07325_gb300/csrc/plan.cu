@@ -361,6 +361,12 @@ stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   return STARK_OK;
 }
 
+stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
+  if (!p || enable < 0 || enable > 1) return STARK_EINVAL;
+  p->pair_mode = enable;
+  return STARK_OK;
+}
+
 stark_status stark_plan_check(stark_plan_t p, void* stream) {
   if (!p) return STARK_EINVAL;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
@@ -563,6 +569,7 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     CUtensorMap tmC;
     std::memset(&tmC, 0, sizeof(tmC));
     a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
+    a.pair = p->pair_mode;
     st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
     if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   } else {

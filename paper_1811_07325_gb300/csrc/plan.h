@@ -50,6 +50,7 @@ struct stark_plan_s {
   int* d_err = nullptr;
   uint64_t timeout_ns = stark::kDefaultTimeoutNs;
   int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics
+  int pair_mode = 1;     // 1: paired CTAs with multicast B tiles where the tiling allows
   CUtensorMap tmA;
   CUtensorMap tmB;
   // end-to-end staging (stark_mul_host / _async), allocated on first use:

@@ -101,6 +101,7 @@ struct LeafTcArgs {
   int* err;
   uint64_t timeout_ns;
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
+  int32_t pair;        // 1: paired CTAs (cluster of 2) share B tiles by multicast
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;

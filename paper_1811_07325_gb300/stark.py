@@ -64,6 +64,7 @@ _SIGS = {
     "stark_plan_operands": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _ci),
     "stark_plan_check": ([_vp, _vp], _ci),
     "stark_plan_set_combine": ([_vp, _ci], _ci),
+    "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
@@ -237,6 +238,10 @@ class Plan:
     def set_combine(self, mode: int):
         """0: TMA bulk reductions where possible (default), 1: vector atomics."""
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
+
+    def set_pairing(self, enable: bool):
+        """Paired CTAs sharing B tiles by multicast (default on where possible)."""
+        _check(_lib.stark_plan_set_pairing(self._h, 1 if enable else 0), "stark_plan_set_pairing")
 
     def check(self, stream=None):
         """Synchronise and raise on a device-side timeout."""

@@ -257,6 +257,29 @@ def test_split_combine_modes_agree(S, n, d):
     assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("n,d", [(2048, 1), (4096, 2), (1536, 0)])
+def test_paired_ctas_agree_with_single(S, n, d):
+    # clusters of two CTAs sharing B tiles by multicast vs one CTA per tile
+    A = synth.normal(n, 62, 0)
+    B = synth.normal(n, 62, 1)
+    rows = synth.sample_rows(n, 64, 62)
+    want = oracle.gemm_rows(A, B, rows)
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    out = []
+    for pair in (True, False):
+        with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
+            p.set_pairing(pair)
+            C = p.mul(dev(A), dev(B))
+            p.check()
+            got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+            out.append(got)
+            diff = got.astype(np.float64) - want
+            assert np.abs(diff).max() / (an * bn) <= 1e-6
+            rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+            assert rel <= SPLIT_BOUND["F32_SPLIT_BF16"] + 3 * (p.leaf / 16) * 2.0 ** -24
+    assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
+
+
 # ----------------------------------------------------------------- API paths
 def test_leaf_partition_sums_to_product(S):
     n, d = 300, 2
