@@ -320,6 +320,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tf32", action="store_true")
+    ap.add_argument("--pairing", action="store_true")
+    ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=600)
@@ -352,6 +354,10 @@ def main():
     B = B_h.cuda()
     C = torch.empty_like(A)
     plan = stark.Plan(n, d, dt)
+    if args.pairing:
+        plan.set_pairing(True)
+    if args.deep_pipeline >= 0:
+        plan.set_pipeline(bool(args.deep_pipeline))
     stream = torch.cuda.current_stream()
 
     def barrier():

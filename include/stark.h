@@ -151,12 +151,18 @@ STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, con
  * within fp32 rounding (the order of the additions into C differs). */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
-/* Leaf launch schedule on the 3xBF16 path: enable = 1 (default) runs CTA
- * pairs (thread-block clusters of 2) on vertically adjacent tiles that share
- * one B tile, fetched once and multicast to both, whenever the leaf side
- * allows (256-wide tiles, an even number of 128-row tiles); 0 runs single
+/* Leaf launch schedule on the 3xBF16 path: enable = 1 runs CTA pairs
+ * (thread-block clusters of 2) on vertically adjacent tiles that share one B
+ * tile, fetched once and multicast to both, whenever the leaf side allows
+ * (256-wide tiles, an even number of 128-row tiles); 0 (default) runs single
  * CTAs.  Results agree within fp32 rounding of the combine's order. */
 STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
+
+/* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1
+ * stages K = 32 per step in four 48 KB buffers (64-byte swizzle), 0 stages
+ * K = 64 in two 96 KB buffers (128-byte swizzle).  Same results up to the
+ * combine's addition order. */
+STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
 
 /* Synchronise the plan's last stream and report any device-side error
  * (STARK_ETIMEOUT) recorded by its kernels since the previous check; the

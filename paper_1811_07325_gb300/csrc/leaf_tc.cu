@@ -33,21 +33,23 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kThreads = 192;
 
-template <int BN, int STAGES, bool TF32>
+// RB: bytes of one swizzled smem row (128: K = 64 bf16 per stage; 64: K = 32
+// bf16 per stage, twice the stages in the same space).
+template <int BN, int STAGES, bool TF32, int RB = 128>
 struct TcCfg {
   static constexpr int ESZ = TF32 ? 4 : 2;
-  static constexpr int BK = 128 / ESZ;               // K per stage: one 128-byte A row
-  static constexpr int A_BYTES = kBM * 128;          // one operand half tile (K-major)
+  static constexpr int BK = RB / ESZ;                // K per stage: one swizzled A row
+  static constexpr int A_BYTES = kBM * RB;           // one operand half tile (K-major)
   static constexpr bool B_MN = !TF32;                // B operand MN-major (bf16) or K-major (tf32)
-  static constexpr int W = B_MN ? 128 / ESZ : BN;    // N elements per B TMA box
+  static constexpr int W = B_MN ? RB / ESZ : BN;     // N elements per B TMA box
   static constexpr int NCHUNK = BN / W;              // B boxes per half tile
-  static constexpr int CH_BYTES = B_MN ? BK * 128 : BN * 128;  // bytes per B box
-  static constexpr int B_BYTES = NCHUNK * CH_BYTES;  // == BN * 128
+  static constexpr int CH_BYTES = B_MN ? BK * RB : BN * RB;  // bytes per B box
+  static constexpr int B_BYTES = NCHUNK * CH_BYTES;  // == BN * RB
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int MMA_K = 32 / ESZ;             // K of one MMA (16 bf16 / 8 tf32)
-  static constexpr int KSTEPS = BK / MMA_K;          // 4 MMAs (x3) per stage
+  static constexpr int KSTEPS = BK / MMA_K;          // MMAs (x3) per stage
   static constexpr int A_KSTEP = 32;                 // bytes along a K-major row
-  static constexpr int B_KSTEP = B_MN ? MMA_K * 128 : 32;  // bytes per MMA K step in a B box
+  static constexpr int B_KSTEP = B_MN ? MMA_K * RB : 32;  // bytes per MMA K step in a B box
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
   static constexpr int EPI_BYTES = 4 * 2 * 4096;     // per epilogue warp: a +/- pair of 32x32 fp32 boxes
   static constexpr int BAR_BYTES = 8 * (2 * STAGES + 4) + 16;
@@ -122,11 +124,11 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
   return it;
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
-  using Cfg = TcCfg<BN, STAGES, TF32>;
+  using Cfg = TcCfg<BN, STAGES, TF32, RB>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -273,15 +275,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < Cfg::KSTEPS; ++k) {
             const uint32_t aoff = k * Cfg::A_KSTEP, boff = k * Cfg::B_KSTEP;
-            const uint64_t a_hi = smem_desc_k_sw128(st + aoff);
-            const uint64_t a_lo = smem_desc_k_sw128(st + Cfg::A_BYTES + aoff);
+            const uint64_t a_hi = smem_desc_k<RB>(st + aoff);
+            const uint64_t a_lo = smem_desc_k<RB>(st + Cfg::A_BYTES + aoff);
             uint64_t b_hi, b_lo;
             if constexpr (Cfg::B_MN) {
-              b_hi = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
-              b_lo = smem_desc_mn_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+              b_hi = smem_desc_mn<RB>(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+              b_lo = smem_desc_mn<RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
             } else {
-              b_hi = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + boff);
-              b_lo = smem_desc_k_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
+              b_hi = smem_desc_k<RB>(st + 2 * Cfg::A_BYTES + boff);
+              b_lo = smem_desc_k<RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
             }
             const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
             if constexpr (TF32) {
@@ -420,11 +422,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (PAIR) cluster_sync();  // no CTA leaves while its peer may still write to it
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
-  using Cfg = TcCfg<BN, STAGES, TF32>;
-  static_assert(Cfg::B_BYTES == BN * 128, "B tile size");
+  using Cfg = TcCfg<BN, STAGES, TF32, RB>;
+  static_assert(Cfg::B_BYTES == BN * RB, "B tile size");
   static_assert(!PAIR || (!GROUPED && Cfg::B_MN && Cfg::NCHUNK % 2 == 0), "paired mode: bf16, single problem");
   int64_t items;
   if constexpr (GROUPED) {
@@ -435,7 +437,7 @@ cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtens
     if (PAIR && (a.L / kBM) % 2 != 0) return cudaErrorInvalidValue;
     items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM / (PAIR ? 2 : 1)) * (a.L / BN);
   }
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR>;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
@@ -486,6 +488,9 @@ cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CU
   // sharing each B tile through TMA multicast (unless disabled by the plan)
   if (bn == 256 && !tf32 && a.pair && (a.L / kBM) % 2 == 0)
     return launch_cfg<256, 2, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
+  // bf16, 256-wide tiles, 64-byte rows: four 48 KB stages instead of two 96 KB
+  if (bn == 256 && !tf32 && a.row_bytes == 64)
+    return launch_cfg<256, 4, false, false, false, 64>(a, tmA, tmB, tmC, num_sms, st);
   if (bn == 256) {
     return tf32 ? launch_cfg<256, 2, true, false>(a, tmA, tmB, tmC, num_sms, st)
                 : launch_cfg<256, 2, false, false>(a, tmA, tmB, tmC, num_sms, st);

@@ -101,16 +101,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 128 bytes of a row x box_rows rows of one plane, 128-byte swizzle.  For
 // the K-major X planes a box is a 128-byte K slice of box_rows M rows; for
 // the MN-major Y planes it is a 128-byte N chunk of box_rows K rows.
-bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows) {
+bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows,
+                      int row_bytes) {
   auto fn = encode_fn();
-  if (!fn) return false;
+  if (!fn || (row_bytes != 128 && row_bytes != 64)) return false;
   const int esz = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(L * esz), (cuuint64_t)(L * L * esz)};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(row_bytes / esz), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
-                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -367,6 +369,12 @@ stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
   return STARK_OK;
 }
 
+stark_status stark_plan_set_pipeline(stark_plan_t p, int deep) {
+  if (!p || deep < 0 || deep > 1) return STARK_EINVAL;
+  p->deep_pipeline = deep;
+  return STARK_OK;
+}
+
 stark_status stark_plan_check(stark_plan_t p, void* stream) {
   if (!p) return STARK_EINVAL;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
@@ -570,7 +578,18 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     std::memset(&tmC, 0, sizeof(tmC));
     a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
     a.pair = p->pair_mode;
-    st = to_status(launch_leaf_tc(a, &p->tmA, &p->tmB, &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
+    a.row_bytes = 128;
+    if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256 && !p->pair_mode) {
+      a.row_bytes = 64;
+      if (!p->has_maps64) {
+        if (!make_tmap_planes(&p->tmA64, p->X, false, p->L, 2 * p->P, 128, 64) ||
+            !make_tmap_planes(&p->tmB64, p->Y, false, p->L, 2 * p->P, 32, 64))
+          return STARK_EUNSUPPORTED;
+        p->has_maps64 = true;
+      }
+    }
+    st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA, a.row_bytes == 64 ? &p->tmB64 : &p->tmB,
+                                  &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
     if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   } else {
     LeafCcArgs a{};

@@ -50,7 +50,10 @@ struct stark_plan_s {
   int* d_err = nullptr;
   uint64_t timeout_ns = stark::kDefaultTimeoutNs;
   int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics
-  int pair_mode = 1;     // 1: paired CTAs with multicast B tiles where the tiling allows
+  int pair_mode = 0;     // 1: paired CTAs with multicast B tiles where the tiling allows
+  int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
+  CUtensorMap tmA64, tmB64;  // operand maps for the 64-byte-row schedule
+  bool has_maps64 = false;
   CUtensorMap tmA;
   CUtensorMap tmB;
   // end-to-end staging (stark_mul_host / _async), allocated on first use:

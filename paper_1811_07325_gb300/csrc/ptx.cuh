@@ -254,6 +254,29 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 //   bits 46-47 descriptor version (1 on sm_100 family)
 //   bits 49-51 base offset (0: atoms are 1024-byte aligned)
 //   bits 61-63 swizzle mode (2 = 128-byte swizzle)
+// Same for a swizzle of RB bytes per row (128 or 64): 8-row atoms of 8*RB
+// bytes; swizzle code 2 (128 B) or 4 (64 B).
+template <int RB>
+__device__ __forceinline__ uint64_t smem_desc_k(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * RB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
+  return d;
+}
+template <int RB>
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t chunk_stride_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((chunk_stride_bytes >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((8 * RB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
+  return d;
+}
+
 __device__ __forceinline__ uint64_t smem_desc_k_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);

@@ -102,6 +102,7 @@ struct LeafTcArgs {
   uint64_t timeout_ns;
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
   int32_t pair;        // 1: paired CTAs (cluster of 2) share B tiles by multicast
+  int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;
@@ -135,7 +136,8 @@ cudaError_t launch_wait_selftest(int* err, uint64_t timeout_ns, cudaStream_t s);
 void count_launch(int k = 1);
 int device_sm_count();
 bool device_is_sm100_family();
-bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows);
+bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows,
+                      int row_bytes = 128);
 // n x n fp32 row-major C with row pitch ld elements, 32 x 32 boxes,
 // 128-byte swizzle (reduction target).  Needs ld % 4 == 0 and a 16-byte
 // aligned base.

@@ -65,6 +65,7 @@ _SIGS = {
     "stark_plan_check": ([_vp, _vp], _ci),
     "stark_plan_set_combine": ([_vp, _ci], _ci),
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
+    "stark_plan_set_pipeline": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
@@ -242,6 +243,10 @@ class Plan:
     def set_pairing(self, enable: bool):
         """Paired CTAs sharing B tiles by multicast (default on where possible)."""
         _check(_lib.stark_plan_set_pairing(self._h, 1 if enable else 0), "stark_plan_set_pairing")
+
+    def set_pipeline(self, deep: bool):
+        """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
+        _check(_lib.stark_plan_set_pipeline(self._h, 1 if deep else 0), "stark_plan_set_pipeline")
 
     def check(self, stream=None):
         """Synchronise and raise on a device-side timeout."""

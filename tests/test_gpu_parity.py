@@ -258,17 +258,19 @@ def test_split_combine_modes_agree(S, n, d):
 
 
 @pytest.mark.parametrize("n,d", [(2048, 1), (4096, 2), (1536, 0)])
-def test_paired_ctas_agree_with_single(S, n, d):
-    # clusters of two CTAs sharing B tiles by multicast vs one CTA per tile
+def test_leaf_schedules_agree(S, n, d):
+    # clusters of two CTAs sharing B tiles by multicast, one CTA per tile, and
+    # the four-stage 64-byte-row pipeline: same products
     A = synth.normal(n, 62, 0)
     B = synth.normal(n, 62, 1)
     rows = synth.sample_rows(n, 64, 62)
     want = oracle.gemm_rows(A, B, rows)
     an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
     out = []
-    for pair in (True, False):
+    for pair, deep in ((True, False), (False, False), (False, True)):
         with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
             p.set_pairing(pair)
+            p.set_pipeline(deep)
             C = p.mul(dev(A), dev(B))
             p.check()
             got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
@@ -278,6 +280,7 @@ def test_paired_ctas_agree_with_single(S, n, d):
             rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
             assert rel <= SPLIT_BOUND["F32_SPLIT_BF16"] + 3 * (p.leaf / 16) * 2.0 ** -24
     assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
+    assert np.abs(out[2] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
 
 # ----------------------------------------------------------------- API paths
