@@ -164,9 +164,25 @@ STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
  * combine's addition order. */
 STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
 
+/* Exact integer leaves on the tensor cores for an I64 plan whose inputs
+ * satisfy |A_ij|, |B_ij| <= max_abs (the integer path of the benchmark spec;
+ * the paper itself is FP64-only).  A depth-d leaf operand is a sum of 2^d
+ * inputs, so with b = max_abs * 2^d the plan multiplies in bf16 (exact for
+ * integers up to 256) with fp32 accumulation (exact while every partial sum
+ * stays within 2^24) whenever b <= 256 and L * b^2 <= 2^24, and combines
+ * into int64: bit-identical to the int64 CUDA-core path.  The divide checks
+ * every operand on the device; a value beyond the range makes the next
+ * stark_plan_check return STARK_EINVAL (the product is then invalid).
+ * max_abs = 0 returns to the CUDA-core path.  Errors: EINVAL (not an I64
+ * plan, max_abs < 0), EUNSUPPORTED (the bound does not give exactness at
+ * this depth / leaf side; the plan keeps the CUDA-core path). */
+STARK_API stark_status stark_plan_set_input_bound(stark_plan_t plan, int64_t max_abs);
+
 /* Synchronise the plan's last stream and report any device-side error
- * (STARK_ETIMEOUT) recorded by its kernels since the previous check; the
- * error word is cleared. */
+ * recorded by its kernels since the previous check: STARK_ETIMEOUT for a
+ * bounded wait that gave up, STARK_EINVAL for an integer operand outside the
+ * bound declared with stark_plan_set_input_bound.  The error word is
+ * cleared. */
 STARK_API stark_status stark_plan_check(stark_plan_t plan, void *stream);
 
 /* Per-phase device timing with CUDA events recorded on the product's own

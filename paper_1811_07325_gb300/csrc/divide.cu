@@ -20,6 +20,7 @@
 // Padding to n_pad is virtual: reads beyond n return zero.
 #include <cuda_bf16.h>
 
+#include "ptx.cuh"
 #include "stark_internal.h"
 
 namespace stark {
@@ -101,10 +102,23 @@ struct Emitter {
   void* lo;
   int64_t plane_elems;  // L * L
   int64_t offset;       // row * L + col of this thread's first element
+  int* range_flag;
 
   __device__ __forceinline__ void operator()(int leaf, const Vec<Acc, VEC>& x) const {
     const int64_t at = (int64_t)leaf * plane_elems + offset;
-    if constexpr (OUT == kOutSplitBf16) {
+    if constexpr (OUT == kOutBf16Exact) {
+      // integer operand sums, exact in bf16 while |v| <= 256 (8 significant bits)
+      __nv_bfloat16 h[VEC];
+      bool bad = false;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const long long v = (long long)x.v[e];
+        bad |= (v > 256 || v < -256);
+        h[e] = __float2bfloat16_rn((float)v);
+      }
+      if (bad) record_error(range_flag, kDevIntRange);
+      store_vec(reinterpret_cast<__nv_bfloat16*>(hi) + at, h);
+    } else if constexpr (OUT == kOutSplitBf16) {
       __nv_bfloat16 h[VEC], l[VEC];
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
   const int64_t i = pos / per_row;
   const int64_t j = (pos % per_row) * VEC;
   const Loader<Tin, VEC> ld{static_cast<const Tin*>(a.X), a.n, vec_ok != 0};
-  const Emitter<OUT, Tin, VEC> emit{a.out_hi, a.out_lo, a.L * a.L, i * a.L + j};
+  const Emitter<OUT, Tin, VEC> emit{a.out_hi, a.out_lo, a.L * a.L, i * a.L + j, a.range_flag};
   const int64_t npad = a.npad;
 
   auto leaf_block = [&](const int* dig, int prefix) {
@@ -322,6 +336,9 @@ cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, O
     return side == 0 ? by_depth<double, kOutPlain, 0>(a, depth, st) : by_depth<double, kOutPlain, 1>(a, depth, st);
   if (in == kInI64 && out == kOutPlain)
     return side == 0 ? by_depth<int64_t, kOutPlain, 0>(a, depth, st) : by_depth<int64_t, kOutPlain, 1>(a, depth, st);
+  if (in == kInI64 && out == kOutBf16Exact)
+    return side == 0 ? by_depth<int64_t, kOutBf16Exact, 0>(a, depth, st)
+                     : by_depth<int64_t, kOutBf16Exact, 1>(a, depth, st);
   return cudaErrorInvalidValue;
 }
 

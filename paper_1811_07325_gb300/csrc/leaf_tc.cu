@@ -35,7 +35,9 @@ constexpr int kThreads = 192;
 
 // RB: bytes of one swizzled smem row (128: K = 64 bf16 per stage; 64: K = 32
 // bf16 per stage, twice the stages in the same space).
-template <int BN, int STAGES, bool TF32, int RB = 128>
+// INT1: one exact bf16 product per K step (integer leaf operands), no lo
+// planes, int64 combine.
+template <int BN, int STAGES, bool TF32, int RB = 128, bool INT1 = false>
 struct TcCfg {
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int BK = RB / ESZ;                // K per stage: one swizzled A row
@@ -45,7 +47,8 @@ struct TcCfg {
   static constexpr int NCHUNK = BN / W;              // B boxes per half tile
   static constexpr int CH_BYTES = B_MN ? BK * RB : BN * RB;  // bytes per B box
   static constexpr int B_BYTES = NCHUNK * CH_BYTES;  // == BN * RB
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int NHALF = INT1 ? 1 : 2;         // operand planes per side (hi, lo)
+  static constexpr int STAGE_BYTES = NHALF * (A_BYTES + B_BYTES);
   static constexpr int MMA_K = 32 / ESZ;             // K of one MMA (16 bf16 / 8 tf32)
   static constexpr int KSTEPS = BK / MMA_K;          // MMAs (x3) per stage
   static constexpr int A_KSTEP = 32;                 // bytes along a K-major row
@@ -124,11 +127,12 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
   return it;
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB, bool INT1>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
-  using Cfg = TcCfg<BN, STAGES, TF32, RB>;
+  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1>;
+  static_assert(!INT1 || (!TF32 && !GROUPED && !PAIR), "integer mode: bf16, single problem");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -202,27 +206,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
           const int k0 = kb * Cfg::BK;
           tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol_a);
-          tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol_a);
+          if constexpr (!INT1) tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol_a);
           if constexpr (PAIR) {
             // this CTA fetches its half of the B chunks for both CTAs
 #pragma unroll
             for (int c = (int)cta_rank * (Cfg::NCHUNK / 2); c < ((int)cta_rank + 1) * (Cfg::NCHUNK / 2); ++c) {
-              tma_load_3d_mc(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf,
+              tma_load_3d_mc(st + Cfg::NHALF * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf,
                              full_bar(s), 0x3, pol_b);
-              tma_load_3d_mc(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
+              tma_load_3d_mc(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
                              it.P + leaf, full_bar(s), 0x3, pol_b);
             }
           } else if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
-              tma_load_3d(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
+              tma_load_3d(st + Cfg::NHALF * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
                           pol_b);
-              tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
-                          it.P + leaf, full_bar(s), pol_b);
+              if constexpr (!INT1)
+                tma_load_3d(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W,
+                            k0, it.P + leaf, full_bar(s), pol_b);
             }
           } else {
-            tma_load_3d(st + 2 * Cfg::A_BYTES, it.tB, k0, n0, leaf, full_bar(s), pol_b);
-            tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, n0, it.P + leaf, full_bar(s), pol_b);
+            tma_load_3d(st + Cfg::NHALF * Cfg::A_BYTES, it.tB, k0, n0, leaf, full_bar(s), pol_b);
+            tma_load_3d(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, n0, it.P + leaf, full_bar(s), pol_b);
           }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
@@ -279,14 +284,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t a_lo = smem_desc_k<RB>(st + Cfg::A_BYTES + aoff);
             uint64_t b_hi, b_lo;
             if constexpr (Cfg::B_MN) {
-              b_hi = smem_desc_mn<RB>(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
-              b_lo = smem_desc_mn<RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+              b_hi = smem_desc_mn<RB>(st + Cfg::NHALF * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+              b_lo = smem_desc_mn<RB>(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
             } else {
-              b_hi = smem_desc_k<RB>(st + 2 * Cfg::A_BYTES + boff);
-              b_lo = smem_desc_k<RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
+              b_hi = smem_desc_k<RB>(st + Cfg::NHALF * Cfg::A_BYTES + boff);
+              b_lo = smem_desc_k<RB>(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + boff);
             }
             const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
-            if constexpr (TF32) {
+            if constexpr (INT1) {
+              mma_f16(d_tmem, a_hi, b_hi, Cfg::IDESC, first);
+            } else if constexpr (TF32) {
               mma_tf32(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
               mma_tf32(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
               mma_tf32(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
@@ -349,7 +356,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + chunk * 32), r);
         tmem_ld_wait();
-        if (it.use_tma_c) {
+        if constexpr (INT1) {
+          // exact integers held in fp32: signed 64-bit adds into C (wrap mod 2^64)
+          unsigned long long* Ci = reinterpret_cast<unsigned long long*>(it.C);
+#pragma unroll 1
+          for (int t = 0; t < nt; ++t) {
+            const CTarget c = tg[t];
+            const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
+            const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
+            if (grow >= it.n || gcol >= it.n) continue;
+            unsigned long long* dst = Ci + grow * it.ldc + gcol;
+            const int64_t lim = it.n - gcol;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const long long v = __float2ll_rn(__uint_as_float(r[j]));
+              if (j < lim && v != 0) atomicAdd(dst + j, (unsigned long long)(c.sign > 0 ? v : -v));
+            }
+          }
+        } else if (it.use_tma_c) {
           if (lane == 0) bulk_wait_group_read<0>();  // the previous boxes have been read
           __syncwarp();
 #pragma unroll
@@ -422,10 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (PAIR) cluster_sync();  // no CTA leaves while its peer may still write to it
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128, bool INT1 = false>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
-  using Cfg = TcCfg<BN, STAGES, TF32, RB>;
+  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1>;
   static_assert(Cfg::B_BYTES == BN * RB, "B tile size");
   static_assert(!PAIR || (!GROUPED && Cfg::B_MN && Cfg::NCHUNK % 2 == 0), "paired mode: bf16, single problem");
   int64_t items;
@@ -437,7 +461,7 @@ cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtens
     if (PAIR && (a.L / kBM) % 2 != 0) return cudaErrorInvalidValue;
     items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM / (PAIR ? 2 : 1)) * (a.L / BN);
   }
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB>;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB, INT1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
@@ -499,6 +523,15 @@ cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CU
     return tf32 ? launch_cfg<128, 3, true, false>(a, tmA, tmB, tmC, num_sms, st)
                 : launch_cfg<128, 3, false, false>(a, tmA, tmB, tmC, num_sms, st);
   }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int bn,
+                               int num_sms, cudaStream_t st) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  if (bn == 256) return launch_cfg<256, 4, false, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
+  if (bn == 128) return launch_cfg<128, 6, false, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
   return cudaErrorInvalidValue;
 }
 

@@ -363,6 +363,27 @@ stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   return STARK_OK;
 }
 
+stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
+  if (!p || p->dt != STARK_I64 || max_abs < 0) return STARK_EINVAL;
+  if (max_abs == 0) {
+    p->int_tc = false;
+    p->int_bound = 0;
+    return STARK_OK;
+  }
+  // leaf operands are sums of 2^depth inputs: exact in bf16 up to 256, and
+  // every fp32 partial sum of a leaf product exact up to 2^24
+  const double xb = (double)max_abs * (double)((int64_t)1 << p->depth);
+  if (xb > 256.0 || (double)p->L * xb * xb > 16777216.0 || p->L % 128 != 0 || !device_is_sm100_family())
+    return STARK_EUNSUPPORTED;
+  p->int_bn = (p->L % 256 == 0) ? 256 : 128;
+  if (!make_tmap_planes(&p->tmAi, p->X, false, p->L, p->P, 128) ||
+      !make_tmap_planes(&p->tmBi, p->Y, false, p->L, p->P, 64))
+    return STARK_EUNSUPPORTED;
+  p->int_bound = max_abs;
+  p->int_tc = true;
+  return STARK_OK;
+}
+
 stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
   if (!p || enable < 0 || enable > 1) return STARK_EINVAL;
   p->pair_mode = enable;
@@ -382,7 +403,7 @@ stark_status stark_plan_check(stark_plan_t p, void* stream) {
   if (cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STARK_ECUDA;
   if (e != 0) {
     cudaMemset(p->d_err, 0, sizeof(int));
-    return STARK_ETIMEOUT;
+    return e == kDevIntRange ? STARK_EINVAL : STARK_ETIMEOUT;
   }
   return STARK_OK;
 }
@@ -529,10 +550,11 @@ static stark_status to_status(cudaError_t e) {
 
 stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s) {
   // divide phase: every leaf operand of A and of B
-  DivideArgs da{A, p->n, p->npad, p->L, p->X, nullptr};
-  DivideArgs db{B, p->n, p->npad, p->L, p->Y, nullptr};
+  DivideArgs da{A, p->n, p->npad, p->L, p->X, nullptr, p->d_err};
+  DivideArgs db{B, p->n, p->npad, p->L, p->Y, nullptr, p->d_err};
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
+  if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
   if (p->is_tc) {
     const int64_t half = p->P * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
     da.out_lo = static_cast<char*>(p->X) + half;
@@ -591,6 +613,21 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA, a.row_bytes == 64 ? &p->tmB64 : &p->tmB,
                                   &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
     if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
+  } else if (p->int_tc) {
+    LeafTcArgs a{};
+    a.P = (int32_t)p->P;
+    a.L = (int32_t)p->L;
+    a.leaf_begin = (int32_t)lb;
+    a.leaf_end = (int32_t)le;
+    a.ctab = p->d_ctab;
+    a.ccount = p->d_ccount;
+    a.maxT = p->maxT;
+    a.C = static_cast<float*>(C);  // int64 C, reinterpreted by the integer epilogue
+    a.ldc = p->n;
+    a.n = p->n;
+    a.err = p->d_err;
+    a.timeout_ns = p->timeout_ns;
+    st = to_status(launch_leaf_tc_int(a, &p->tmAi, &p->tmBi, p->int_bn, p->num_sms, s));
   } else {
     LeafCcArgs a{};
     a.P = (int32_t)p->P;

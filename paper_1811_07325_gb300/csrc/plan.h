@@ -54,6 +54,11 @@ struct stark_plan_s {
   int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
   CUtensorMap tmA64, tmB64;  // operand maps for the 64-byte-row schedule
   bool has_maps64 = false;
+  // I64 with a declared input bound: exact bf16 tensor-core leaves
+  int64_t int_bound = 0;
+  bool int_tc = false;
+  int int_bn = 128;
+  CUtensorMap tmAi, tmBi;
   CUtensorMap tmA;
   CUtensorMap tmB;
   // end-to-end staging (stark_mul_host / _async), allocated on first use:

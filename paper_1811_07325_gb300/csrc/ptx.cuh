@@ -20,6 +20,7 @@ enum DeviceError : int {
   kDevTimeoutAccEmpty = 4,  // MMA issuer waited too long for a free accumulator
   kDevTimeoutTest = 5,      // the self-test wait on a flag that nobody sets
   kDevBadConfig = 6,        // launch parameters inconsistent with the kernel
+  kDevIntRange = 7,         // an integer leaf operand exceeded the declared exact range
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -53,7 +53,7 @@ void build_quadrant_table(int depth, int side, std::vector<int32_t>& count, std:
 void quadrant_offsets(int depth, int64_t npad, int32_t q, int64_t* row, int64_t* col);
 
 // ------------------------------------------------------------------ launches
-enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2 };
+enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2, kOutBf16Exact = 3 };
 enum InType { kInF32 = 0, kInF64 = 1, kInI64 = 2 };
 
 struct DivideArgs {
@@ -63,6 +63,7 @@ struct DivideArgs {
   int64_t L;          // leaf side = npad >> depth
   void* out_hi;       // planes [P][L][L] (split: hi part; plain: the value)
   void* out_lo;       // planes [P][L][L] (split: lo part; plain: unused)
+  int* range_flag;    // bf16-exact output: set to kDevIntRange when |value| > 256
 };
 
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
@@ -113,6 +114,10 @@ struct LeafTcArgs {
 // 3xBF16 / 3xTF32 leaf GEMMs with the combine fused in the epilogue.
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t s);
+// Exact integer leaves: one bf16 product per K step over [P][L][L] bf16
+// planes holding integers, combined into an int64 C (a.C reinterpreted).
+cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int bn,
+                               int num_sms, cudaStream_t s);
 // Grouped launch over a.groups (tensor maps taken from the descriptors).
 cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t s);
 int leaf_tc_smem_bytes(bool tf32, int bn);

@@ -66,6 +66,7 @@ _SIGS = {
     "stark_plan_set_combine": ([_vp, _ci], _ci),
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_pipeline": ([_vp, _ci], _ci),
+    "stark_plan_set_input_bound": ([_vp, _i64], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
@@ -247,6 +248,10 @@ class Plan:
     def set_pipeline(self, deep: bool):
         """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
         _check(_lib.stark_plan_set_pipeline(self._h, 1 if deep else 0), "stark_plan_set_pipeline")
+
+    def set_input_bound(self, max_abs: int):
+        """I64 plans: inputs bounded by max_abs run as exact bf16 tensor-core products."""
+        _check(_lib.stark_plan_set_input_bound(self._h, int(max_abs)), "stark_plan_set_input_bound")
 
     def check(self, stream=None):
         """Synchronise and raise on a device-side timeout."""

@@ -71,6 +71,47 @@ def test_int64_bit_exact(S, n, depths):
             assert np.array_equal(C.cpu().numpy(), want), d
 
 
+@pytest.mark.parametrize("n,depths", [(1000, [1, 2, 3]), (512, [0, 1, 2]), (2048, [1, 2, 3, 4])])
+def test_int64_tensor_core_exact(S, n, depths):
+    # bounded integers on the bf16 tensor cores: bit-identical to the oracle
+    A = synth.integers(n, 200 + n, 0, -16, 16)
+    B = synth.integers(n, 200 + n, 1, -16, 16)
+    want = oracle.gemm_classical(A, B)
+    dA, dB = dev(A), dev(B)
+    for d in depths:
+        with S.Plan(n, d, S.DType.I64) as p:
+            p.set_input_bound(16)
+            C = p.mul(dA, dB)
+            p.check()
+            assert np.array_equal(C.cpu().numpy(), want), d
+
+
+def test_int64_tensor_core_bound_checks(S):
+    n = 512
+    with S.Plan(n, 2, S.DType.I64) as p:
+        with pytest.raises(S.StarkError) as e:
+            p.set_input_bound(200)  # 200 * 4 > 256: not exact at depth 2
+        assert e.value.status == S.Status.EUNSUPPORTED
+        p.set_input_bound(16)
+        # an input beyond the declared bound is reported, not silently wrong
+        A = synth.integers(n, 9, 0, -16, 16)
+        A[3, 5] = 1000
+        B = synth.integers(n, 9, 1, -16, 16)
+        p.mul(dev(A), dev(B))
+        with pytest.raises(S.StarkError) as e:
+            p.check()
+        assert e.value.status == S.Status.EINVAL
+        # within the bound again: exact
+        A[3, 5] = 7
+        C = p.mul(dev(A), dev(B))
+        p.check()
+        assert np.array_equal(C.cpu().numpy(), oracle.gemm_classical(A, B))
+        p.set_input_bound(0)  # back to the CUDA-core path
+        C = p.mul(dev(A), dev(B))
+        p.check()
+        assert np.array_equal(C.cpu().numpy(), oracle.gemm_classical(A, B))
+
+
 def test_int64_wraps_modulo_2_64(S):
     n = 130
     A = synth.integers(n, 5, 0, -2**63, 2**63 - 1)
