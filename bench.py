@@ -321,6 +321,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tf32", action="store_true")
     ap.add_argument("--pairing", action="store_true")
+    ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -356,6 +357,8 @@ def main():
     plan = stark.Plan(n, d, dt)
     if args.pairing:
         plan.set_pairing(True)
+    if args.combine:
+        plan.set_combine(args.combine)
     if args.deep_pipeline >= 0:
         plan.set_pipeline(bool(args.deep_pipeline))
     stream = torch.cuda.current_stream()

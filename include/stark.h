@@ -144,11 +144,17 @@ STARK_API stark_status stark_mul_leaves(stark_plan_t plan, const void *A, const 
 STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, const void *B, void *stream, const void **X,
                                  const void **Y);
 
-/* How the fused combine adds leaf tiles into C on the tensor-core dtypes:
- * mode 0 (default) uses TMA bulk add-reductions of 32 x 32 boxes whenever C
- * is addressable by TMA (16-byte aligned, n a multiple of 4) and signed
- * vector atomics otherwise; mode 1 always uses the atomics.  Results agree
- * within fp32 rounding (the order of the additions into C differs). */
+/* How the combine (Alg. 5) adds leaf tiles into C on the tensor-core dtypes:
+ * mode 0 (default) fuses it into the leaf epilogue with TMA bulk
+ * add-reductions of 32 x 32 boxes (through an aligned staging copy of C when
+ * n is not a multiple of 4); mode 1 fuses it with signed vector atomics;
+ * mode 2 is deterministic: the leaf epilogue stores every product M_l
+ * (allocating [leaves][L][L] fp32 planes) and a separate pass writes each C
+ * element once as its signed sum in ascending leaf order, so results are
+ * bitwise reproducible run to run (depth <= 3; stark_mul_leaves keeps the
+ * fused path).  Modes 0 and 1 agree with mode 2 within fp32 rounding (the
+ * order of the additions differs).  Errors: EINVAL, EUNSUPPORTED (mode 2 on
+ * an fp64/int64 plan or depth > 3), ENOMEM. */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
 /* Leaf launch schedule on the 3xBF16 path: enable = 1 runs CTA pairs

@@ -373,6 +373,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (j < lim && v != 0) atomicAdd(dst + j, (unsigned long long)(c.sign > 0 ? v : -v));
             }
           }
+        } else if (p.store_m) {
+          // unfused, deterministic combine: this leaf's tile goes to its M
+          // plane (tmC maps the M planes here); the combine kernel adds later
+          if (lane == 0) bulk_wait_group_read<0>();
+          __syncwarp();
+          const uint32_t row_addr = ebuf + (uint32_t)lane * 128u;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[4 * c]), "r"(r[4 * c + 1]),
+                         "r"(r[4 * c + 2]), "r"(r[4 * c + 3])
+                         : "memory");
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_3d(it.tC, n0 + chunk * 32, m0 + quarter * 32, it.leaf - p.leaf_begin, ebuf);
+            bulk_commit_group();
+          }
         } else if (it.use_tma_c) {
           if (lane == 0) bulk_wait_group_read<0>();  // the previous boxes have been read
           __syncwarp();

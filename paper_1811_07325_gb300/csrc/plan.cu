@@ -117,6 +117,18 @@ bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t 
   return r == CUDA_SUCCESS;
 }
 
+bool make_tmap_mplanes(CUtensorMap* m, void* base, int64_t L, int64_t planes) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(L * 4), (cuuint64_t)(L * L * 4)};
+  cuuint32_t box[3] = {32, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool make_tmap_c(CUtensorMap* m, void* C, int64_t n, int64_t ld) {
   auto fn = encode_fn();
   if (!fn || n <= 0 || ld < n || (ld % 4) != 0 || (reinterpret_cast<uintptr_t>(C) & 15) != 0) return false;
@@ -358,7 +370,20 @@ stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* 
 }
 
 stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
-  if (!p || mode < 0 || mode > 1) return STARK_EINVAL;
+  if (!p || mode < 0 || mode > 2) return STARK_EINVAL;
+  if (mode == 2) {
+    if (!p->is_tc || p->depth > 3) return STARK_EUNSUPPORTED;
+    if (!p->m_planes && p->n > 0) {
+      const size_t bytes = (size_t)p->P * p->L * p->L * sizeof(float);
+      if (cudaMalloc(&p->m_planes, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->m_planes = nullptr;
+        return STARK_ENOMEM;
+      }
+      p->ws_bytes += (int64_t)bytes;
+      if (!make_tmap_mplanes(&p->tmM, p->m_planes, p->L, p->P)) return STARK_EUNSUPPORTED;
+    }
+  }
   p->combine_mode = mode;
   return STARK_OK;
 }
@@ -536,6 +561,7 @@ void plan_release(stark_plan_s* p) {
     for (cudaEvent_t e : {p->ev_in[i], p->ev_comp[i], p->ev_out[i]})
       if (e) cudaEventDestroy(e);
   cudaFree(p->cstage);
+  cudaFree(p->m_planes);
   for (auto e : p->ev)
     if (e) cudaEventDestroy(e);
   p->ev.clear();
@@ -590,7 +616,8 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     a.ctab = p->d_ctab;
     a.ccount = p->d_ccount;
     a.maxT = p->maxT;
-    const bool staged = plan_uses_cstage(p, C);
+    const bool deterministic = p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P;
+    const bool staged = !deterministic && plan_uses_cstage(p, C);
     a.C = static_cast<float*>(staged ? p->cstage : C);
     a.ldc = staged ? staged_ld(p->n) : p->n;
     a.n = p->n;
@@ -598,10 +625,15 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     a.timeout_ns = p->timeout_ns;
     CUtensorMap tmC;
     std::memset(&tmC, 0, sizeof(tmC));
-    a.use_tma_c = (p->combine_mode != 1 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
-    a.pair = p->pair_mode;
+    a.use_tma_c = (p->combine_mode == 0 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
+    if (deterministic) {
+      a.store_m = 1;
+      a.use_tma_c = 0;
+      tmC = p->tmM;
+    }
+    a.pair = deterministic ? 0 : p->pair_mode;
     a.row_bytes = 128;
-    if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256 && !p->pair_mode) {
+    if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256 && !a.pair) {
       a.row_bytes = 64;
       if (!p->has_maps64) {
         if (!make_tmap_planes(&p->tmA64, p->X, false, p->L, 2 * p->P, 128, 64) ||
@@ -613,6 +645,9 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA, a.row_bytes == 64 ? &p->tmB64 : &p->tmB,
                                   &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
     if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
+    if (st == STARK_OK && deterministic)
+      st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, p->n,
+                                    static_cast<float*>(C), p->n, s));
   } else if (p->int_tc) {
     LeafTcArgs a{};
     a.P = (int32_t)p->P;
@@ -658,7 +693,9 @@ stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, in
     ++p->timing_used;
     p->timing_active = true;
   }
-  if (p->is_tc && plan_uses_cstage(p, C)) {
+  if (p->is_tc && p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P) {
+    // deterministic combine writes every element of C: nothing to clear
+  } else if (p->is_tc && plan_uses_cstage(p, C)) {
     if (cudaMemsetAsync(p->cstage, 0, (size_t)p->n * staged_ld(p->n) * 4, s) != cudaSuccess)
       return to_status(cudaGetLastError());
   } else if (cudaMemsetAsync(C, 0, (size_t)p->n * p->n * p->esz, s) != cudaSuccess) {

@@ -49,7 +49,10 @@ struct stark_plan_s {
   int32_t maxT = 1;
   int* d_err = nullptr;
   uint64_t timeout_ns = stark::kDefaultTimeoutNs;
-  int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics
+  int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics,
+                         // 2: deterministic (store M planes, ordered combine pass)
+  void* m_planes = nullptr;  // [P][L][L] fp32 leaf products (combine mode 2)
+  CUtensorMap tmM;
   int pair_mode = 0;     // 1: paired CTAs with multicast B tiles where the tiling allows
   int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
   CUtensorMap tmA64, tmB64;  // operand maps for the 64-byte-row schedule

@@ -69,6 +69,12 @@ struct DivideArgs {
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
+// Deterministic combine of stored leaf products: C_q = sum over leaves l
+// (ascending) of W_d[q, l] * M_l, every element written once.  M planes are
+// [leaves][L][L] fp32 for leaves [0, P); depth <= 3.
+cudaError_t launch_combine(const float* M, int depth, int64_t L, int64_t npad, int64_t n, float* C, int64_t ldc,
+                           cudaStream_t s);
+bool make_tmap_mplanes(CUtensorMap* m, void* base, int64_t L, int64_t planes);
 // In-place transpose of `count` square L x L fp32 planes.
 cudaError_t launch_transpose_planes(float* planes, int64_t L, int64_t count, cudaStream_t s);
 
@@ -104,6 +110,7 @@ struct LeafTcArgs {
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
   int32_t pair;        // 1: paired CTAs (cluster of 2) share B tiles by multicast
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
+  int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;

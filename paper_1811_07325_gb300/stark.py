@@ -238,7 +238,8 @@ class Plan:
         return X, Y
 
     def set_combine(self, mode: int):
-        """0: TMA bulk reductions where possible (default), 1: vector atomics."""
+        """0: fused, TMA bulk reductions (default); 1: fused, vector atomics;
+        2: deterministic (stored leaf products, ordered combine pass)."""
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
 
     def set_pairing(self, enable: bool):

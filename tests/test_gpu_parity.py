@@ -298,6 +298,27 @@ def test_split_combine_modes_agree(S, n, d):
     assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("n,d,dtype", [(1024, 2, "F32_SPLIT_BF16"), (1001, 3, "F32_SPLIT_BF16"),
+                                       (777, 1, "F32_SPLIT_TF32"), (2048, 0, "F32_SPLIT_BF16")])
+def test_deterministic_combine_is_bitwise_reproducible(S, n, d, dtype):
+    A = synth.normal(n, 63, 0)
+    B = synth.normal(n, 63, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        p.set_combine(2)
+        dA, dB = dev(A), dev(B)
+        C1 = p.mul(dA, dB).cpu().numpy()
+        C2 = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        L = p.leaf
+        p.set_combine(0)
+        Cf = p.mul(dA, dB).cpu().numpy()
+    assert np.array_equal(C1.view(np.uint32), C2.view(np.uint32))  # bit for bit
+    check_split(C1, want, an, bn, dtype, L=L)
+    assert np.abs(C1 - Cf).max() <= 1e-5 * np.abs(want).max()  # same products, other order
+
+
 @pytest.mark.parametrize("n,d", [(2048, 1), (4096, 2), (1536, 0)])
 def test_leaf_schedules_agree(S, n, d):
     # clusters of two CTAs sharing B tiles by multicast, one CTA per tile, and
