@@ -491,6 +491,28 @@ def main():
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
 
+    deterministic = None
+    if rank == 0 and not args.no_tf32 and args.combine == 0:
+        # the same product with the deterministic (unfused, ordered) combine
+        plan.set_combine(2)
+        for _ in range(2):
+            plan.mul(A, B, C)
+        plan.check()
+        plan.set_timing(10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            plan.mul(A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        msd = e0.elapsed_time(e1) / 10
+        deterministic = {"value": flops / (msd * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": msd,
+                         "phases_ms": plan.phase_ms(),
+                         "note": "leaf epilogue stores M planes, ordered combine pass; bitwise reproducible"}
+        plan.set_timing(0)
+        plan.set_combine(0)
+
     tf32 = None
     if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
         # the same product with 3xTF32 leaves, for comparison
@@ -546,7 +568,8 @@ def main():
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
-               "error_vs_fp64": error, "comparators": comparators, "tf32": tf32, "batch": batch, "serve": serve,
+               "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32,
+               "batch": batch, "serve": serve,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     plan.close()
