@@ -547,6 +547,35 @@ def main():
         del C32
         torch.cuda.empty_cache()
 
+    int64 = None
+    if rank == 0 and not args.no_batch:
+        # integer form (n = 4096, entries in [-16, 16]): exact int64 Strassen on
+        # the bf16 tensor cores (declared bound) and on the CUDA cores
+        ni = 4096
+        Ai = torch.from_numpy(synth.integers(ni, args.seed + 31, 0, -16, 16)).cuda()
+        Bi = torch.from_numpy(synth.integers(ni, args.seed + 31, 1, -16, 16)).cuda()
+        Ci = torch.empty_like(Ai)
+        int64 = {"workload": "n=4096 int64 U{-16..16}, exact (bit-identical to the oracle in the tests)"}
+        for label, d, bound, reps in (("tensor_core_d1", 1, 16, 10), ("tensor_core_d2", 2, 16, 10),
+                                      ("cuda_core_d2", 2, 0, 2)):
+            pi = stark.Plan(ni, d, stark.DType.I64)
+            if bound:
+                pi.set_input_bound(bound)
+            pi.mul(Ai, Bi, Ci)
+            pi.check()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                pi.mul(Ai, Bi, Ci)
+            e1.record()
+            torch.cuda.synchronize()
+            pi.check()
+            msi = e0.elapsed_time(e1) / reps
+            int64[label] = {"ms": msi, "effective_tops": 2.0 * ni ** 3 / (msi * 1e-3) / 1e12}
+            pi.close()
+        del Ai, Bi, Ci
+        torch.cuda.empty_cache()
+
     batch = serve = None
     if rank == 0 and not args.no_batch:
         batch = run_batch(args, stark, synth, torch)
@@ -568,7 +597,7 @@ def main():
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
-               "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32,
+               "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32, "int64": int64,
                "batch": batch, "serve": serve,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
