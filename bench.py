@@ -130,7 +130,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n, seed, budget_s=12.0, rows_cap=256):
+def cpu_baseline(n, seed, budget_s=12.0, rows_cap=4096):
     """The oracle's classical FP64 row product on the host cores, on a bounded
     row sample of the n x n workload; eff TFLOP/s = 2 n^2 rows / t."""
     import oracle
