@@ -213,8 +213,9 @@ typedef struct stark_batch_s *stark_batch_t;
  * in a CUDA graph on first use and replayed while the pointers stay the
  * same.  depth = -1: each member's depth is chosen by the autotuner, which
  * times the candidate depths on the device (cached per (n, dtype) for the
- * process); the leaf tile width is 256 when every member allows it, else
- * 128.  Allocates every member's workspace.
+ * process); members whose leaf side allows 256-wide tiles share one grouped
+ * launch, the others a second one with 128-wide tiles.  Allocates every
+ * member's workspace.
  * Errors: EINVAL (count <= 0 or > 4096, n[i] <= 0, depth out of range),
  * EUNSUPPORTED (other dtypes, not a GB300), ENOMEM, ECUDA. */
 STARK_API stark_status stark_batch_create(int32_t count, const int64_t *n, int depth, stark_dtype dtype,
@@ -233,8 +234,9 @@ STARK_API stark_status stark_batch_mul(stark_batch_t batch, const void *const *A
 /* Depth chosen for member `index`. */
 STARK_API stark_status stark_batch_depth(stark_batch_t batch, int32_t index, int32_t *depth);
 
-/* Leaf tile width, number of grouped work items, device workspace bytes,
- * and graph replays so far (any pointer may be NULL). */
+/* Widest leaf tile used (256 when any member runs 256-wide tiles), number of
+ * grouped work items, device workspace bytes, and graph replays so far (any
+ * pointer may be NULL). */
 STARK_API stark_status stark_batch_info(stark_batch_t batch, int32_t *tile_n, int64_t *work_items,
                                         int64_t *workspace_bytes, int64_t *graph_replays);
 

@@ -12,8 +12,8 @@
 // Depth per member: given, or chosen by the autotuner, which times the
 // candidate depths on the device (one warm-up and three timed products per
 // candidate on scratch inputs) and caches the winner per (n, dtype) for the
-// process.  The leaf tile width of the grouped launch is 256 when every
-// member's leaf side allows it, else 128.
+// process.  Members whose leaf side allows 256-wide tiles share one grouped
+// launch with that tile width, the others a second one with 128-wide tiles.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -101,7 +101,9 @@ int autotune_depth(int64_t n_req, stark_dtype dt) {
 
 struct stark_batch_s {
   stark_dtype dt = STARK_F32_SPLIT_BF16;
-  int bn = 128;
+  int bn = 128;     // 256 when any member runs 256-wide tiles
+  int split = 0;    // members [0, split) run 256-wide tiles, the rest 128-wide
+  int items_wide = 0;
   std::vector<stark_plan_s*> plans;
   std::vector<stark::GroupDesc> host_desc;
   stark::GroupDesc* d_desc = nullptr;
@@ -160,20 +162,30 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     batch_free(b);
     return st;
   }
-  b->bn = 256;
-  for (auto* p : b->plans)
-    if (p->L % 256 != 0) b->bn = 128;
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return b->plans[x]->n > b->plans[y]->n; });
-  // descriptors: work items of member order[0] first
+  // two grouped launches: members whose leaf side allows 256-wide tiles
+  // first, then the rest with 128-wide tiles; largest products first in each
+  auto wide = [&](int i) { return b->plans[i]->L % 256 == 0; };
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    if (wide(x) != wide(y)) return wide(x);
+    return b->plans[x]->n > b->plans[y]->n;
+  });
+  b->split = 0;
+  while (b->split < count && wide(order[b->split])) ++b->split;
+  b->bn = b->split > 0 ? 256 : 128;
   b->host_desc.resize(count);
-  int64_t items = 0;
+  int64_t items = 0, items_wide = 0;
   for (int k = 0; k < count; ++k) {
+    if (k == b->split) {
+      items_wide = items;
+      items = 0;  // the second launch numbers its own items
+    }
     stark_plan_s* p = b->plans[order[k]];
+    const int bn = k < b->split ? 256 : 128;
     GroupDesc& g = b->host_desc[k];
     std::memset(&g, 0, sizeof(g));
     g.tmA = p->tmA;
     if (dt == STARK_F32_SPLIT_TF32) {
-      if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, b->bn)) st = STARK_EUNSUPPORTED;
+      if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn)) st = STARK_EUNSUPPORTED;
     } else {
       g.tmB = p->tmB;
     }
@@ -184,10 +196,16 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     g.ccount = p->d_ccount;
     g.maxT = p->maxT;
     g.n = p->n;
-    items += p->P * (p->L / 128) * (p->L / b->bn);
+    items += p->P * (p->L / 128) * (p->L / bn);
   }
+  if (b->split == count) {
+    items_wide = items;
+    items = 0;
+  }
+  if (items_wide > 0x7FFFFFFF) st = STARK_EINVAL;
+  b->items_wide = (int)items_wide;
   if (items > 0x7FFFFFFF) st = STARK_EINVAL;
-  b->total_items = (int)items;
+  b->total_items = (int)items;  // items of the 128-wide launch
   // keep the member order used by the descriptors
   std::vector<stark_plan_s*> sorted(count);
   for (int k = 0; k < count; ++k) sorted[k] = b->plans[order[k]];
@@ -229,7 +247,7 @@ stark_status stark_batch_info(stark_batch_t b, int32_t* tile_n, int64_t* work_it
                               int64_t* graph_replays) {
   if (!b) return STARK_EINVAL;
   if (tile_n) *tile_n = b->bn;
-  if (work_items) *work_items = b->total_items;
+  if (work_items) *work_items = (int64_t)b->total_items + b->items_wide;
   if (workspace_bytes) {
     int64_t w = 0;
     for (auto* p : b->plans) w += p->ws_bytes;
@@ -286,12 +304,19 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
       LeafTcArgs a{};
       a.err = b->d_err;
       a.timeout_ns = kDefaultTimeoutNs;
-      a.groups = b->d_desc;
-      a.ngroups = count;
-      a.total_items = b->total_items;
-      if (launch_leaf_tc_grouped(a, b->dt == STARK_F32_SPLIT_TF32, b->bn, device_sm_count(), b->cap) !=
-          cudaSuccess)
-        st = STARK_ECUDA;
+      const bool tf32 = b->dt == STARK_F32_SPLIT_TF32;
+      if (b->split > 0) {  // 256-wide members
+        a.groups = b->d_desc;
+        a.ngroups = b->split;
+        a.total_items = b->items_wide;
+        if (launch_leaf_tc_grouped(a, tf32, 256, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
+      }
+      if (st == STARK_OK && b->split < count) {  // 128-wide members
+        a.groups = b->d_desc + b->split;
+        a.ngroups = count - b->split;
+        a.total_items = b->total_items;
+        if (launch_leaf_tc_grouped(a, tf32, 128, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
+      }
       // members combined into a staging copy: move the result into C
       for (int k = 0; k < count && st == STARK_OK; ++k)
         if (b->host_desc[k].C != ptrs[3 * k + 2])
