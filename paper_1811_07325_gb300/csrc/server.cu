@@ -197,12 +197,18 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
     if (e != STARK_OK) return e;
   }
   if (!tc.empty()) {
-    int bn = 256;
-    for (Request* r : tc)
-      if (r->ws->L % 256 != 0) bn = 128;
-    int64_t items = 0;
+    // 256-wide members first (one grouped launch), then 128-wide ones
+    std::stable_partition(tc.begin(), tc.end(), [](Request* r) { return r->ws->L % 256 == 0; });
+    int split = 0;
+    while (split < (int)tc.size() && tc[split]->ws->L % 256 == 0) ++split;
     const bool tf32 = tc[0]->dt == STARK_F32_SPLIT_TF32;
+    int64_t items_wide = 0, items = 0;
     for (size_t k = 0; k < tc.size(); ++k) {
+      if ((int)k == split) {
+        items_wide = items;
+        items = 0;
+      }
+      const int bn = (int)k < split ? 256 : 128;
       stark_plan_s* p = tc[k]->ws;
       GroupDesc& g = slot.h_desc[k];
       std::memset(&g, 0, sizeof(g));
@@ -224,16 +230,28 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n, g.ldc) ? 1 : 0;
       items += p->P * (p->L / 128) * (p->L / bn);
     }
+    if (split == (int)tc.size()) {
+      items_wide = items;
+      items = 0;
+    }
     if (cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(GroupDesc) * tc.size(), cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
       return STARK_ECUDA;
     LeafTcArgs a{};
     a.err = s->d_err;
     a.timeout_ns = kDefaultTimeoutNs;
-    a.groups = slot.d_desc;
-    a.ngroups = (int32_t)tc.size();
-    a.total_items = (int32_t)items;
-    if (launch_leaf_tc_grouped(a, tf32, bn, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+    if (split > 0) {
+      a.groups = slot.d_desc;
+      a.ngroups = split;
+      a.total_items = (int32_t)items_wide;
+      if (launch_leaf_tc_grouped(a, tf32, 256, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+    }
+    if (split < (int)tc.size()) {
+      a.groups = slot.d_desc + split;
+      a.ngroups = (int32_t)tc.size() - split;
+      a.total_items = (int32_t)items;
+      if (launch_leaf_tc_grouped(a, tf32, 128, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+    }
     for (Request* r : tc)
       if (r->target != r->C) {
         const size_t w = (size_t)r->n * sizeof(float);
