@@ -20,6 +20,8 @@
 // Padding to n_pad is virtual: reads beyond n return zero.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "ptx.cuh"
 #include "stark_internal.h"
 
@@ -227,6 +229,21 @@ __device__ __forceinline__ TermPair terms_of(int m) {
   return TermPair{t[0], t[1], t[2]};
 }
 
+// Depth-first traversal: the subproblem's input is the level-1 operand sum
+// of product `top`, formed on the fly from the four quadrants of the full
+// (padded) input, in the same order as the level-by-level divide.
+template <typename Tin, int VEC, int SIDE>
+struct TopLoader {
+  using Acc = typename AccOf<Tin>::type;
+  Loader<Tin, VEC> ld;
+  int top;
+  int64_t half;  // quadrant side of the full problem
+
+  __device__ __forceinline__ Vec<Acc, VEC> operator()(int64_t row, int64_t col) const {
+    return level_sum<SIDE, Vec<Acc, VEC>>(top, [&](int q) { return ld(row + (q >> 1) * half, col + (q & 1) * half); });
+  }
+};
+
 // Value at position (row, col) of the level-F operand sum S_F selected by the
 // M-indices dig[0..F) (top level first).  S_k(p) = level_sum(i_k, quadrant q
 // of S_{k-1} at p), S_0 = the input: the outermost sum is the deepest level,
@@ -252,7 +269,7 @@ struct Prefix {
   }
 };
 
-template <typename Tin, int OUT, int D, int SIDE, int VEC>
+template <typename Tin, int OUT, int D, int SIDE, int VEC, bool TOP>
 __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok) {
   using Acc = typename AccOf<Tin>::type;
   constexpr int R = D < 2 ? D : 2;  // levels done in registers
@@ -262,7 +279,14 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
   if (pos >= a.L * per_row) return;
   const int64_t i = pos / per_row;
   const int64_t j = (pos % per_row) * VEC;
-  const Loader<Tin, VEC> ld{static_cast<const Tin*>(a.X), a.n, vec_ok != 0};
+  const Loader<Tin, VEC> ld0{static_cast<const Tin*>(a.X), a.n, vec_ok != 0};
+  using LoadT = std::conditional_t<TOP, TopLoader<Tin, VEC, SIDE>, Loader<Tin, VEC>>;
+  LoadT ld;
+  if constexpr (TOP) {
+    ld = LoadT{ld0, a.top, a.npad};  // a.npad is the subproblem's side = the full quadrant side
+  } else {
+    ld = ld0;
+  }
   const Emitter<OUT, Tin, VEC> emit{a.out_hi, a.out_lo, a.L * a.L, i * a.L + j, a.range_flag};
   const int64_t npad = a.npad;
 
@@ -278,7 +302,7 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
         r += (int64_t)(digit >> 1) * (npad >> (F + k + 1));
         c += (int64_t)(digit & 1) * (npad >> (F + k + 1));
       }
-      in[g] = Prefix<SIDE, Acc, VEC, F, Loader<Tin, VEC>>::eval(ld, dig, npad, r, c);
+      in[g] = Prefix<SIDE, Acc, VEC, F, LoadT>::eval(ld, dig, npad, r, c);
     }
     Tree<Acc, SIDE, R, VEC>::run(in, prefix, emit);
   };
@@ -300,7 +324,7 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
   }
 }
 
-template <typename Tin, int OUT, int D, int SIDE>
+template <typename Tin, int OUT, int D, int SIDE, bool TOP>
 cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
   constexpr int VEC = 16 / (int)sizeof(Tin);  // one 16-byte load per quadrant
   if (a.L % VEC != 0) return cudaErrorInvalidValue;
@@ -308,19 +332,28 @@ cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
   const int64_t threads = a.L * (a.L / VEC);
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  divide_kernel<Tin, OUT, D, SIDE, VEC><<<(unsigned)blocks, 256, 0, st>>>(a, vec_ok);
+  divide_kernel<Tin, OUT, D, SIDE, VEC, TOP><<<(unsigned)blocks, 256, 0, st>>>(a, vec_ok);
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename Tin, int OUT, int SIDE>
 cudaError_t by_depth(const DivideArgs& a, int depth, cudaStream_t st) {
+  if (a.top >= 0) {  // depth-first subtree: `depth` levels below the top one
+    switch (depth) {
+      case 0: return launch_one<Tin, OUT, 0, SIDE, true>(a, st);
+      case 1: return launch_one<Tin, OUT, 1, SIDE, true>(a, st);
+      case 2: return launch_one<Tin, OUT, 2, SIDE, true>(a, st);
+      case 3: return launch_one<Tin, OUT, 3, SIDE, true>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (depth) {
-    case 0: return launch_one<Tin, OUT, 0, SIDE>(a, st);
-    case 1: return launch_one<Tin, OUT, 1, SIDE>(a, st);
-    case 2: return launch_one<Tin, OUT, 2, SIDE>(a, st);
-    case 3: return launch_one<Tin, OUT, 3, SIDE>(a, st);
-    case 4: return launch_one<Tin, OUT, 4, SIDE>(a, st);
+    case 0: return launch_one<Tin, OUT, 0, SIDE, false>(a, st);
+    case 1: return launch_one<Tin, OUT, 1, SIDE, false>(a, st);
+    case 2: return launch_one<Tin, OUT, 2, SIDE, false>(a, st);
+    case 3: return launch_one<Tin, OUT, 3, SIDE, false>(a, st);
+    case 4: return launch_one<Tin, OUT, 4, SIDE, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -39,8 +39,9 @@ __global__ void __launch_bounds__(256) leaf_cc_kernel(LeafCcArgs p) {
   const int leaf = p.leaf_begin + blockIdx.z;
   const int64_t L = p.L;
   const int64_t m0 = (int64_t)blockIdx.y * BT, n0 = (int64_t)blockIdx.x * BT;
-  const Acc* __restrict__ X = static_cast<const Acc*>(p.X) + (int64_t)leaf * L * L;
-  const Acc* __restrict__ Y = static_cast<const Acc*>(p.Y) + (int64_t)leaf * L * L;
+  const int plane = leaf - p.plane_base;  // workspace plane of this leaf
+  const Acc* __restrict__ X = static_cast<const Acc*>(p.X) + (int64_t)plane * L * L;
+  const Acc* __restrict__ Y = static_cast<const Acc*>(p.Y) + (int64_t)plane * L * L;
 
   Acc acc[4][4];
 #pragma unroll

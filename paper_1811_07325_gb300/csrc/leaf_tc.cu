@@ -196,7 +196,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int item = unit; ok && item < num_items; item += units) {
         const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
-        const int leaf = it.leaf, m0 = it.m0, n0 = it.n0;
+        // plane of this leaf in the workspace (depth-first traversal keeps
+        // one subtree's leaves, numbered from plane_base)
+        const int leaf = GROUPED ? it.leaf : it.leaf - p.plane_base;
+        const int m0 = it.m0, n0 = it.n0;
         for (int kb = 0; kb < it.kblocks; ++kb) {
           if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) {
             ok = false;

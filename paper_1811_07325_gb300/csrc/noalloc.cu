@@ -135,6 +135,7 @@ extern "C" stark_status stark_mul_noalloc(int64_t n, int depth, const void* A, c
   p.npad = padded_side(n, depth, dt);
   p.L = p.npad >> depth;
   p.P = P;
+  p.P_ws = P;
   p.bn = (p.L % 256 == 0) ? 256 : 128;
   p.device = dev;
   p.num_sms = device_sm_count();

@@ -372,7 +372,7 @@ stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* 
 stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   if (!p || mode < 0 || mode > 2) return STARK_EINVAL;
   if (mode == 2) {
-    if (!p->is_tc || p->depth > 3) return STARK_EUNSUPPORTED;
+    if (!p->is_tc || p->depth > 3 || p->dfs) return STARK_EUNSUPPORTED;
     if (!p->m_planes && p->n > 0) {
       const size_t bytes = (size_t)p->P * p->L * p->L * sizeof(float);
       if (cudaMalloc(&p->m_planes, bytes) != cudaSuccess) {
@@ -388,6 +388,47 @@ stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   return STARK_OK;
 }
 
+// Workspace for `planes_per_half` leaves per operand side, with its maps.
+static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
+  const int64_t per = p->dt == STARK_F32_SPLIT_BF16 ? 4 : 8;  // bytes per leaf element per operand
+  const int64_t bytes = planes * p->L * p->L * per;
+  if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
+  const int64_t old = p->P_ws * p->L * p->L * per;
+  cudaFree(p->X);
+  cudaFree(p->Y);
+  p->X = p->Y = nullptr;
+  p->ws_bytes -= 2 * old;
+  if (cudaMalloc(&p->X, (size_t)bytes) != cudaSuccess || cudaMalloc(&p->Y, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ENOMEM;
+  }
+  p->ws_bytes += 2 * bytes;
+  p->P_ws = planes;
+  p->has_maps64 = false;
+  if (p->is_tc) {
+    const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
+    if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * planes, 128) ||
+        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * planes, tf32 ? p->bn : 64))
+      return STARK_EUNSUPPORTED;
+  }
+  if (p->int_tc && (!make_tmap_planes(&p->tmAi, p->X, false, p->L, planes, 128) ||
+                    !make_tmap_planes(&p->tmBi, p->Y, false, p->L, planes, 64)))
+    return STARK_EUNSUPPORTED;
+  return STARK_OK;
+}
+
+stark_status stark_plan_set_traversal(stark_plan_t p, int depth_first) {
+  if (!p || depth_first < 0 || depth_first > 1) return STARK_EINVAL;
+  if (depth_first == (p->dfs ? 1 : 0) || p->n == 0) {
+    p->dfs = depth_first == 1;
+    return STARK_OK;
+  }
+  if (depth_first && (p->depth < 1 || p->combine_mode == 2)) return STARK_EUNSUPPORTED;
+  const stark_status st = plan_alloc_operands(p, depth_first ? p->P / 7 : p->P);
+  p->dfs = st == STARK_OK && depth_first == 1;
+  return st;
+}
+
 stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
   if (!p || p->dt != STARK_I64 || max_abs < 0) return STARK_EINVAL;
   if (max_abs == 0) {
@@ -401,8 +442,8 @@ stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
   if (xb > 256.0 || (double)p->L * xb * xb > 16777216.0 || p->L % 128 != 0 || !device_is_sm100_family())
     return STARK_EUNSUPPORTED;
   p->int_bn = (p->L % 256 == 0) ? 256 : 128;
-  if (!make_tmap_planes(&p->tmAi, p->X, false, p->L, p->P, 128) ||
-      !make_tmap_planes(&p->tmBi, p->Y, false, p->L, p->P, 64))
+  if (!make_tmap_planes(&p->tmAi, p->X, false, p->L, p->P_ws, 128) ||
+      !make_tmap_planes(&p->tmBi, p->Y, false, p->L, p->P_ws, 64))
     return STARK_EUNSUPPORTED;
   p->int_bound = max_abs;
   p->int_tc = true;
@@ -492,6 +533,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
   p->npad = padded_side(n, depth, dt);
   p->L = p->npad >> depth;
   p->P = pow7i(depth);
+  p->P_ws = p->P;
   p->bn = (p->L % 256 == 0) ? 256 : 128;
   cudaGetDevice(&p->device);
   p->num_sms = device_sm_count();
@@ -574,42 +616,45 @@ static stark_status to_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? STARK_ENOMEM : STARK_ECUDA;
 }
 
-stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s) {
-  // divide phase: every leaf operand of A and of B
-  DivideArgs da{A, p->n, p->npad, p->L, p->X, nullptr, p->d_err};
-  DivideArgs db{B, p->n, p->npad, p->L, p->Y, nullptr, p->d_err};
+// Divide phase into the workspace.  top < 0: every leaf operand (breadth
+// first); top = i1: only the subtree below top-level product M_{i1+1}
+// (depth-first traversal), its leaves in planes 0..7^(d-1)-1.
+stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top) {
+  const int64_t npad = top >= 0 ? p->npad / 2 : p->npad;
+  const int depth = top >= 0 ? p->depth - 1 : p->depth;
+  DivideArgs da{A, p->n, npad, p->L, p->X, nullptr, p->d_err, top};
+  DivideArgs db{B, p->n, npad, p->L, p->Y, nullptr, p->d_err, top};
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
   if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
   if (p->is_tc) {
-    const int64_t half = p->P * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
+    const int64_t half = p->P_ws * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
     da.out_lo = static_cast<char*>(p->X) + half;
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
-  stark_status st = to_status(launch_divide(da, p->depth, 0, in, om, s));
+  stark_status st = to_status(launch_divide(da, depth, 0, in, om, s));
   if (st != STARK_OK) return st;
-  st = to_status(launch_divide(db, p->depth, 1, in, om, s));
+  st = to_status(launch_divide(db, depth, 1, in, om, s));
   if (st != STARK_OK) return st;
   if (p->dt == STARK_F32_SPLIT_TF32)  // the 3xTF32 leaf GEMM takes B K-major (N x K planes)
-    st = to_status(launch_transpose_planes(static_cast<float*>(p->Y), p->L, 2 * p->P, s));
+    st = to_status(launch_transpose_planes(static_cast<float*>(p->Y), p->L, 2 * p->P_ws, s));
   return st;
 }
 
-stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
-                                 cudaStream_t s) {
-  if (p->n == 0) return STARK_OK;
-  if (!A || !B || !C) return STARK_EINVAL;
-  cudaEvent_t* ev = (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
-                        ? &p->ev[(size_t)(p->timing_used - 1) * 4]
-                        : nullptr;
-  if (ev) cudaEventRecord(ev[1], s);
-  stark_status st = plan_divide(p, A, B, s);
-  if (st != STARK_OK) return st;
-  if (ev) cudaEventRecord(ev[2], s);
-  // leaf products with the combine in the epilogue
+stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s) {
+  if (p->dfs) return STARK_EUNSUPPORTED;  // the workspace holds one subtree only
+  return plan_divide_top(p, A, B, s, -1);
+}
+
+// Leaf products of leaves [lb, le) with the combine, operands in workspace
+// planes numbered from plane_base.
+static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le, int64_t plane_base,
+                                cudaStream_t s, bool copy_stage = true) {
+  stark_status st = STARK_OK;
   if (p->is_tc) {
     LeafTcArgs a{};
-    a.P = (int32_t)p->P;
+    a.P = (int32_t)p->P_ws;
+    a.plane_base = (int32_t)plane_base;
     a.L = (int32_t)p->L;
     a.leaf_begin = (int32_t)lb;
     a.leaf_end = (int32_t)le;
@@ -636,21 +681,22 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256 && !a.pair) {
       a.row_bytes = 64;
       if (!p->has_maps64) {
-        if (!make_tmap_planes(&p->tmA64, p->X, false, p->L, 2 * p->P, 128, 64) ||
-            !make_tmap_planes(&p->tmB64, p->Y, false, p->L, 2 * p->P, 32, 64))
+        if (!make_tmap_planes(&p->tmA64, p->X, false, p->L, 2 * p->P_ws, 128, 64) ||
+            !make_tmap_planes(&p->tmB64, p->Y, false, p->L, 2 * p->P_ws, 32, 64))
           return STARK_EUNSUPPORTED;
         p->has_maps64 = true;
       }
     }
     st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA, a.row_bytes == 64 ? &p->tmB64 : &p->tmB,
                                   &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
-    if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
+    if (st == STARK_OK && staged && copy_stage) st = plan_copy_cstage(p, C, s);
     if (st == STARK_OK && deterministic)
       st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, p->n,
                                     static_cast<float*>(C), p->n, s));
   } else if (p->int_tc) {
     LeafTcArgs a{};
-    a.P = (int32_t)p->P;
+    a.P = (int32_t)p->P_ws;
+    a.plane_base = (int32_t)plane_base;
     a.L = (int32_t)p->L;
     a.leaf_begin = (int32_t)lb;
     a.leaf_end = (int32_t)le;
@@ -665,7 +711,8 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     st = to_status(launch_leaf_tc_int(a, &p->tmAi, &p->tmBi, p->int_bn, p->num_sms, s));
   } else {
     LeafCcArgs a{};
-    a.P = (int32_t)p->P;
+    a.P = (int32_t)p->P_ws;
+    a.plane_base = (int32_t)plane_base;
     a.L = (int32_t)p->L;
     a.leaf_begin = (int32_t)lb;
     a.leaf_end = (int32_t)le;
@@ -678,6 +725,38 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     a.ldc = p->n;
     a.n = p->n;
     st = to_status(p->dt == STARK_F64 ? launch_leaf_f64(a, s) : launch_leaf_i64(a, s));
+  }
+  return st;
+}
+
+stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
+                                 cudaStream_t s) {
+  if (p->n == 0) return STARK_OK;
+  if (!A || !B || !C) return STARK_EINVAL;
+  cudaEvent_t* ev = (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
+                        ? &p->ev[(size_t)(p->timing_used - 1) * 4]
+                        : nullptr;
+  if (ev) cudaEventRecord(ev[1], s);
+  stark_status st = STARK_OK;
+  if (!p->dfs) {
+    st = plan_divide_top(p, A, B, s, -1);
+    if (st != STARK_OK) return st;
+    if (ev) cudaEventRecord(ev[2], s);
+    st = plan_leaves(p, C, lb, le, 0, s);
+  } else {
+    // depth-first over the top level: one subtree's operands at a time
+    // (divide and leaves interleave; the phase timer reports them together)
+    if (ev) cudaEventRecord(ev[2], s);
+    int last = -1;
+    for (int top = 0; top < 7; ++top)
+      if (std::max<int64_t>(lb, top * p->P_ws) < std::min<int64_t>(le, (top + 1) * p->P_ws)) last = top;
+    for (int top = 0; top <= last && st == STARK_OK; ++top) {
+      const int64_t b0 = top * p->P_ws, b1 = b0 + p->P_ws;
+      const int64_t lo = lb > b0 ? lb : b0, hi = le < b1 ? le : b1;
+      if (lo >= hi) continue;
+      st = plan_divide_top(p, A, B, s, top);
+      if (st == STARK_OK) st = plan_leaves(p, C, lo, hi, b0, s, top == last);
+    }
   }
   if (ev) cudaEventRecord(ev[3], s);
   p->timing_active = false;

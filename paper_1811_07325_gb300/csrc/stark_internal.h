@@ -64,6 +64,9 @@ struct DivideArgs {
   void* out_hi;       // planes [P][L][L] (split: hi part; plain: the value)
   void* out_lo;       // planes [P][L][L] (split: lo part; plain: unused)
   int* range_flag;    // bf16-exact output: set to kDevIntRange when |value| > 256
+  int top;            // >= 0: depth-first subtree; the input is read through the
+                      // level-1 sum of product `top` (M1..M7 = 0..6) and npad is
+                      // the subproblem's side (half the full padded side)
 };
 
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
@@ -111,6 +114,7 @@ struct LeafTcArgs {
   int32_t pair;        // 1: paired CTAs (cluster of 2) share B tiles by multicast
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
+  int32_t plane_base;  // leaf stored in workspace plane 0 (depth-first traversal); P = planes per half
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;
@@ -131,6 +135,7 @@ int leaf_tc_smem_bytes(bool tf32, int bn);
 
 struct LeafCcArgs {
   int32_t P, L, leaf_begin, leaf_end;
+  int32_t plane_base;  // leaf stored in workspace plane 0
   const void* X;  // planes [P][L][L]
   const void* Y;  // planes [P][L][L] (K x N, row-major)
   const CTarget* ctab;

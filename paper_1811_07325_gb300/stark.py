@@ -67,6 +67,7 @@ _SIGS = {
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_pipeline": ([_vp, _ci], _ci),
     "stark_plan_set_input_bound": ([_vp, _i64], _ci),
+    "stark_plan_set_traversal": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
@@ -249,6 +250,13 @@ class Plan:
     def set_pipeline(self, deep: bool):
         """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
         _check(_lib.stark_plan_set_pipeline(self._h, 1 if deep else 0), "stark_plan_set_pipeline")
+
+    def set_traversal(self, depth_first: bool):
+        """Depth-first over the top level (7x less workspace) or breadth-first."""
+        _check(_lib.stark_plan_set_traversal(self._h, 1 if depth_first else 0), "stark_plan_set_traversal")
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
+        self.workspace_bytes = info.workspace_bytes
 
     def set_input_bound(self, max_abs: int):
         """I64 plans: inputs bounded by max_abs run as exact bf16 tensor-core products."""

@@ -345,6 +345,46 @@ def test_leaf_schedules_agree(S, n, d):
     assert np.abs(out[2] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("n,d,dtype", [(2048, 2, "F32_SPLIT_BF16"), (1001, 3, "F32_SPLIT_BF16"),
+                                       (777, 1, "F32_SPLIT_TF32")])
+def test_depth_first_traversal_matches(S, n, d, dtype):
+    A = synth.normal(n, 64, 0)
+    B = synth.normal(n, 64, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        ws_bfs = p.workspace_bytes
+        Cb = p.mul(dA, dB).cpu().numpy()
+        p.set_traversal(True)
+        assert p.workspace_bytes < ws_bfs * 0.5  # one subtree's operands instead of all
+        Cd = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        check_split(Cd, want, an, bn, dtype, L=p.leaf)
+    assert np.abs(Cd - Cb).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("bound", [0, 16])
+def test_depth_first_int64_exact_and_leaf_ranges(S, bound):
+    n, d = 1000, 2
+    A = synth.integers(n, 65, 0, -16, 16)
+    B = synth.integers(n, 65, 1, -16, 16)
+    want = oracle.gemm_classical(A, B)
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType.I64) as p:
+        p.set_traversal(True)
+        if bound:
+            p.set_input_bound(bound)
+        C = p.mul(dA, dB)
+        p.check()
+        assert np.array_equal(C.cpu().numpy(), want)
+        total = torch.zeros((n, n), dtype=torch.int64, device="cuda")
+        for a, b in ((0, 10), (10, 30), (30, 49)):  # ranges across subtree boundaries
+            total += p.mul_leaves(dA, dB, a, b)
+        p.check()
+        assert np.array_equal(total.cpu().numpy(), want)
+
+
 # ----------------------------------------------------------------- API paths
 def test_leaf_partition_sums_to_product(S):
     n, d = 300, 2
