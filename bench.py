@@ -36,9 +36,10 @@ sys.path.insert(0, ROOT)
 METRIC = "effective TFLOP/s (2n³/t) at n=16384, stated error vs FP64; p50/p99 serve latency"
 
 
-LEAF_SOURCES = ["paper_1811_07325_gb300/csrc/leaf_tc.cu", "paper_1811_07325_gb300/csrc/ptx.cuh",
-                "paper_1811_07325_gb300/csrc/stark_internal.h"]
-TRAFFIC_PROFILE = "profiles/leaf_tc_traffic_n16384_d2_bf16.md"
+LEAF_SOURCES = ["paper_1811_07325_gb300/csrc/leaf_tc2.cu", "paper_1811_07325_gb300/csrc/leaf_common.cuh",
+                "paper_1811_07325_gb300/csrc/ptx.cuh", "paper_1811_07325_gb300/csrc/stark_internal.h"]
+TRAFFIC_PROFILE = "profiles/leaf_tc2_traffic_n16384_d2_bf16.md"
+PAIR_KERNEL = "leaf_tc2_kernel"
 
 
 def leaf_source_hash():
@@ -50,9 +51,11 @@ def leaf_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic(n, depth):
+def measured_traffic(n, depth, kernel):
     """DRAM bytes per leaf launch from the committed ncu summary, if it was
-    taken on this exact kernel source and workload; else None."""
+    taken on this exact kernel source, kernel and workload; else None."""
+    if kernel != PAIR_KERNEL:
+        return None
     try:
         kv = {}
         with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
@@ -320,7 +323,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tf32", action="store_true")
-    ap.add_argument("--pairing", action="store_true")
+    ap.add_argument("--pairing", type=int, default=-1,
+                    help="leaf schedule: 0 single CTAs, 1 multicast pairs, 2 cta_group::2 pairs")
     ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--no-serve", action="store_true")
@@ -355,8 +359,8 @@ def main():
     B = B_h.cuda()
     C = torch.empty_like(A)
     plan = stark.Plan(n, d, dt)
-    if args.pairing:
-        plan.set_pairing(True)
+    if args.pairing >= 0:
+        plan.set_pairing(args.pairing)
     if args.combine:
         plan.set_combine(args.combine)
     if args.deep_pipeline >= 0:
@@ -440,9 +444,12 @@ def main():
     pk = peaks()
     leaf_flops = 3 * 2.0 * plan.leaves * plan.leaf ** 3  # three bf16 products per leaf
     achieved = leaf_flops / (phases["leaf_combine"] * 1e-3) / 1e12
-    roofline = {"kernel": "leaf_tc_kernel (3xBF16 leaf GEMMs + fused combine)", "bound": "tensor",
+    pair_mode = args.pairing if args.pairing >= 0 else 2
+    kernel = PAIR_KERNEL if (pair_mode == 2 and plan.leaf % 256 == 0 and args.deep_pipeline != 1) \
+        else "leaf_tc_kernel"
+    roofline = {"kernel": f"{kernel} (3xBF16 leaf GEMMs + fused combine)", "bound": "tensor",
                 "achieved": achieved, "peak": pk["bf16_sustained"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_sustained"], "traffic": measured_traffic(n, plan.depth),
+                "frac": achieved / pk["bf16_sustained"], "traffic": measured_traffic(n, plan.depth, kernel),
                 "peak_source": f"{pk['source']} bf16 sustained",
                 "algorithmic_flops_per_launch": leaf_flops,
                 "launch_ms": phases["leaf_combine"]}

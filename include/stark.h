@@ -157,11 +157,17 @@ STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, con
  * an fp64/int64 plan or depth > 3), ENOMEM. */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
-/* Leaf launch schedule on the 3xBF16 path: enable = 1 runs CTA pairs
- * (thread-block clusters of 2) on vertically adjacent tiles that share one B
- * tile, fetched once and multicast to both, whenever the leaf side allows
- * (256-wide tiles, an even number of 128-row tiles); 0 (default) runs single
- * CTAs.  Results agree within fp32 rounding of the combine's order. */
+/* Leaf launch schedule of the split-fp32 paths (Alg. 4 leaf products), for leaf
+ * sides that allow it (256-wide tiles, L a multiple of 256):
+ *   0  single CTAs, each a 128 x 256 tile;
+ *   1  CTA pairs (thread-block clusters of 2) on vertically adjacent tiles
+ *      that share one B tile, fetched once and multicast to both (3xBF16
+ *      only);
+ *   2  CTA pairs sharing one 256 x 256 tensor-core MMA (cta_group::2): each
+ *      CTA stages half of the A rows and half of the B columns (3xBF16 and
+ *      3xTF32; the default).
+ * Other leaf sides run mode 0.  Results agree within fp32 rounding of the
+ * combine's order.  Errors: EINVAL (null plan, mode outside 0..2). */
 STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
 
 /* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1

@@ -24,13 +24,11 @@
 // drains its in-flight copies and MMAs, frees TMEM and returns.
 #include <cstring>
 
-#include "ptx.cuh"
-#include "stark_internal.h"
+#include "leaf_common.cuh"
 
 namespace stark {
 namespace {
 
-constexpr int kBM = 128;
 constexpr int kThreads = 192;
 
 // RB: bytes of one swizzled smem row (128: K = 64 bf16 per stage; 64: K = 32
@@ -59,73 +57,6 @@ struct TcCfg {
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + BAR_BYTES;
   static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, B_MN>();
 };
-
-// Everything one work item (a BM x BN tile of one leaf product) needs.
-struct ItemInfo {
-  const CUtensorMap* tA;
-  const CUtensorMap* tB;
-  const CUtensorMap* tC;
-  int leaf, P, m0, n0, kblocks;
-  const CTarget* tg;
-  int nt;
-  float* C;
-  int64_t n, ldc;
-  int use_tma_c;
-};
-
-template <int BN, int BK, bool GROUPED, bool PAIR>
-__device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, const CUtensorMap* tmA,
-                                                const CUtensorMap* tmB, const CUtensorMap* tmC, uint32_t rank) {
-  ItemInfo it;
-  if constexpr (GROUPED) {
-    // member owning this item: the last one whose item_base <= item
-    int lo = 0, hi = p.ngroups - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (p.groups[mid].item_base <= item) lo = mid; else hi = mid - 1;
-    }
-    const GroupDesc* g = p.groups + lo;
-    const int L = g->L;
-    const int tiles_n = L / BN;
-    const int per_leaf = (L / kBM) * tiles_n;
-    const int rem = item - g->item_base;
-    it.tA = &g->tmA;
-    it.tB = &g->tmB;
-    it.tC = &g->tmC;
-    it.leaf = rem / per_leaf;
-    it.P = g->P;
-    it.m0 = ((rem % per_leaf) / tiles_n) * kBM;
-    it.n0 = ((rem % per_leaf) % tiles_n) * BN;
-    it.kblocks = L / BK;
-    it.tg = g->ctab + (int64_t)it.leaf * g->maxT;
-    it.nt = g->ccount[it.leaf];
-    it.C = g->C;
-    it.n = g->n;
-    it.ldc = g->ldc;
-    it.use_tma_c = g->use_tma_c;
-  } else {
-    // PAIR: an item is a pair of vertically adjacent tiles sharing one B
-    // tile; this CTA (cluster rank 0 or 1) computes the upper or lower one
-    const int tiles_n = p.L / BN;
-    const int per_leaf = (p.L / kBM / (PAIR ? 2 : 1)) * tiles_n;
-    const int rem = item % per_leaf;
-    it.tA = tmA;
-    it.tB = tmB;
-    it.tC = tmC;
-    it.leaf = p.leaf_begin + item / per_leaf;
-    it.P = p.P;
-    it.m0 = PAIR ? ((rem / tiles_n) * 2 + (int)rank) * kBM : (rem / tiles_n) * kBM;
-    it.n0 = (rem % tiles_n) * BN;
-    it.kblocks = p.L / BK;
-    it.tg = p.ctab + (int64_t)it.leaf * p.maxT;
-    it.nt = p.ccount[it.leaf];
-    it.C = p.C;
-    it.n = p.n;
-    it.ldc = p.ldc;
-    it.use_tma_c = p.use_tma_c;
-  }
-  return it;
-}
 
 template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB, bool INT1>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -333,14 +264,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // Combine (Alg. 5) fused here: the accumulator tile of leaf l is added,
-    // with its sign, into every C target of l.  Fast path: each warp stages
-    // its 32 x 32 fp32 box (and its negation when a target needs it) in
-    // shared memory with the 128-byte swizzle and issues one TMA bulk
-    // add-reduction per target (the add happens at L2).  Fallback (C not
-    // 16-byte addressable by TMA): signed vector atomics from registers.
+    // (combine fused: epilogue_item adds each finished tile into its C targets)
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    const int row_in_tile = quarter * 32 + lane;
     const uint32_t ebuf = epi_base + (uint32_t)(warp - 2) * 8192u;  // [+ box][- box]
     const uint64_t pol_c = policy_evict_first();  // C lines: add and move on
     int acc = 0;
@@ -349,107 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
       const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
-      const int m0 = it.m0, n0 = it.n0, nt = it.nt;
-      const CTarget* tg = it.tg;
-      bool has_pos = false, has_neg = false;
-      for (int t = 0; t < nt; ++t) (tg[t].sign > 0 ? has_pos : has_neg) = true;
-      const bool vec_ok = ((reinterpret_cast<uintptr_t>(it.C) & 15) == 0) && ((it.ldc & 3) == 0);
-#pragma unroll 1
-      for (int chunk = 0; chunk < BN / 32; ++chunk) {
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + chunk * 32), r);
-        tmem_ld_wait();
-        if constexpr (INT1) {
-          // exact integers held in fp32: signed 64-bit adds into C (wrap mod 2^64)
-          unsigned long long* Ci = reinterpret_cast<unsigned long long*>(it.C);
-#pragma unroll 1
-          for (int t = 0; t < nt; ++t) {
-            const CTarget c = tg[t];
-            const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
-            const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
-            if (grow >= it.n || gcol >= it.n) continue;
-            unsigned long long* dst = Ci + grow * it.ldc + gcol;
-            const int64_t lim = it.n - gcol;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const long long v = __float2ll_rn(__uint_as_float(r[j]));
-              if (j < lim && v != 0) atomicAdd(dst + j, (unsigned long long)(c.sign > 0 ? v : -v));
-            }
-          }
-        } else if (p.store_m) {
-          // unfused, deterministic combine: this leaf's tile goes to its M
-          // plane (tmC maps the M planes here); the combine kernel adds later
-          if (lane == 0) bulk_wait_group_read<0>();
-          __syncwarp();
-          const uint32_t row_addr = ebuf + (uint32_t)lane * 128u;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[4 * c]), "r"(r[4 * c + 1]),
-                         "r"(r[4 * c + 2]), "r"(r[4 * c + 3])
-                         : "memory");
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            tma_store_3d(it.tC, n0 + chunk * 32, m0 + quarter * 32, it.leaf - p.leaf_begin, ebuf);
-            bulk_commit_group();
-          }
-        } else if (it.use_tma_c) {
-          if (lane == 0) bulk_wait_group_read<0>();  // the previous boxes have been read
-          __syncwarp();
-#pragma unroll
-          for (int sg = 0; sg < 2; ++sg) {
-            if (sg == 0 ? !has_pos : !has_neg) continue;
-            const uint32_t row_addr = ebuf + (uint32_t)sg * 4096u + (uint32_t)lane * 128u;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              float4 v = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
-                                     __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
-              if (sg == 1) v = make_float4(-v.x, -v.y, -v.z, -v.w);
-              const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
-              asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-                           "f"(v.w)
-                           : "memory");
-            }
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            for (int t = 0; t < nt; ++t) {
-              const CTarget c = tg[t];
-              const int64_t y = (int64_t)c.row_off + m0 + quarter * 32;
-              const int64_t x = (int64_t)c.col_off + n0 + chunk * 32;
-              if (y >= it.n || x >= it.n) continue;
-              tma_reduce_add_2d(it.tC, (int32_t)x, (int32_t)y, ebuf + (c.sign > 0 ? 0u : 4096u), pol_c);
-            }
-            bulk_commit_group();
-          }
-        } else {
-#pragma unroll 1
-          for (int t = 0; t < nt; ++t) {
-            const CTarget c = tg[t];
-            const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
-            const int64_t gcol = (int64_t)c.col_off + n0 + chunk * 32;
-            if (grow >= it.n || gcol >= it.n) continue;
-            float* dst = it.C + grow * it.ldc + gcol;
-            const float sg = (float)c.sign;
-            if (vec_ok && gcol + 32 <= it.n) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
-                                       sg * __uint_as_float(r[4 * j + 2]), sg * __uint_as_float(r[4 * j + 3]));
-                atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
-              }
-            } else {
-              const int64_t lim = it.n - gcol;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
-            }
-          }
-        }
-      }
+      epilogue_item<BN, INT1>(it, p, tmem_base, (uint32_t)(acc * BN), quarter, lane, ebuf, pol_c);
       tc_fence_before();
       mbar_arrive(acce_bar(acc));
       if (++acc == 2) {
@@ -531,8 +356,9 @@ int leaf_tc_smem_bytes(bool tf32, int bn) {
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
   // bf16 with 256-wide tiles and an even number of tile rows: paired CTAs
-  // sharing each B tile through TMA multicast (unless disabled by the plan)
-  if (bn == 256 && !tf32 && a.pair && (a.L / kBM) % 2 == 0)
+  // sharing each B tile through TMA multicast (pair == 1; the cta_group::2
+  // pairs of pair == 2 are launched by launch_leaf_tc2)
+  if (bn == 256 && !tf32 && a.pair == 1 && (a.L / kBM) % 2 == 0)
     return launch_cfg<256, 2, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
   // bf16, 256-wide tiles, 64-byte rows: four 48 KB stages instead of two 96 KB
   if (bn == 256 && !tf32 && a.row_bytes == 64)

@@ -405,6 +405,7 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
   p->ws_bytes += 2 * bytes;
   p->P_ws = planes;
   p->has_maps64 = false;
+  p->has_mapbp = false;
   if (p->is_tc) {
     const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
     if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * planes, 128) ||
@@ -451,7 +452,7 @@ stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
 }
 
 stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
-  if (!p || enable < 0 || enable > 1) return STARK_EINVAL;
+  if (!p || enable < 0 || enable > 2) return STARK_EINVAL;
   p->pair_mode = enable;
   return STARK_OK;
 }
@@ -676,9 +677,10 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       a.use_tma_c = 0;
       tmC = p->tmM;
     }
-    a.pair = deterministic ? 0 : p->pair_mode;
+    a.pair = (deterministic && p->pair_mode == 1) ? 0 : p->pair_mode;
     a.row_bytes = 128;
-    if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256 && !a.pair) {
+    if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256) {
+      a.pair = 0;  // the 64-byte-row schedule runs single CTAs
       a.row_bytes = 64;
       if (!p->has_maps64) {
         if (!make_tmap_planes(&p->tmA64, p->X, false, p->L, 2 * p->P_ws, 128, 64) ||
@@ -687,8 +689,18 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
         p->has_maps64 = true;
       }
     }
-    st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA, a.row_bytes == 64 ? &p->tmB64 : &p->tmB,
-                                  &tmC, p->dt == STARK_F32_SPLIT_TF32, p->bn, p->num_sms, s));
+    const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
+    if (a.pair == 2 && p->bn == 256 && leaf_tc2_fits(a)) {
+      // CTA pairs on one 256 x 256 MMA; tf32 needs Y boxes of 128 rows
+      if (tf32 && !p->has_mapbp) {
+        if (!make_tmap_planes(&p->tmBp, p->Y, true, p->L, 2 * p->P_ws, 128)) return STARK_EUNSUPPORTED;
+        p->has_mapbp = true;
+      }
+      st = to_status(launch_leaf_tc2(a, &p->tmA, tf32 ? &p->tmBp : &p->tmB, &tmC, tf32, p->num_sms, s));
+    } else {
+      st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA,
+                                    a.row_bytes == 64 ? &p->tmB64 : &p->tmB, &tmC, tf32, p->bn, p->num_sms, s));
+    }
     if (st == STARK_OK && staged && copy_stage) st = plan_copy_cstage(p, C, s);
     if (st == STARK_OK && deterministic)
       st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, p->n,

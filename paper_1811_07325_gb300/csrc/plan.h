@@ -55,7 +55,10 @@ struct stark_plan_s {
                          // 2: deterministic (store M planes, ordered combine pass)
   void* m_planes = nullptr;  // [P][L][L] fp32 leaf products (combine mode 2)
   CUtensorMap tmM;
-  int pair_mode = 0;     // 1: paired CTAs with multicast B tiles where the tiling allows
+  int pair_mode = 2;     // leaf schedule where the tiling allows (L % 256 == 0): 2 CTA pairs on one
+                         // cta_group::2 MMA, 1 paired CTAs with multicast B tiles, 0 single CTAs
+  CUtensorMap tmBp;      // tf32 Y map with 128-row boxes for the pair MMA
+  bool has_mapbp = false;
   int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
   CUtensorMap tmA64, tmB64;  // operand maps for the 64-byte-row schedule
   bool has_maps64 = false;

@@ -111,7 +111,7 @@ struct LeafTcArgs {
   int* err;
   uint64_t timeout_ns;
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
-  int32_t pair;        // 1: paired CTAs (cluster of 2) share B tiles by multicast
+  int32_t pair;        // 1: paired CTAs share B tiles by multicast; 2: cta_group::2 pair MMA
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
   int32_t plane_base;  // leaf stored in workspace plane 0 (depth-first traversal); P = planes per half
@@ -132,6 +132,12 @@ cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, cons
 // Grouped launch over a.groups (tensor maps taken from the descriptors).
 cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t s);
 int leaf_tc_smem_bytes(bool tf32, int bn);
+// 3xBF16 / 3xTF32 leaves on CTA pairs sharing one cta_group::2 MMA of
+// 256 x 256 (requires L a multiple of 256).  The tf32 Y map's box is 128
+// rows (each CTA stages half of the 256 columns).
+bool leaf_tc2_fits(const LeafTcArgs& a);
+cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                            const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t s);
 
 struct LeafCcArgs {
   int32_t P, L, leaf_begin, leaf_end;

@@ -243,9 +243,11 @@ class Plan:
         2: deterministic (stored leaf products, ordered combine pass)."""
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
 
-    def set_pairing(self, enable: bool):
-        """Paired CTAs sharing B tiles by multicast (default on where possible)."""
-        _check(_lib.stark_plan_set_pairing(self._h, 1 if enable else 0), "stark_plan_set_pairing")
+    def set_pairing(self, mode):
+        """Leaf schedule of the split-fp32 paths: 0 single CTAs; 1 (or True)
+        CTA pairs sharing B tiles by multicast (3xBF16); 2 (default) CTA pairs
+        on one cta_group::2 MMA of 256 x 256."""
+        _check(_lib.stark_plan_set_pairing(self._h, int(mode)), "stark_plan_set_pairing")
 
     def set_pipeline(self, deep: bool):
         """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""

@@ -321,15 +321,16 @@ def test_deterministic_combine_is_bitwise_reproducible(S, n, d, dtype):
 
 @pytest.mark.parametrize("n,d", [(2048, 1), (4096, 2), (1536, 0)])
 def test_leaf_schedules_agree(S, n, d):
-    # clusters of two CTAs sharing B tiles by multicast, one CTA per tile, and
-    # the four-stage 64-byte-row pipeline: same products
+    # clusters of two CTAs sharing B tiles by multicast, one CTA per tile, the
+    # four-stage 64-byte-row pipeline and CTA pairs on one cta_group::2 MMA:
+    # same products
     A = synth.normal(n, 62, 0)
     B = synth.normal(n, 62, 1)
     rows = synth.sample_rows(n, 64, 62)
     want = oracle.gemm_rows(A, B, rows)
     an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
     out = []
-    for pair, deep in ((True, False), (False, False), (False, True)):
+    for pair, deep in ((1, False), (0, False), (0, True), (2, False)):
         with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
             p.set_pairing(pair)
             p.set_pipeline(deep)
@@ -343,6 +344,40 @@ def test_leaf_schedules_agree(S, n, d):
             assert rel <= SPLIT_BOUND["F32_SPLIT_BF16"] + 3 * (p.leaf / 16) * 2.0 ** -24
     assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
     assert np.abs(out[2] - out[1]).max() <= 1e-5 * np.abs(want).max()
+    assert np.abs(out[3] - out[1]).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("dtype,n,d,combine,dfs", [
+    ("F32_SPLIT_BF16", 1024, 1, 0, False), ("F32_SPLIT_BF16", 1001, 1, 0, False),
+    ("F32_SPLIT_BF16", 2048, 2, 2, False), ("F32_SPLIT_BF16", 2048, 2, 0, True),
+    ("F32_SPLIT_BF16", 1900, 2, 1, False), ("F32_SPLIT_BF16", 777, 0, 0, False),
+    ("F32_SPLIT_TF32", 1024, 1, 0, False), ("F32_SPLIT_TF32", 1001, 1, 2, False),
+    ("F32_SPLIT_TF32", 2048, 2, 0, True)])
+def test_pair_mma_matches_oracle(S, dtype, n, d, combine, dfs):
+    # CTA pairs on one 256 x 256 cta_group::2 MMA, every element against the
+    # FP64 oracle; leaf sides that are not a multiple of 256 (n=777, d=0) take
+    # the single-CTA kernel
+    A = synth.normal(n, 65, 0)
+    B = synth.normal(n, 65, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        p.set_pairing(2)
+        p.set_combine(combine)
+        if dfs:
+            p.set_traversal(True)
+        C1 = p.mul(dA, dB).cpu().numpy()
+        C2 = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        check_split(C1, want, an, bn, dtype, L=p.leaf)
+        p.set_pairing(0)
+        C0 = p.mul(dA, dB).cpu().numpy()
+    assert np.abs(C1 - C0).max() <= 1e-5 * np.abs(want).max()
+    if combine == 2:
+        assert np.array_equal(C1.view(np.uint32), C2.view(np.uint32))
+    else:
+        assert np.abs(C1 - C2).max() <= 1e-5 * np.abs(want).max()
 
 
 @pytest.mark.parametrize("n,d,dtype", [(2048, 2, "F32_SPLIT_BF16"), (1001, 3, "F32_SPLIT_BF16"),
