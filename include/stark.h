@@ -119,10 +119,33 @@ STARK_API stark_status stark_mul_host(stark_plan_t plan, const void *A, const vo
  * plan-owned streams with alternating staging sets, so the copies of one
  * call overlap the product of the previous one, and makes `stream` wait for
  * this product's result.  The host buffers must stay valid and unmodified
- * (C unread) until `stream` has passed that point; consecutive calls may not
- * reuse a C buffer before the earlier call completed.  Errors as stark_mul. */
+ * (C unread) until `stream` has passed that point.  Copies out run in call
+ * order, so a C buffer passed again to a later call ends up holding the
+ * later result; read it in between only after the earlier call completed.
+ * Errors as stark_mul. */
 STARK_API stark_status stark_mul_host_async(stark_plan_t plan, const void *A, const void *B, void *C,
                                             void *stream);
+
+/* The same pipeline without a wait on a caller's stream: enqueues the copy
+ * in and the product and returns; the copy out of this product is enqueued
+ * by the next call (after that call's copy in), by stark_plan_host_wait or by
+ * stark_plan_destroy, and stark_plan_host_wait collects every product
+ * enqueued so far.  CUDA multiplexes streams onto a few hardware queues; an
+ * operation that waits on a later event holds back everything queued behind
+ * it in a shared queue, so this form enqueues operations in the order they
+ * become ready and puts no wait on any stream it does not own: copies in of
+ * one call then overlap the product of the previous one whatever the
+ * queue assignment.  (stark_mul_host_async's wait on `stream` can hold back
+ * the next call's copies when `stream` shares a queue with the plan's.)
+ * Buffer rules as stark_mul_host_async, with "until stark_plan_host_wait
+ * returned" for "until `stream` has passed that point".  Errors as
+ * stark_mul. */
+STARK_API stark_status stark_mul_host_enqueue(stark_plan_t plan, const void *A, const void *B, void *C);
+
+/* Blocks until every product enqueued with stark_mul_host_enqueue (or
+ * stark_mul_host_async) has its C in host memory, then reports the device
+ * error word as stark_plan_check does.  OK at once when nothing is pending. */
+STARK_API stark_status stark_plan_host_wait(stark_plan_t plan);
 
 /* Partial product for sharding the leaves across devices (the independent
  * products of one recursion tree, Sec. III-C): C = sum over leaves l in

@@ -279,8 +279,11 @@ stark_status stark_plan(int64_t n, int depth, stark_dtype dt, stark_plan_t* out)
   return STARK_OK;
 }
 
+static bool flush_copy_out(stark_plan_t p);
+
 stark_status stark_plan_destroy(stark_plan_t p) {
   if (!p) return STARK_OK;
+  if (p->s_out) flush_copy_out(p);  // a product still owed to host memory
   cudaDeviceSynchronize();
   plan_release(p);
   delete p;
@@ -331,35 +334,78 @@ static stark_status ensure_host_pipeline(stark_plan_t p) {
   return STARK_OK;
 }
 
-stark_status stark_mul_host_async(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
-  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
-  if (p->n == 0) return STARK_OK;
+// The host pipeline: copies in on s_in, products on s_comp, copies out on
+// s_out, two staging sets used alternately.  CUDA feeds streams to the GPU
+// through a few hardware queues, and two streams may share one; an operation
+// that waits on a later event then holds back everything queued behind it.
+// So operations are enqueued in the order they become ready on the GPU: the
+// copy out of product k (ready when product k ends) goes in after the copy
+// in of product k+1 (ready when product k-1 ends), i.e. during the next call
+// or at the wait that collects the results.
+static bool flush_copy_out(stark_plan_t p) {
+  if (p->pend_set < 0) return true;
+  const int k = p->pend_set;
+  const size_t bytes = (size_t)p->n * p->n * p->esz;
+  void* dC = k ? p->stage2[2] : p->stage_C;
+  bool ok = cudaStreamWaitEvent(p->s_out, p->ev_comp[k], 0) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(p->pend_C, dC, bytes, cudaMemcpyDeviceToHost, p->s_out) == cudaSuccess;
+  ok = ok && cudaEventRecord(p->ev_out[k], p->s_out) == cudaSuccess;
+  p->pend_set = -1;
+  p->pend_C = nullptr;
+  return ok;
+}
+
+// Enqueues copy in and product of one call; its copy out stays pending.
+static stark_status host_enqueue(stark_plan_t p, const void* A, const void* B, void* C) {
   if (stark_status st = ensure_host_pipeline(p); st != STARK_OK) return st;
   const size_t bytes = (size_t)p->n * p->n * p->esz;
   const int k = p->host_calls++ & 1;  // buffer set of this call
   void* dA = k ? p->stage2[0] : p->stage_A;
   void* dB = k ? p->stage2[1] : p->stage_B;
   void* dC = k ? p->stage2[2] : p->stage_C;
-  cudaStream_t user = (cudaStream_t)stream;
   bool ok = true;
   // inputs of this set may be overwritten once the product two calls ago has
-  // read them; its C once that C has been copied out
+  // read them
   ok = ok && cudaStreamWaitEvent(p->s_in, p->ev_comp[k], 0) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(dA, A, bytes, cudaMemcpyHostToDevice, p->s_in) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(dB, B, bytes, cudaMemcpyHostToDevice, p->s_in) == cudaSuccess;
   ok = ok && cudaEventRecord(p->ev_in[k], p->s_in) == cudaSuccess;
+  ok = ok && flush_copy_out(p);  // the previous call's result
+  // this set's C may be overwritten once it has been copied out
   ok = ok && cudaStreamWaitEvent(p->s_comp, p->ev_in[k], 0) == cudaSuccess;
   ok = ok && cudaStreamWaitEvent(p->s_comp, p->ev_out[k], 0) == cudaSuccess;
   if (!ok) return STARK_ECUDA;
   stark_status st = plan_run(p, dA, dB, dC, 0, p->P, p->s_comp);
   if (st != STARK_OK) return st;
-  ok = ok && cudaEventRecord(p->ev_comp[k], p->s_comp) == cudaSuccess;
-  ok = ok && cudaStreamWaitEvent(p->s_out, p->ev_comp[k], 0) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(C, dC, bytes, cudaMemcpyDeviceToHost, p->s_out) == cudaSuccess;
-  ok = ok && cudaEventRecord(p->ev_out[k], p->s_out) == cudaSuccess;
+  if (cudaEventRecord(p->ev_comp[k], p->s_comp) != cudaSuccess) return STARK_ECUDA;
+  p->pend_set = k;
+  p->pend_C = C;
+  return STARK_OK;
+}
+
+stark_status stark_mul_host_async(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
+  if (p->n == 0) return STARK_OK;
+  if (stark_status st = host_enqueue(p, A, B, C); st != STARK_OK) return st;
+  const int k = p->pend_set;
+  if (!flush_copy_out(p)) return STARK_ECUDA;
   // the caller's stream observes completion of this product
-  ok = ok && cudaStreamWaitEvent(user, p->ev_out[k], 0) == cudaSuccess;
-  return ok ? STARK_OK : STARK_ECUDA;
+  if (cudaStreamWaitEvent((cudaStream_t)stream, p->ev_out[k], 0) != cudaSuccess) return STARK_ECUDA;
+  return STARK_OK;
+}
+
+stark_status stark_mul_host_enqueue(stark_plan_t p, const void* A, const void* B, void* C) {
+  if (!p || (p->n > 0 && (!A || !B || !C))) return STARK_EINVAL;
+  if (p->n == 0) return STARK_OK;
+  return host_enqueue(p, A, B, C);
+}
+
+stark_status stark_plan_host_wait(stark_plan_t p) {
+  if (!p) return STARK_EINVAL;
+  if (!p->s_out) return STARK_OK;  // nothing was ever enqueued
+  if (!flush_copy_out(p)) return STARK_ECUDA;
+  // s_out carries every copy out in call order: its completion covers all
+  return stark_plan_check(p, p->s_out);
 }
 
 stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* C, void* stream) {

@@ -78,6 +78,8 @@ struct stark_plan_s {
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   int host_calls = 0;
+  int pend_set = -1;          // staging set whose copy out is not yet enqueued
+  void* pend_C = nullptr;     // its host destination
   // staging copy of C (row pitch staged_ld(n)) for the tensor-core combine
   // when C cannot be a TMA target (n not a multiple of 4)
   void* cstage = nullptr;

@@ -60,6 +60,8 @@ _SIGS = {
     "stark_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
     "stark_mul_host": ([_vp, _vp, _vp, _vp, _vp], _ci),
     "stark_mul_host_async": ([_vp, _vp, _vp, _vp, _vp], _ci),
+    "stark_mul_host_enqueue": ([_vp, _vp, _vp, _vp], _ci),
+    "stark_plan_host_wait": ([_vp], _ci),
     "stark_mul_leaves": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _ci),
     "stark_plan_operands": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _ci),
     "stark_plan_check": ([_vp, _vp], _ci),
@@ -215,6 +217,23 @@ class Plan:
         fn = _lib.stark_mul_host_async if asynchronous else _lib.stark_mul_host
         _check(fn(self._h, ptr(A, "A"), ptr(B, "B"), ptr(C, "C"), _stream_handle(stream)), "stark_mul_host")
         return C
+
+    def mul_host_enqueue(self, A, B, C):
+        """Pipelined product from host memory with no wait on any stream:
+        returns at once; ``host_wait()`` collects every product enqueued so
+        far.  A, B, C stay untouched (C unread) until then."""
+        def ptr(x, name):
+            if not hasattr(x, "data_ptr") or x.is_cuda or tuple(x.shape) != (self.n, self.n) \
+                    or not x.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous host {self.n}x{self.n} tensor")
+            return ctypes.c_void_p(x.data_ptr())
+        _check(_lib.stark_mul_host_enqueue(self._h, ptr(A, "A"), ptr(B, "B"), ptr(C, "C")), "stark_mul_host_enqueue")
+        return C
+
+    def host_wait(self):
+        """Block until every enqueued host product is in host memory; raises
+        on a device error (as ``check``)."""
+        _check(_lib.stark_plan_host_wait(self._h), "stark_plan_host_wait")
 
     def operands(self, A, B, stream=None):
         """Divide phase only; returns torch views (X, Y) of the leaf operand planes."""

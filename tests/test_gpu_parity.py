@@ -466,6 +466,34 @@ def test_mul_host_async_pipeline(S):
         check_split(Cs[k].numpy(), want, an, bn, "F32_SPLIT_BF16")
 
 
+def test_mul_host_enqueue_and_wait(S):
+    # the host pipeline without a stream wait: five products through two
+    # staging sets, collected by one host_wait; then a second round on the
+    # same plan reusing the first C buffers
+    n = 1000
+    pairs = [(synth.normal(n, 80 + k, 0), synth.normal(n, 80 + k, 1)) for k in range(5)]
+    As = [torch.from_numpy(a).pin_memory() for a, _ in pairs]
+    Bs = [torch.from_numpy(b).pin_memory() for _, b in pairs]
+    Cs = [torch.full((n, n), float("nan"), dtype=torch.float32).pin_memory() for _ in pairs]
+    with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
+        p.host_wait()  # nothing pending yet
+        for k in range(5):
+            p.mul_host_enqueue(As[k], Bs[k], Cs[k])
+        p.host_wait()
+        first = [c.clone() for c in Cs]
+        for k in range(2):
+            p.mul_host_enqueue(As[4 - k], Bs[4 - k], Cs[k])
+        p.host_wait()
+        with pytest.raises(ValueError):
+            p.mul_host_enqueue(As[0].cuda(), Bs[0], Cs[0])
+    for k, (a, b) in enumerate(pairs):
+        want = oracle.gemm_classical(a.astype(np.float64), b.astype(np.float64))
+        an, bn = np.linalg.norm(a.astype(np.float64)), np.linalg.norm(b.astype(np.float64))
+        check_split(first[k].numpy(), want, an, bn, "F32_SPLIT_BF16")
+    for k in range(2):
+        assert np.abs(Cs[k].numpy() - first[4 - k].numpy()).max() <= 1e-5 * np.abs(first[4 - k].numpy()).max()
+
+
 def test_empty_and_bad_arguments(S):
     with S.Plan(0, 1, S.DType.F32_SPLIT_BF16) as p:
         e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
