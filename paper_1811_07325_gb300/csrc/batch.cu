@@ -13,7 +13,8 @@
 // candidate depths on the device (one warm-up and three timed products per
 // candidate on scratch inputs) and caches the winner per (n, dtype) for the
 // process.  Members whose leaf side allows 256-wide tiles share one grouped
-// launch with that tile width, the others a second one with 128-wide tiles.
+// launch of CTA pairs (256 x 256 tiles, cta_group::2), the others a second
+// one with 128 x 128 tiles on single CTAs.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -185,7 +186,8 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     std::memset(&g, 0, sizeof(g));
     g.tmA = p->tmA;
     if (dt == STARK_F32_SPLIT_TF32) {
-      if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn)) st = STARK_EUNSUPPORTED;
+      // 256-wide members run CTA pairs: each CTA loads 128 Y rows
+      if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn == 256 ? 128 : bn)) st = STARK_EUNSUPPORTED;
     } else {
       g.tmB = p->tmB;
     }
@@ -196,7 +198,8 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     g.ccount = p->d_ccount;
     g.maxT = p->maxT;
     g.n = p->n;
-    items += p->P * (p->L / 128) * (p->L / bn);
+    // 256-wide members: 256 x 256 pair tiles (CTA pairs); others 128 x 128
+    items += bn == 256 ? p->P * (p->L / 256) * (p->L / 256) : p->P * (p->L / 128) * (p->L / 128);
   }
   if (b->split == count) {
     items_wide = items;
@@ -309,7 +312,7 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
         a.groups = b->d_desc;
         a.ngroups = b->split;
         a.total_items = b->items_wide;
-        if (launch_leaf_tc_grouped(a, tf32, 256, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
+        if (launch_leaf_tc2_grouped(a, tf32, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
       }
       if (st == STARK_OK && b->split < count) {  // 128-wide members
         a.groups = b->d_desc + b->split;

@@ -36,14 +36,14 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     const GroupDesc* g = p.groups + lo;
     const int L = g->L;
     const int tiles_n = L / BN;
-    const int per_leaf = (L / kBM) * tiles_n;
+    const int per_leaf = (L / kBM / (PAIR ? 2 : 1)) * tiles_n;
     const int rem = item - g->item_base;
     it.tA = &g->tmA;
     it.tB = &g->tmB;
     it.tC = &g->tmC;
     it.leaf = rem / per_leaf;
     it.P = g->P;
-    it.m0 = ((rem % per_leaf) / tiles_n) * kBM;
+    it.m0 = PAIR ? (((rem % per_leaf) / tiles_n) * 2 + (int)rank) * kBM : ((rem % per_leaf) / tiles_n) * kBM;
     it.n0 = ((rem % per_leaf) % tiles_n) * BN;
     it.kblocks = L / BK;
     it.tg = g->ctab + (int64_t)it.leaf * g->maxT;
@@ -53,8 +53,9 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     it.ldc = g->ldc;
     it.use_tma_c = g->use_tma_c;
   } else {
-    // PAIR: an item is a pair of vertically adjacent tiles sharing one B
-    // tile; this CTA (cluster rank 0 or 1) computes the upper or lower one
+    // (both branches) PAIR: an item is a pair of vertically adjacent 128-row
+    // tiles sharing one B tile; this CTA (cluster rank 0 or 1) computes the
+    // upper or lower one
     const int tiles_n = p.L / BN;
     const int per_leaf = (p.L / kBM / (PAIR ? 2 : 1)) * tiles_n;
     const int rem = item % per_leaf;

@@ -348,11 +348,6 @@ cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtens
 
 }  // namespace
 
-int leaf_tc_smem_bytes(bool tf32, int bn) {
-  if (bn == 256) return tf32 ? TcCfg<256, 2, true>::SMEM : TcCfg<256, 2, false>::SMEM;
-  return tf32 ? TcCfg<128, 3, true>::SMEM : TcCfg<128, 3, false>::SMEM;
-}
-
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
   // bf16 with 256-wide tiles and an even number of tile rows: paired CTAs
@@ -384,12 +379,9 @@ cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, cons
 }
 
 cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t st) {
+  // 256-wide members run on CTA pairs (launch_leaf_tc2_grouped)
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  if (bn == 256) {
-    return tf32 ? launch_cfg<256, 2, true, true>(a, &none, &none, &none, num_sms, st)
-                : launch_cfg<256, 2, false, true>(a, &none, &none, &none, num_sms, st);
-  }
   if (bn == 128) {
     return tf32 ? launch_cfg<128, 3, true, true>(a, &none, &none, &none, num_sms, st)
                 : launch_cfg<128, 3, false, true>(a, &none, &none, &none, num_sms, st);

@@ -59,7 +59,9 @@ struct Tc2Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
-template <bool TF32>
+// GROUPED: items of several problems (GroupDesc array, tensor maps in global
+// memory), as in the single-CTA kernel's grouped mode.
+template <bool TF32, bool GROUPED>
 __global__ void __launch_bounds__(kThreads2, 1)
     leaf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
   const bool leader = rank == 0;
   const int unit = (int)(blockIdx.x >> 1);
   const int units = (int)(gridDim.x >> 1);
-  const int num_items = (p.leaf_end - p.leaf_begin) * (p.L / (2 * kBM)) * (p.L / Cfg::BN);
+  const int num_items =
+      GROUPED ? p.total_items : (p.leaf_end - p.leaf_begin) * (p.L / (2 * kBM)) * (p.L / Cfg::BN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -95,9 +98,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
       mbar_init(acce_bar(a), 8);  // even CTA: 4 epilogue warps of each CTA
     }
     fence_mbar_init();
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    if (p.use_tma_c || p.store_m) prefetch_tmap(&tmC);
+    if (!GROUPED) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      if (p.use_tma_c || p.store_m) prefetch_tmap(&tmC);
+    }
   }
   if (warp == 1) {
     tmem_alloc2(smem_u32(tmem_slot), Cfg::TMEM_COLS);
@@ -118,8 +123,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
       uint32_t armed = 0, armed_phase = 0;
       bool ok = true;
       for (int item = unit; ok && item < num_items; item += units) {
-        const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, false, true>(item, p, &tmA, &tmB, &tmC, rank);
-        const int leaf = it.leaf - p.plane_base;
+        const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, GROUPED, true>(item, p, &tmA, &tmB, &tmC, rank);
+        const int leaf = GROUPED ? it.leaf : it.leaf - p.plane_base;  // workspace plane
         const int m0 = it.m0;                                 // this CTA's 128 rows
         const int nb = it.n0 + (int)rank * Cfg::BNH;          // this CTA's 128 columns
         for (int kb = 0; kb < it.kblocks; ++kb) {
@@ -131,18 +136,18 @@ __global__ void __launch_bounds__(kThreads2, 1)
           const uint32_t fb = mapa_shared(full_bar(s), 0);
           if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * Cfg::STAGE_BYTES);
           const int k0 = kb * Cfg::BK;
-          tma_load_3d_cg2(st, &tmA, k0, m0, leaf, fb, pol_a);
-          tma_load_3d_cg2(st + Cfg::A_BYTES, &tmA, k0, m0, it.P + leaf, fb, pol_a);
+          tma_load_3d_cg2(st, it.tA, k0, m0, leaf, fb, pol_a);
+          tma_load_3d_cg2(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, fb, pol_a);
           if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
-              tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, &tmB, nb + c * Cfg::W, k0, leaf, fb, pol_b);
-              tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, &tmB, nb + c * Cfg::W, k0,
+              tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, nb + c * Cfg::W, k0, leaf, fb, pol_b);
+              tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, nb + c * Cfg::W, k0,
                               it.P + leaf, fb, pol_b);
             }
           } else {
-            tma_load_3d_cg2(st + 2 * Cfg::A_BYTES, &tmB, k0, nb, leaf, fb, pol_b);
-            tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB, k0, nb, it.P + leaf, fb, pol_b);
+            tma_load_3d_cg2(st + 2 * Cfg::A_BYTES, it.tB, k0, nb, leaf, fb, pol_b);
+            tma_load_3d_cg2(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, it.tB, k0, nb, it.P + leaf, fb, pol_b);
           }
           armed |= 1u << s;
           armed_phase = (armed_phase & ~(1u << s)) | (phase << s);
@@ -182,8 +187,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
       uint32_t acc_phase = 0;
       bool ok = true;
       bool issued = false;
-      const int kblocks = p.L / Cfg::BK;
       for (int item = unit; ok && item < num_items; item += units) {
+        const int kblocks = GROUPED ? decode_item<Cfg::BN, Cfg::BK, true, true>(item, p, &tmA, &tmB, &tmC, rank).kblocks
+                                    : p.L / Cfg::BK;
         // both CTAs' epilogues have drained this accumulator
         if (!mbar_wait_bounded_cluster(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
           ok = false;
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     for (int item = unit; item < num_items; item += units) {
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
-      const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, false, true>(item, p, &tmA, &tmB, &tmC, rank);
+      const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, GROUPED, true>(item, p, &tmA, &tmB, &tmC, rank);
       epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(acc * Cfg::BN), quarter, lane, ebuf, pol_c);
       tc_fence_before();
       __syncwarp();
@@ -272,12 +278,18 @@ __global__ void __launch_bounds__(kThreads2, 1)
   cluster_sync();
 }
 
-template <bool TF32>
+template <bool TF32, bool GROUPED>
 cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                     int num_sms, cudaStream_t st) {
   using Cfg = Tc2Cfg<TF32>;
-  auto kern = leaf_tc2_kernel<TF32>;
-  const int64_t items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / (2 * kBM)) * (a.L / Cfg::BN);
+  auto kern = leaf_tc2_kernel<TF32, GROUPED>;
+  int64_t items;
+  if constexpr (GROUPED) {
+    if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
+    items = a.total_items;
+  } else {
+    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / (2 * kBM)) * (a.L / Cfg::BN);
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
@@ -315,7 +327,15 @@ bool leaf_tc2_fits(const LeafTcArgs& a) { return a.L % 256 == 0; }
 cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                             const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t st) {
   if (!leaf_tc2_fits(a)) return cudaErrorInvalidValue;
-  return tf32 ? launch2<true>(a, tmA, tmB, tmC, num_sms, st) : launch2<false>(a, tmA, tmB, tmC, num_sms, st);
+  return tf32 ? launch2<true, false>(a, tmA, tmB, tmC, num_sms, st)
+              : launch2<false, false>(a, tmA, tmB, tmC, num_sms, st);
+}
+
+cudaError_t launch_leaf_tc2_grouped(const LeafTcArgs& a, bool tf32, int num_sms, cudaStream_t st) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  return tf32 ? launch2<true, true>(a, &none, &none, &none, num_sms, st)
+              : launch2<false, true>(a, &none, &none, &none, num_sms, st);
 }
 
 }  // namespace stark

@@ -214,7 +214,8 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       std::memset(&g, 0, sizeof(g));
       g.tmA = p->tmA;
       if (tf32) {
-        if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn)) return STARK_EUNSUPPORTED;
+        // 256-wide members run CTA pairs: each CTA loads 128 Y rows
+        if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn == 256 ? 128 : bn)) return STARK_EUNSUPPORTED;
       } else {
         g.tmB = p->tmB;
       }
@@ -228,7 +229,7 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       g.n = tc[k]->n;
       g.ldc = tc[k]->ld;
       g.use_tma_c = make_tmap_c(&g.tmC, g.C, g.n, g.ldc) ? 1 : 0;
-      items += p->P * (p->L / 128) * (p->L / bn);
+      items += bn == 256 ? p->P * (p->L / 256) * (p->L / 256) : p->P * (p->L / 128) * (p->L / 128);
     }
     if (split == (int)tc.size()) {
       items_wide = items;
@@ -244,7 +245,7 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       a.groups = slot.d_desc;
       a.ngroups = split;
       a.total_items = (int32_t)items_wide;
-      if (launch_leaf_tc_grouped(a, tf32, 256, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
+      if (launch_leaf_tc2_grouped(a, tf32, s->num_sms, st) != cudaSuccess) return STARK_ECUDA;
     }
     if (split < (int)tc.size()) {
       a.groups = slot.d_desc + split;

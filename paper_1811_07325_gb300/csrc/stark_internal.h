@@ -129,15 +129,19 @@ cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CU
 // planes holding integers, combined into an int64 C (a.C reinterpreted).
 cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, int bn,
                                int num_sms, cudaStream_t s);
-// Grouped launch over a.groups (tensor maps taken from the descriptors).
+// Grouped single-CTA launch over a.groups (tensor maps taken from the
+// descriptors), 128 x 128 tiles (bn == 128 only).
 cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int num_sms, cudaStream_t s);
-int leaf_tc_smem_bytes(bool tf32, int bn);
 // 3xBF16 / 3xTF32 leaves on CTA pairs sharing one cta_group::2 MMA of
 // 256 x 256 (requires L a multiple of 256).  The tf32 Y map's box is 128
 // rows (each CTA stages half of the 256 columns).
 bool leaf_tc2_fits(const LeafTcArgs& a);
 cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                             const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t s);
+// Grouped CTA-pair launch over a.groups: every member's L a multiple of 256,
+// items numbered per member as leaf * (L/256)^2 + row * (L/256) + column of
+// 256 x 256 pair tiles; tf32 members' Y maps with 128-row boxes.
+cudaError_t launch_leaf_tc2_grouped(const LeafTcArgs& a, bool tf32, int num_sms, cudaStream_t s);
 
 struct LeafCcArgs {
   int32_t P, L, leaf_begin, leaf_end;

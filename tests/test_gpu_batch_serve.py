@@ -33,7 +33,8 @@ def check(C, A, B, L, dtype="F32_SPLIT_BF16"):
 
 @pytest.mark.parametrize("sizes,depth,dtype", [([512, 768, 1000, 300, 1536], -1, "F32_SPLIT_BF16"),
                                                ([1024, 2048, 512, 1536], 1, "F32_SPLIT_BF16"),
-                                               ([640, 384, 1100], -1, "F32_SPLIT_TF32")])
+                                               ([640, 384, 1100], -1, "F32_SPLIT_TF32"),
+                                               ([1000, 640, 2048, 384], 1, "F32_SPLIT_TF32")])
 def test_batch_matches_oracle_and_replays(stark_lib, sizes, depth, dtype):
     S = stark_lib
     dt = S.DType[dtype]
