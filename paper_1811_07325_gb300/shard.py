@@ -4,7 +4,9 @@ The 7^d leaf products of one recursion tree are independent (the paper runs
 them as parallel tasks, Sec. III-C and Alg. 4); each rank computes the leaves
 of its share with ``stark_mul_leaves`` (its partial C is the sum of those
 leaves' signed combine contributions), and one sum all-reduce over the ranks
-gives every rank C = A.B.  This is the only exchange the path has.
+gives every rank C = A.B (``mul_sharded``), or one sum reduce-scatter gives
+each rank its block of rows of C (``mul_sharded_rows``).  That reduction is
+the only exchange the path has.
 
 Argument marshalling only: the products run in libstark.so; the reduction
 is torch.distributed's (NCCL on GPUs).
@@ -34,3 +36,33 @@ def mul_sharded(plan, A, B, C, group=None, stream=None):
     plan.mul_leaves(A, B, begin, end, C=C, stream=stream)
     dist.all_reduce(C, op=dist.ReduceOp.SUM, group=group)
     return C
+
+
+def row_block(n: int, world: int, rank: int) -> tuple[int, int]:
+    """Rows [begin, end) of C held by ``rank`` after ``mul_sharded_rows``:
+    blocks of ceil(n / world) rows, the last ones shorter or empty."""
+    if world <= 0 or not 0 <= rank < world or n < 0:
+        raise ValueError("bad world/rank/n")
+    rb = -(-n // world)
+    return min(rank * rb, n), min((rank + 1) * rb, n)
+
+
+def mul_sharded_rows(plan, A, B, group=None, stream=None):
+    """Rows of C = A @ B, one block per rank of ``group``: local leaves into a
+    partial C, then one sum reduce-scatter over row blocks.
+
+    Returns ``(begin, end, rows)``: ``rows`` holds C[begin:end] (a view of a
+    ceil(n / world) x n buffer; rows past ``end - begin`` are padding)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    n = plan.n
+    rb = -(-n // world)
+    partial = torch.zeros((world * rb, n), dtype=A.dtype, device=A.device)
+    begin, end = leaf_range(plan.leaves, world, rank)
+    plan.mul_leaves(A, B, begin, end, C=partial[:n], stream=stream)
+    out = torch.empty((rb, n), dtype=A.dtype, device=A.device)
+    dist.reduce_scatter_tensor(out, partial, op=dist.ReduceOp.SUM, group=group)
+    r0, r1 = row_block(n, world, rank)
+    return r0, r1, out

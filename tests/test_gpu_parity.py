@@ -560,7 +560,10 @@ def test_mul_sharded_single_rank_nccl(S, tmp_path):
         with S.Plan(n, 2, S.DType.I64) as p:
             C = torch.empty((n, n), dtype=torch.int64, device="cuda")
             shard.mul_sharded(p, dev(A), dev(B), C)
+            r0, r1, rows = shard.mul_sharded_rows(p, dev(A), dev(B))
             torch.cuda.synchronize()
-        assert np.array_equal(C.cpu().numpy(), oracle.gemm_classical(A, B))
+        want = oracle.gemm_classical(A, B)
+        assert np.array_equal(C.cpu().numpy(), want)
+        assert (r0, r1) == (0, n) and np.array_equal(rows[:n].cpu().numpy(), want)
     finally:
         dist.destroy_process_group()

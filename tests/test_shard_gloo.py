@@ -69,7 +69,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, n, depth, npad, out_path, fail_rank):
+def _worker(rank, world, port, n, depth, npad, out_path, fail_rank, rows=False):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -85,8 +85,13 @@ def _worker(rank, world, port, n, depth, npad, out_path, fail_rank):
         if rank == fail_rank:
             raise SystemExit(3)  # this rank dies before the collective
         try:
-            shard.mul_sharded(CpuLeafPlan(n, depth, npad), A, B, C)
-            np.save(f"{out_path}.{rank}.npy", C.numpy())
+            if rows:
+                r0, r1, blk = shard.mul_sharded_rows(CpuLeafPlan(n, depth, npad), A, B)
+                np.save(f"{out_path}.{rank}.npy", blk[:r1 - r0].numpy())
+                np.save(f"{out_path}.{rank}.span.npy", np.array([r0, r1]))
+            else:
+                shard.mul_sharded(CpuLeafPlan(n, depth, npad), A, B, C)
+                np.save(f"{out_path}.{rank}.npy", C.numpy())
         except Exception as e:  # the collective must fail, not hang
             with open(f"{out_path}.{rank}.err", "w") as f:
                 f.write(type(e).__name__)
@@ -103,6 +108,31 @@ def test_two_ranks_all_reduce_to_product(tmp_path, n, depth, npad):
     want = oracle.gemm_classical(synth.integers(n, 77, 0, -16, 16), synth.integers(n, 77, 1, -16, 16))
     for r in range(2):
         assert np.array_equal(np.load(f"{out}.{r}.npy"), want)
+
+
+@pytest.mark.parametrize("n,depth,npad", [(40, 2, 64), (33, 1, 64)])
+def test_two_ranks_reduce_scatter_rows(tmp_path, n, depth, npad):
+    # each rank ends with its block of rows of the exact product; the blocks
+    # tile [0, n) (n = 33: blocks of 17 and 16 rows)
+    import oracle
+    out = str(tmp_path / "c")
+    mp.start_processes(_worker, args=(2, _free_port(), n, depth, npad, out, -1, True), nprocs=2,
+                       start_method="spawn")
+    want = oracle.gemm_classical(synth.integers(n, 77, 0, -16, 16), synth.integers(n, 77, 1, -16, 16))
+    spans = [tuple(np.load(f"{out}.{r}.span.npy")) for r in range(2)]
+    assert spans[0][0] == 0 and spans[0][1] == spans[1][0] and spans[1][1] == n
+    for r, (r0, r1) in enumerate(spans):
+        assert np.array_equal(np.load(f"{out}.{r}.npy"), want[r0:r1])
+
+
+def test_row_block_partitions():
+    for n in (0, 1, 33, 64, 1000):
+        for world in (1, 2, 3, 8):
+            spans = [shard.row_block(n, world, r) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+    with pytest.raises(ValueError):
+        shard.row_block(4, 2, 2)
 
 
 def test_failed_rank_is_detected_not_hung(tmp_path):
