@@ -155,6 +155,35 @@ def cpu_baseline(n, seed, budget_s=12.0, rows_cap=4096):
                       f"{t:.1f} s on {threads} OpenMP threads"}
 
 
+def oracle_timings(seed):
+    """The oracle's own times at the smaller configurations, beside the GPU:
+    the classical FP64 product on all host cores (n = 1024, 4096) and the
+    serial FP64 Strassen recursion (Alg. 1) on one core (n = 1024 at depth 3,
+    n = 2048 at depth 3), the latter scaled to n = 16384 at depth 6 (the same
+    leaf side, 256) by 7^3 and labelled as extrapolated."""
+    import oracle
+    from paper_1811_07325_gb300 import synth
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"classical_cores": threads, "strassen_cores": 1}
+
+    def timed(f):
+        t0 = time.perf_counter()
+        f()
+        return time.perf_counter() - t0
+    for n in (1024, 4096):
+        A, B = synth.uniform(n, seed, 0), synth.uniform(n, seed, 1)
+        t = timed(lambda: oracle.gemm_classical(A, B))
+        out[f"classical_n{n}_s"] = t
+        out[f"classical_n{n}_tflops"] = 2.0 * n ** 3 / t / 1e12
+    for n in (1024, 2048):
+        A, B = synth.uniform(n, seed, 0), synth.uniform(n, seed, 1)
+        t = timed(lambda: oracle.strassen(A, B, 3))
+        out[f"strassen_n{n}_d3_s"] = t
+        out[f"strassen_n{n}_d3_effective_tflops"] = 2.0 * n ** 3 / t / 1e12
+    out["strassen_n16384_d6_s_extrapolated"] = out["strassen_n2048_d3_s"] * 7 ** 3
+    return out
+
+
 def run_batch(args, stark, synth, torch):
     """Batched form: 64 products, n drawn from {512, ..., 4096}, FP32 U[-1,1],
     3xBF16, autotuned depth; one grouped graph-replayed launch per step,
@@ -328,6 +357,7 @@ def main():
     ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-oracle-timings", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=600)
     args = ap.parse_args()
@@ -593,6 +623,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, args.seed)
+        if not args.no_oracle_timings:
+            cpu["oracle_timings"] = oracle_timings(args.seed)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
