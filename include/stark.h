@@ -68,14 +68,15 @@ typedef struct stark_plan_s *stark_plan_t;
 /* What a plan decided; filled by stark_plan_get_info. */
 typedef struct {
   int64_t n;               /* problem side                                              */
-  int64_t n_pad;           /* padded side: multiple of 2^depth * tile granularity       */
+  int64_t n_pad;           /* recursion's padded side: multiple of 2^depth * granularity */
   int64_t leaf;            /* L = n_pad / 2^depth                                        */
   int32_t depth;           /* recursion levels                                           */
   int32_t dtype;           /* stark_dtype                                                 */
   int64_t leaves;          /* 7^depth                                                    */
   int64_t workspace_bytes; /* device bytes the plan owns (leaf operands, tables, ...)    */
   int32_t tile_m, tile_n;  /* leaf GEMM output tile                                      */
-  int32_t reserved[6];
+  int32_t peel;            /* edge rows/columns done classically (STARK_PLAN_PEEL), else 0 */
+  int32_t reserved[5];
 } stark_plan_info;
 
 /* ----------------------------------------------------------------- plans */
@@ -92,6 +93,23 @@ typedef struct {
  * Errors: EINVAL (n < 0 or > 2^20, depth < -1 or > 4, unknown dtype, out == NULL),
  * ENOMEM, ECUDA, EUNSUPPORTED (current device is not a GB300 / sm_103). */
 STARK_API stark_status stark_plan(int64_t n, int depth, stark_dtype dtype, stark_plan_t *out);
+
+/* Plan options for stark_plan_ex.
+ * STARK_PLAN_PEEL: edge peeling instead of padding for sizes the tiling does
+ *   not divide.  With g = 2^depth * 128 (64 for F64/I64), n = m + r and m the
+ *   largest multiple of g not above n, the recursion runs on the m x m core
+ *   of A and B (no padding) and three classical products on the CUDA cores
+ *   finish C: C[:m,:m] += A[:m,m:] B[m:,:m], C[:m,m:] = A[:m,:] B[:,m:],
+ *   C[m:,:] = A[m:,:] B (block form of A B; fp32 FMA for the split dtypes,
+ *   fp64, or wrapping int64).  Padding costs (n_pad^3 - n^3) extra tensor
+ *   work; peeling costs about 6 n^2 r CUDA-core operations, so it pays for
+ *   small r (n just above a multiple of g).  No effect when g divides n or
+ *   n < g; stark_plan_info.peel reports r. */
+#define STARK_PLAN_PEEL 1u
+
+/* stark_plan with options (a bitwise OR of STARK_PLAN_* flags; 0 is
+ * stark_plan).  Errors as stark_plan, and EINVAL for unknown flags. */
+STARK_API stark_status stark_plan_ex(int64_t n, int depth, stark_dtype dtype, unsigned flags, stark_plan_t *out);
 
 /* Release a plan and its workspace (waits for the device to finish using it).
  * NULL is accepted and ignored. */

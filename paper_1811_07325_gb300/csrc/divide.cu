@@ -188,13 +188,14 @@ template <typename Tin, int VEC>
 struct Loader {
   using Acc = typename AccOf<Tin>::type;
   const Tin* __restrict__ X;
-  int64_t n;
+  int64_t n;    // rows and columns read; zeros beyond
+  int64_t ld;   // row stride
   bool vec_ok;  // rows are VEC-aligned: vector loads allowed where in bounds
 
   __device__ __forceinline__ Vec<Acc, VEC> operator()(int64_t row, int64_t col) const {
     Vec<Acc, VEC> r;
     if (row < n && col + VEC <= n && vec_ok) {
-      const Tin* p = X + row * n + col;
+      const Tin* p = X + row * ld + col;
       if constexpr (sizeof(Tin) * VEC == 16) {
         const int4 raw = __ldcs(reinterpret_cast<const int4*>(p));
         const Tin* t = reinterpret_cast<const Tin*>(&raw);
@@ -207,7 +208,7 @@ struct Loader {
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; ++e)
-        r.v[e] = (row < n && col + e < n) ? (Acc)__ldcs(X + row * n + col + e) : Acc(0);
+        r.v[e] = (row < n && col + e < n) ? (Acc)__ldcs(X + row * ld + col + e) : Acc(0);
     }
     return r;
   }
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
   if (pos >= a.L * per_row) return;
   const int64_t i = pos / per_row;
   const int64_t j = (pos % per_row) * VEC;
-  const Loader<Tin, VEC> ld0{static_cast<const Tin*>(a.X), a.n, vec_ok != 0};
+  const Loader<Tin, VEC> ld0{static_cast<const Tin*>(a.X), a.n, a.ld, vec_ok != 0};
   using LoadT = std::conditional_t<TOP, TopLoader<Tin, VEC, SIDE>, Loader<Tin, VEC>>;
   LoadT ld;
   if constexpr (TOP) {
@@ -328,7 +329,8 @@ template <typename Tin, int OUT, int D, int SIDE, bool TOP>
 cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
   constexpr int VEC = 16 / (int)sizeof(Tin);  // one 16-byte load per quadrant
   if (a.L % VEC != 0) return cudaErrorInvalidValue;
-  const int vec_ok = (a.n % VEC == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+  if (a.ld < a.n) return cudaErrorInvalidValue;
+  const int vec_ok = (a.ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
   const int64_t threads = a.L * (a.L / VEC);
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;

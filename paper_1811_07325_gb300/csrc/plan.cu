@@ -258,7 +258,12 @@ stark_status stark_quadrant_table(int depth, int side, int32_t* count, int32_t* 
 }
 
 stark_status stark_plan(int64_t n, int depth, stark_dtype dt, stark_plan_t* out) {
+  return stark_plan_ex(n, depth, dt, 0u, out);
+}
+
+stark_status stark_plan_ex(int64_t n, int depth, stark_dtype dt, unsigned flags, stark_plan_t* out) {
   if (!out) return STARK_EINVAL;
+  if (flags & ~(unsigned)STARK_PLAN_PEEL) return STARK_EINVAL;
   *out = nullptr;
   if (n < 0 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;
   if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
@@ -269,7 +274,7 @@ stark_status stark_plan(int64_t n, int depth, stark_dtype dt, stark_plan_t* out)
     depth = (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
   auto* p = new (std::nothrow) stark_plan_s();
   if (!p) return STARK_ENOMEM;
-  stark_status st = plan_init(p, n, depth, dt);
+  stark_status st = plan_init(p, n, depth, dt, (flags & STARK_PLAN_PEEL) != 0);
   if (st != STARK_OK) {
     plan_release(p);
     delete p;
@@ -295,6 +300,7 @@ stark_status stark_plan_get_info(stark_plan_t p, stark_plan_info* info) {
   std::memset(info, 0, sizeof(*info));
   info->n = p->n;
   info->n_pad = p->npad;
+  info->peel = (int32_t)p->peel;
   info->leaf = p->L;
   info->depth = p->depth;
   info->dtype = p->dt;
@@ -571,13 +577,16 @@ stark_status stark_selftest_bounded_wait(uint64_t timeout_ns) {
 // ====================================================================== plan internals
 namespace stark {
 
-stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel) {
   p->n = n;
   p->depth = depth;
   p->dt = dt;
   p->is_tc = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
   p->esz = element_size(dt);
-  p->npad = padded_side(n, depth, dt);
+  const int64_t g = ((int64_t)1 << depth) * tile_granularity(dt);
+  p->peel = (peel && n >= g) ? n % g : 0;
+  const int64_t core = n - p->peel;  // the recursion's side; a multiple of g when peeled
+  p->npad = padded_side(core, depth, dt);
   p->L = p->npad >> depth;
   p->P = pow7i(depth);
   p->P_ws = p->P;
@@ -586,7 +595,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt) {
   p->num_sms = device_sm_count();
   if (p->L > 0x7FFFFFFF / 2) return STARK_EINVAL;
 
-  const int64_t ws = operand_bytes(n, depth, dt);
+  const int64_t ws = operand_bytes(core, depth, dt);
   if (cudaMalloc(&p->X, (size_t)(ws / 2)) != cudaSuccess || cudaMalloc(&p->Y, (size_t)(ws / 2)) != cudaSuccess) {
     cudaGetLastError();
     return STARK_ENOMEM;
@@ -669,8 +678,9 @@ static stark_status to_status(cudaError_t e) {
 stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top) {
   const int64_t npad = top >= 0 ? p->npad / 2 : p->npad;
   const int depth = top >= 0 ? p->depth - 1 : p->depth;
-  DivideArgs da{A, p->n, npad, p->L, p->X, nullptr, p->d_err, top};
-  DivideArgs db{B, p->n, npad, p->L, p->Y, nullptr, p->d_err, top};
+  // the core of A and B (all of them unless an edge is peeled), row stride n
+  DivideArgs da{A, core_side(p), npad, p->L, p->X, nullptr, p->d_err, top, p->n};
+  DivideArgs db{B, core_side(p), npad, p->L, p->Y, nullptr, p->d_err, top, p->n};
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
   if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
@@ -693,10 +703,17 @@ stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStre
   return plan_divide_top(p, A, B, s, -1);
 }
 
+// Whether leaves [lb, le) use the deterministic combine (stored M planes and
+// an ordered pass) rather than the fused epilogue.
+static bool plan_deterministic(const stark_plan_s* p, int64_t lb, int64_t le) {
+  return p->is_tc && p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P;
+}
+
 // Leaf products of leaves [lb, le) with the combine, operands in workspace
-// planes numbered from plane_base.
+// planes numbered from plane_base.  With a staging copy of C the products
+// land there; plan_run_accumulate moves them into C.
 static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le, int64_t plane_base,
-                                cudaStream_t s, bool copy_stage = true) {
+                                cudaStream_t s) {
   stark_status st = STARK_OK;
   if (p->is_tc) {
     LeafTcArgs a{};
@@ -708,16 +725,16 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     a.ctab = p->d_ctab;
     a.ccount = p->d_ccount;
     a.maxT = p->maxT;
-    const bool deterministic = p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P;
+    const bool deterministic = plan_deterministic(p, lb, le);
     const bool staged = !deterministic && plan_uses_cstage(p, C);
     a.C = static_cast<float*>(staged ? p->cstage : C);
     a.ldc = staged ? staged_ld(p->n) : p->n;
-    a.n = p->n;
+    a.n = core_side(p);  // C rows/columns the combine covers
     a.err = p->d_err;
     a.timeout_ns = p->timeout_ns;
     CUtensorMap tmC;
     std::memset(&tmC, 0, sizeof(tmC));
-    a.use_tma_c = (p->combine_mode == 0 && make_tmap_c(&tmC, a.C, p->n, a.ldc)) ? 1 : 0;
+    a.use_tma_c = (p->combine_mode == 0 && make_tmap_c(&tmC, a.C, core_side(p), a.ldc)) ? 1 : 0;
     if (deterministic) {
       a.store_m = 1;
       a.use_tma_c = 0;
@@ -747,9 +764,8 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA,
                                     a.row_bytes == 64 ? &p->tmB64 : &p->tmB, &tmC, tf32, p->bn, p->num_sms, s));
     }
-    if (st == STARK_OK && staged && copy_stage) st = plan_copy_cstage(p, C, s);
     if (st == STARK_OK && deterministic)
-      st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, p->n,
+      st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, core_side(p),
                                     static_cast<float*>(C), p->n, s));
   } else if (p->int_tc) {
     LeafTcArgs a{};
@@ -763,7 +779,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     a.maxT = p->maxT;
     a.C = static_cast<float*>(C);  // int64 C, reinterpreted by the integer epilogue
     a.ldc = p->n;
-    a.n = p->n;
+    a.n = core_side(p);
     a.err = p->d_err;
     a.timeout_ns = p->timeout_ns;
     st = to_status(launch_leaf_tc_int(a, &p->tmAi, &p->tmBi, p->int_bn, p->num_sms, s));
@@ -781,10 +797,35 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     a.maxT = p->maxT;
     a.C = C;
     a.ldc = p->n;
-    a.n = p->n;
+    a.n = core_side(p);
     st = to_status(p->dt == STARK_F64 ? launch_leaf_f64(a, s) : launch_leaf_i64(a, s));
   }
   return st;
+}
+
+// The peeled edge of a product with n = m + r (Ct: C or its staging copy,
+// row stride ldc): the rank-r update of the core and the two edge strips,
+//   C[:m, :m] += A[:m, m:] B[m:, :m],  C[:m, m:] = A[:m, :] B[:, m:],
+//   C[m:, :] = A[m:, :] B,
+// so that with the recursion's C[:m, :m] = A[:m, :m] B[:m, :m] every
+// element of C is the classical product's (block form of A B).
+static stark_status plan_border(stark_plan_s* p, const void* A, const void* B, void* Ct, int64_t ldc,
+                                cudaStream_t s) {
+  const int64_t n = p->n, m = core_side(p), r = p->peel;
+  const InType t = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
+  const int64_t e = (int64_t)p->esz;
+  auto in = [&](const void* base, int64_t row, int64_t col) {
+    return static_cast<const void*>(static_cast<const char*>(base) + (row * n + col) * e);
+  };
+  auto out = [&](int64_t row, int64_t col) { return static_cast<void*>(static_cast<char*>(Ct) + (row * ldc + col) * e); };
+  const BorderArgs parts[3] = {
+      {in(A, 0, m), n, in(B, m, 0), n, out(0, 0), ldc, m, m, r, 1},  // core update
+      {A, n, in(B, 0, m), n, out(0, m), ldc, m, r, n, 0},            // right strip
+      {in(A, m, 0), n, B, n, out(m, 0), ldc, r, n, n, 0},            // bottom strip
+  };
+  for (const BorderArgs& a : parts)
+    if (stark_status st = to_status(launch_border(a, t, s)); st != STARK_OK) return st;
+  return STARK_OK;
 }
 
 stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,
@@ -813,9 +854,16 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
       const int64_t lo = lb > b0 ? lb : b0, hi = le < b1 ? le : b1;
       if (lo >= hi) continue;
       st = plan_divide_top(p, A, B, s, top);
-      if (st == STARK_OK) st = plan_leaves(p, C, lo, hi, b0, s, top == last);
+      if (st == STARK_OK) st = plan_leaves(p, C, lo, hi, b0, s);
     }
   }
+  // the peeled edge, once per product (with the range that holds leaf 0, so
+  // the partial products of a leaf partition still sum to A B), then the
+  // staging copy into C
+  const bool staged = p->is_tc && !plan_deterministic(p, lb, le) && plan_uses_cstage(p, C);
+  if (st == STARK_OK && p->peel > 0 && lb == 0)
+    st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, s);
+  if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   if (ev) cudaEventRecord(ev[3], s);
   p->timing_active = false;
   return st;

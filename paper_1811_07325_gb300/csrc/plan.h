@@ -78,6 +78,7 @@ struct stark_plan_s {
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   int host_calls = 0;
+  int64_t peel = 0;           // edge rows/columns done classically (n = core + peel)
   int pend_set = -1;          // staging set whose copy out is not yet enqueued
   void* pend_C = nullptr;     // its host destination
   // staging copy of C (row pitch staged_ld(n)) for the tensor-core combine
@@ -91,7 +92,12 @@ struct stark_plan_s {
 };
 
 namespace stark {
-stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt);
+// peel: run the recursion on the largest m <= n that the tiling divides and
+// finish the r = n - m edge rows/columns with classical products (when n is
+// already a multiple, or smaller than one tile granule, nothing is peeled).
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel = false);
+// Side of the product the recursion covers (n minus the peeled edge).
+inline int64_t core_side(const stark_plan_s* p) { return p->n - p->peel; }
 void plan_release(stark_plan_s* p);
 // Enqueue C = sum over leaves [lb, le) of their combine contributions.
 stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, int64_t lb, int64_t le,

@@ -57,8 +57,8 @@ enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2, kOutBf16Exac
 enum InType { kInF32 = 0, kInF64 = 1, kInI64 = 2 };
 
 struct DivideArgs {
-  const void* X;      // n x n row-major input
-  int64_t n;          // input side
+  const void* X;      // n x n row-major input (row stride ld)
+  int64_t n;          // input side read (the core of a peeled product)
   int64_t npad;       // padded side (zeros beyond n)
   int64_t L;          // leaf side = npad >> depth
   void* out_hi;       // planes [P][L][L] (split: hi part; plain: the value)
@@ -67,11 +67,28 @@ struct DivideArgs {
   int top;            // >= 0: depth-first subtree; the input is read through the
                       // level-1 sum of product `top` (M1..M7 = 0..6) and npad is
                       // the subproblem's side (half the full padded side)
+  int64_t ld;         // row stride of X in elements (>= n)
 };
 
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
+// C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
+// elements) on the CUDA cores: the edges of a peeled product.  Element type
+// float (fp32 accumulate), double or int64 (wrapping); accumulate = 0
+// overwrites C.
+struct BorderArgs {
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  int64_t M, N, K;
+  int accumulate;
+};
+cudaError_t launch_border(const BorderArgs& a, InType t, cudaStream_t s);
+
 // Deterministic combine of stored leaf products: C_q = sum over leaves l
 // (ascending) of W_d[q, l] * M_l, every element written once.  M planes are
 // [leaves][L][L] fp32 for leaves [0, P); depth <= 3.

@@ -49,12 +49,13 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("leaf", ctypes.c_int64),
                 ("depth", ctypes.c_int32), ("dtype", ctypes.c_int32), ("leaves", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("peel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _i64, _i32, _vp, _ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int
 _SIGS = {
     "stark_plan": ([_i64, _ci, _ci, ctypes.POINTER(_vp)], _ci),
+    "stark_plan_ex": ([_i64, _ci, _ci, ctypes.c_uint, ctypes.POINTER(_vp)], _ci),
     "stark_plan_destroy": ([_vp], _ci),
     "stark_plan_get_info": ([_vp, ctypes.POINTER(PlanInfo)], _ci),
     "stark_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
@@ -145,9 +146,13 @@ class _CudaBuffer:
 class Plan:
     """A plan for n x n products (``stark_plan``)."""
 
-    def __init__(self, n: int, depth: int = -1, dtype: DType = DType.F32_SPLIT_BF16):
+    PEEL = 1  # STARK_PLAN_PEEL
+
+    def __init__(self, n: int, depth: int = -1, dtype: DType = DType.F32_SPLIT_BF16, peel: bool = False):
+        """``peel``: edge peeling instead of padding (``STARK_PLAN_PEEL``)."""
         h = _vp()
-        _check(_lib.stark_plan(int(n), int(depth), int(dtype), ctypes.byref(h)), "stark_plan")
+        _check(_lib.stark_plan_ex(int(n), int(depth), int(dtype), self.PEEL if peel else 0, ctypes.byref(h)),
+               "stark_plan_ex")
         self._h = h
         info = PlanInfo()
         _check(_lib.stark_plan_get_info(h, ctypes.byref(info)), "stark_plan_get_info")
@@ -155,6 +160,7 @@ class Plan:
         self.dtype = DType(info.dtype)
         self.leaves, self.workspace_bytes = info.leaves, info.workspace_bytes
         self.tile = (info.tile_m, info.tile_n)
+        self.peel = info.peel
 
     def close(self):
         if getattr(self, "_h", None):

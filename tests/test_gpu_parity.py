@@ -434,6 +434,82 @@ def test_leaf_partition_sums_to_product(S):
         assert np.array_equal(total.cpu().numpy(), oracle.gemm_classical(A, B))
 
 
+# ----------------------------------------------------------------- peeling
+@pytest.mark.parametrize("dtype,n,d,combine,dfs,peel", [
+    ("F32_SPLIT_BF16", 1025, 1, 0, False, 1),    # n % 4 != 0: staged C
+    ("F32_SPLIT_BF16", 2049, 2, 0, False, 1),
+    ("F32_SPLIT_BF16", 1300, 1, 0, False, 20),
+    ("F32_SPLIT_BF16", 777, 0, 0, False, 9),
+    ("F32_SPLIT_BF16", 2050, 2, 2, False, 2),    # deterministic combine
+    ("F32_SPLIT_BF16", 2060, 2, 0, True, 12),    # depth-first traversal
+    ("F32_SPLIT_BF16", 1100, 1, 1, False, 76),   # vector-atomic combine
+    ("F32_SPLIT_TF32", 1030, 1, 0, False, 6),
+    ("F64", 1000, 2, 0, False, 232),
+    ("F64", 130, 1, 0, False, 2)])
+def test_peeled_edge_matches_oracle(S, dtype, n, d, combine, dfs, peel):
+    # recursion on the m x m core, classical products for the r-wide edge:
+    # every element against the FP64 oracle, as the padded plan
+    A = synth.normal(n, 95, 0) if dtype != "F64" else synth.uniform(n, 95, 0)
+    B = synth.normal(n, 95, 1) if dtype != "F64" else synth.uniform(n, 95, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype], peel=True) as p:
+        assert p.peel == peel and p.n_pad == n - peel
+        p.set_combine(combine)
+        if dfs:
+            p.set_traversal(True)
+        C = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        L = p.leaf
+    with S.Plan(n, d, S.DType[dtype]) as q:
+        assert q.peel == 0 and q.n_pad > n
+        Cpad = q.mul(dA, dB).cpu().numpy()
+        Lpad = q.leaf
+    if dtype == "F64":
+        err = np.abs(C - want).max()
+        assert err <= higham_bound(n, d, A, B), err
+        assert err / (np.linalg.norm(A) * np.linalg.norm(B)) <= 1e-12
+    else:
+        an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+        check_split(C, want, an, bn, dtype, L=L)
+        # the edge itself is a plain fp32 product: far inside the split bound
+        edge = np.abs(C[:, n - peel:] - want[:, n - peel:]).max() / (an * bn)
+        assert edge <= 1e-8, edge
+        # the padded plan splits differently (other leaf side): same bound
+        check_split(Cpad, want, an, bn, dtype, L=Lpad)
+
+
+@pytest.mark.parametrize("n,d,bound", [(1029, 2, 0), (300, 1, 0), (1100, 2, 16)])
+def test_peeled_int64_exact_and_leaf_ranges(S, n, d, bound):
+    # int64 (CUDA cores, or bf16 tensor cores with a declared bound): exact;
+    # partial products over a leaf partition still sum to A B (the edge is
+    # added once, with the range that holds leaf 0)
+    A = synth.integers(n, 97, 0, -16, 16)
+    B = synth.integers(n, 97, 1, -16, 16)
+    want = oracle.gemm_classical(A, B)
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType.I64, peel=True) as p:
+        assert p.peel > 0
+        if bound:
+            p.set_input_bound(bound)
+        assert np.array_equal(p.mul(dA, dB).cpu().numpy(), want)
+        cuts = [0, 3, p.leaves // 2, p.leaves]
+        total = torch.zeros((n, n), dtype=torch.int64, device="cuda")
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            total += p.mul_leaves(dA, dB, a, b)
+        p.check()
+        assert np.array_equal(total.cpu().numpy(), want)
+
+
+def test_peel_is_a_no_op_where_nothing_is_left(S):
+    for n, d in ((1024, 1), (100, 1)):  # g divides n; n below one granule
+        with S.Plan(n, d, S.DType.F32_SPLIT_BF16, peel=True) as p:
+            assert p.peel == 0
+    import ctypes
+    h = ctypes.c_void_p()
+    assert S._lib.stark_plan_ex(64, 1, int(S.DType.F64), 0x80, ctypes.byref(h)) == S.Status.EINVAL  # unknown flag
+
+
 def test_mul_host_matches_device(S):
     n = 777
     A = synth.normal(n, 51, 0)
