@@ -236,6 +236,36 @@ def run_batch(args, stark, synth, torch):
             "graph_replays": info["graph_replays"]}
 
 
+def run_peel(args, stark, synth, torch):
+    """Sizes just above a multiple of the tile granularity: padding to the next
+    multiple against peeling the edge (STARK_PLAN_PEEL), depth 2, 3xBF16."""
+    out = {"depth": 2}
+    for n in (4097, 16385):
+        A = torch.from_numpy(synth.normal(n, args.seed + 5, 0)).cuda()
+        B = torch.from_numpy(synth.normal(n, args.seed + 5, 1)).cuda()
+        C = torch.empty_like(A)
+        row = {}
+        for label, peel in (("pad", False), ("peel", True)):
+            with stark.Plan(n, 2, stark.DType.F32_SPLIT_BF16, peel=peel) as p:
+                for _ in range(2):
+                    p.mul(A, B, C)
+                p.check()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(5):
+                    p.mul(A, B, C)
+                e1.record()
+                torch.cuda.synchronize()
+                p.check()
+                ms = e0.elapsed_time(e1) / 5
+                row[label] = {"ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "recursion_side": p.n_pad,
+                              "edge": p.peel}
+        out[f"n{n}"] = row
+        del A, B, C
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_serve(args, stark, synth, torch):
     """Served form: Poisson arrivals (200/s), n log-uniform in [256, 8192],
     FP32 N(0,1), 3xBF16, device budget 150 GB; latency from submission to
@@ -619,6 +649,9 @@ def main():
         batch = run_batch(args, stark, synth, torch)
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, stark, synth, torch)
+    peel = None
+    if rank == 0 and not args.no_batch:
+        peel = run_peel(args, stark, synth, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -638,7 +671,7 @@ def main():
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
                "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32, "int64": int64,
-               "batch": batch, "serve": serve,
+               "batch": batch, "serve": serve, "peel": peel,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     plan.close()

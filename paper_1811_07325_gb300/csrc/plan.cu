@@ -810,7 +810,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
 // so that with the recursion's C[:m, :m] = A[:m, :m] B[:m, :m] every
 // element of C is the classical product's (block form of A B).
 static stark_status plan_border(stark_plan_s* p, const void* A, const void* B, void* Ct, int64_t ldc,
-                                cudaStream_t s) {
+                                bool deterministic, cudaStream_t s) {
   const int64_t n = p->n, m = core_side(p), r = p->peel;
   const InType t = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   const int64_t e = (int64_t)p->esz;
@@ -818,13 +818,20 @@ static stark_status plan_border(stark_plan_s* p, const void* A, const void* B, v
     return static_cast<const void*>(static_cast<const char*>(base) + (row * n + col) * e);
   };
   auto out = [&](int64_t row, int64_t col) { return static_cast<void*>(static_cast<char*>(Ct) + (row * ldc + col) * e); };
+  // the strips are added into zeros (the deterministic combine does not
+  // clear C), so their K can be split across blocks, except where results
+  // must be bitwise reproducible
+  const int split = deterministic ? 0 : 1;
+  if (cudaMemset2DAsync(out(0, m), (size_t)(ldc * e), 0, (size_t)(r * e), (size_t)m, s) != cudaSuccess ||
+      cudaMemset2DAsync(out(m, 0), (size_t)(ldc * e), 0, (size_t)(n * e), (size_t)r, s) != cudaSuccess)
+    return to_status(cudaGetLastError());
   const BorderArgs parts[3] = {
-      {in(A, 0, m), n, in(B, m, 0), n, out(0, 0), ldc, m, m, r, 1},  // core update
-      {A, n, in(B, 0, m), n, out(0, m), ldc, m, r, n, 0},            // right strip
-      {in(A, m, 0), n, B, n, out(m, 0), ldc, r, n, n, 0},            // bottom strip
+      {in(A, 0, m), n, in(B, m, 0), n, out(0, 0), ldc, m, m, r, 1, split, 0},  // core update
+      {A, n, in(B, 0, m), n, out(0, m), ldc, m, r, n, 1, split, 0},            // right strip
+      {in(A, m, 0), n, B, n, out(m, 0), ldc, r, n, n, 1, split, 0},            // bottom strip
   };
   for (const BorderArgs& a : parts)
-    if (stark_status st = to_status(launch_border(a, t, s)); st != STARK_OK) return st;
+    if (stark_status st = to_status(launch_border(a, t, p->num_sms, s)); st != STARK_OK) return st;
   return STARK_OK;
 }
 
@@ -862,7 +869,8 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
   // staging copy into C
   const bool staged = p->is_tc && !plan_deterministic(p, lb, le) && plan_uses_cstage(p, C);
   if (st == STARK_OK && p->peel > 0 && lb == 0)
-    st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, s);
+    st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, plan_deterministic(p, lb, le),
+                     s);
   if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   if (ev) cudaEventRecord(ev[3], s);
   p->timing_active = false;

@@ -76,7 +76,7 @@ cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, O
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
 // elements) on the CUDA cores: the edges of a peeled product.  Element type
 // float (fp32 accumulate), double or int64 (wrapping); accumulate = 0
-// overwrites C.
+// overwrites C (then K is not split).  kc is set by the launcher.
 struct BorderArgs {
   const void* A;
   int64_t lda;
@@ -86,8 +86,10 @@ struct BorderArgs {
   int64_t ldc;
   int64_t M, N, K;
   int accumulate;
+  int split;   // 1: K may be split across blocks (atomic adds; fp32 order varies)
+  int64_t kc;  // K per block (grid z splits K), set by the launcher
 };
-cudaError_t launch_border(const BorderArgs& a, InType t, cudaStream_t s);
+cudaError_t launch_border(const BorderArgs& a, InType t, int num_sms, cudaStream_t s);
 
 // Deterministic combine of stored leaf products: C_q = sum over leaves l
 // (ascending) of W_d[q, l] * M_l, every element written once.  M planes are

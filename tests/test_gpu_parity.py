@@ -459,6 +459,8 @@ def test_peeled_edge_matches_oracle(S, dtype, n, d, combine, dfs, peel):
         if dfs:
             p.set_traversal(True)
         C = p.mul(dA, dB).cpu().numpy()
+        if combine == 2:  # deterministic: the edge is computed without atomics too
+            assert np.array_equal(p.mul(dA, dB).cpu().numpy().view(np.uint32), C.view(np.uint32))
         p.check()
         L = p.leaf
     with S.Plan(n, d, S.DType[dtype]) as q:
