@@ -386,6 +386,7 @@ def main():
                     help="leaf schedule: 0 single CTAs, 1 multicast pairs, 2 cta_group::2 pairs")
     ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
+    ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-oracle-timings", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -425,6 +426,8 @@ def main():
         plan.set_combine(args.combine)
     if args.deep_pipeline >= 0:
         plan.set_pipeline(bool(args.deep_pipeline))
+    if args.raster >= 0:
+        plan.set_raster(args.raster)
     stream = torch.cuda.current_stream()
 
     def barrier():

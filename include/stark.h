@@ -211,6 +211,14 @@ STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
  * combine's order.  Errors: EINVAL (null plan, mode outside 0..2). */
 STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
 
+/* Order of a leaf's output tiles in the split-fp32 leaf launch: band > 0
+ * runs them in bands of `band` tile columns (row-major within a band), so
+ * the tiles in flight at one time share fewer B panels; 0 (default) is
+ * row-major over the whole leaf.  A band that does not divide the leaf's
+ * tile columns means row-major.  Results agree within fp32 rounding of the
+ * combine's order.  Errors: EINVAL (null plan, band < 0 or > 4096). */
+STARK_API stark_status stark_plan_set_raster(stark_plan_t plan, int band);
+
 /* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1
  * stages K = 32 per step in four 48 KB buffers (64-byte swizzle), 0 stages
  * K = 64 in two 96 KB buffers (128-byte swizzle).  Same results up to the

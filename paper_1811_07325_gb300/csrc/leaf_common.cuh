@@ -57,15 +57,28 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     // tiles sharing one B tile; this CTA (cluster rank 0 or 1) computes the
     // upper or lower one
     const int tiles_n = p.L / BN;
-    const int per_leaf = (p.L / kBM / (PAIR ? 2 : 1)) * tiles_n;
+    const int tiles_m = p.L / kBM / (PAIR ? 2 : 1);
+    const int per_leaf = tiles_m * tiles_n;
     const int rem = item % per_leaf;
+    int row, col;
+    if (p.band > 0 && p.band < tiles_n && tiles_n % p.band == 0) {
+      // bands of p.band tile columns: the tiles that run at the same time
+      // share fewer B panels (L2 reuse of a leaf's Y planes)
+      const int per_band = tiles_m * p.band;
+      const int w = rem % per_band;
+      row = w / p.band;
+      col = (rem / per_band) * p.band + w % p.band;
+    } else {
+      row = rem / tiles_n;
+      col = rem % tiles_n;
+    }
     it.tA = tmA;
     it.tB = tmB;
     it.tC = tmC;
     it.leaf = p.leaf_begin + item / per_leaf;
     it.P = p.P;
-    it.m0 = PAIR ? ((rem / tiles_n) * 2 + (int)rank) * kBM : (rem / tiles_n) * kBM;
-    it.n0 = (rem % tiles_n) * BN;
+    it.m0 = PAIR ? (row * 2 + (int)rank) * kBM : row * kBM;
+    it.n0 = col * BN;
     it.kblocks = p.L / BK;
     it.tg = p.ctab + (int64_t)it.leaf * p.maxT;
     it.nt = p.ccount[it.leaf];

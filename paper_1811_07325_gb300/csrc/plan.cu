@@ -509,6 +509,12 @@ stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
   return STARK_OK;
 }
 
+stark_status stark_plan_set_raster(stark_plan_t p, int band) {
+  if (!p || band < 0 || band > 4096) return STARK_EINVAL;
+  p->raster_band = band;
+  return STARK_OK;
+}
+
 stark_status stark_plan_set_pipeline(stark_plan_t p, int deep) {
   if (!p || deep < 0 || deep > 1) return STARK_EINVAL;
   p->deep_pipeline = deep;
@@ -741,6 +747,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       tmC = p->tmM;
     }
     a.pair = (deterministic && p->pair_mode == 1) ? 0 : p->pair_mode;
+    a.band = p->raster_band;
     a.row_bytes = 128;
     if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256) {
       a.pair = 0;  // the 64-byte-row schedule runs single CTAs

@@ -134,6 +134,8 @@ struct LeafTcArgs {
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
   int32_t plane_base;  // leaf stored in workspace plane 0 (depth-first traversal); P = planes per half
+  int32_t band;        // > 0: a leaf's tiles run in bands of `band` tile columns (row-major inside a
+                       // band); 0 or not dividing the tile columns: row-major over the whole leaf
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;

@@ -69,6 +69,7 @@ _SIGS = {
     "stark_plan_set_combine": ([_vp, _ci], _ci),
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_pipeline": ([_vp, _ci], _ci),
+    "stark_plan_set_raster": ([_vp, _ci], _ci),
     "stark_plan_set_input_bound": ([_vp, _i64], _ci),
     "stark_plan_set_traversal": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
@@ -273,6 +274,10 @@ class Plan:
         CTA pairs sharing B tiles by multicast (3xBF16); 2 (default) CTA pairs
         on one cta_group::2 MMA of 256 x 256."""
         _check(_lib.stark_plan_set_pairing(self._h, int(mode)), "stark_plan_set_pairing")
+
+    def set_raster(self, band: int):
+        """Leaf tile order: bands of ``band`` tile columns (0: row-major)."""
+        _check(_lib.stark_plan_set_raster(self._h, int(band)), "stark_plan_set_raster")
 
     def set_pipeline(self, deep: bool):
         """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
