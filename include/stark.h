@@ -219,6 +219,14 @@ STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
  * combine's order.  Errors: EINVAL (null plan, band < 0 or > 4096). */
 STARK_API stark_status stark_plan_set_raster(stark_plan_t plan, int band);
 
+/* Layout of the 3xTF32 path's B operand (the leaf planes Y_l): mn = 0
+ * transposes the planes in place after the divide and reads them K-major;
+ * mn = 1 (default) keeps them row-major (K x N) and reads them MN-major with
+ * the 128-byte swizzle of 32-byte atoms, with no transpose pass.  Errors:
+ * EINVAL (null plan, mn outside 0..1), EUNSUPPORTED (mn = 1 on a plan of
+ * another dtype). */
+STARK_API stark_status stark_plan_set_tf32_layout(stark_plan_t plan, int mn);
+
 /* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1
  * stages K = 32 per step in four 48 KB buffers (64-byte swizzle), 0 stages
  * K = 64 in two 96 KB buffers (128-byte swizzle).  Same results up to the

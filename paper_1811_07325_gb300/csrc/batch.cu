@@ -185,8 +185,8 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     GroupDesc& g = b->host_desc[k];
     std::memset(&g, 0, sizeof(g));
     g.tmA = p->tmA;
-    if (dt == STARK_F32_SPLIT_TF32) {
-      // 256-wide members run CTA pairs: each CTA loads 128 Y rows
+    if (dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn) {
+      // K-major tf32 Y; 256-wide members run CTA pairs: each CTA loads 128 Y rows
       if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn == 256 ? 128 : bn)) st = STARK_EUNSUPPORTED;
     } else {
       g.tmB = p->tmB;
@@ -308,6 +308,7 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
       a.err = b->d_err;
       a.timeout_ns = kDefaultTimeoutNs;
       const bool tf32 = b->dt == STARK_F32_SPLIT_TF32;
+      a.b_mn = tf32 && b->plans[0]->tf32_mn;  // every member has the plan default
       if (b->split > 0) {  // 256-wide members
         a.groups = b->d_desc;
         a.ngroups = b->split;

@@ -35,12 +35,15 @@ constexpr int kThreads = 192;
 // bf16 per stage, twice the stages in the same space).
 // INT1: one exact bf16 product per K step (integer leaf operands), no lo
 // planes, int64 combine.
-template <int BN, int STAGES, bool TF32, int RB = 128, bool INT1 = false>
+// TMN: tf32 with the Y planes row-major (K x N), read MN-major in 128-byte
+// boxes with the 32-byte-atom swizzle (no transpose pass).
+template <int BN, int STAGES, bool TF32, int RB = 128, bool INT1 = false, bool TMN = false>
 struct TcCfg {
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int BK = RB / ESZ;                // K per stage: one swizzled A row
   static constexpr int A_BYTES = kBM * RB;           // one operand half tile (K-major)
-  static constexpr bool B_MN = !TF32;                // B operand MN-major (bf16) or K-major (tf32)
+  static constexpr bool B_MN = !TF32 || TMN;         // B operand MN-major (bf16, tf32 TMN) or K-major
+  static constexpr int B_SWZ = TF32 ? 1 : 0;         // MN descriptor swizzle (tf32: 32-byte atoms)
   static constexpr int W = B_MN ? RB / ESZ : BN;     // N elements per B TMA box
   static constexpr int NCHUNK = BN / W;              // B boxes per half tile
   static constexpr int CH_BYTES = B_MN ? BK * RB : BN * RB;  // bytes per B box
@@ -58,11 +61,11 @@ struct TcCfg {
   static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, B_MN>();
 };
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB, bool INT1>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB, bool INT1, bool TMN>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
-  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1>;
+  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1, TMN>;
   static_assert(!INT1 || (!TF32 && !GROUPED && !PAIR), "integer mode: bf16, single problem");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms
@@ -218,8 +221,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t a_lo = smem_desc_k<RB>(st + Cfg::A_BYTES + aoff);
             uint64_t b_hi, b_lo;
             if constexpr (Cfg::B_MN) {
-              b_hi = smem_desc_mn<RB>(st + Cfg::NHALF * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
-              b_lo = smem_desc_mn<RB>(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+              b_hi = smem_desc_mn<RB, Cfg::B_SWZ>(st + Cfg::NHALF * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+              b_lo = smem_desc_mn<RB, Cfg::B_SWZ>(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + boff,
+                                                  Cfg::CH_BYTES);
             } else {
               b_hi = smem_desc_k<RB>(st + Cfg::NHALF * Cfg::A_BYTES + boff);
               b_lo = smem_desc_k<RB>(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + boff);
@@ -293,10 +297,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (PAIR) cluster_sync();  // no CTA leaves while its peer may still write to it
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128, bool INT1 = false>
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128, bool INT1 = false,
+          bool TMN = false>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
-  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1>;
+  using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1, TMN>;
   static_assert(Cfg::B_BYTES == BN * RB, "B tile size");
   static_assert(!PAIR || (!GROUPED && Cfg::B_MN && Cfg::NCHUNK % 2 == 0), "paired mode: bf16, single problem");
   int64_t items;
@@ -308,7 +313,7 @@ cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtens
     if (PAIR && (a.L / kBM) % 2 != 0) return cudaErrorInvalidValue;
     items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM / (PAIR ? 2 : 1)) * (a.L / BN);
   }
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB, INT1>;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB, INT1, TMN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
@@ -358,6 +363,11 @@ cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CU
   // bf16, 256-wide tiles, 64-byte rows: four 48 KB stages instead of two 96 KB
   if (bn == 256 && !tf32 && a.row_bytes == 64)
     return launch_cfg<256, 4, false, false, false, 64>(a, tmA, tmB, tmC, num_sms, st);
+  if (tf32 && a.b_mn) {
+    if (bn == 256) return launch_cfg<256, 2, true, false, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
+    if (bn == 128) return launch_cfg<128, 3, true, false, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
+    return cudaErrorInvalidValue;
+  }
   if (bn == 256) {
     return tf32 ? launch_cfg<256, 2, true, false>(a, tmA, tmB, tmC, num_sms, st)
                 : launch_cfg<256, 2, false, false>(a, tmA, tmB, tmC, num_sms, st);
@@ -383,6 +393,7 @@ cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int n
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
   if (bn == 128) {
+    if (tf32 && a.b_mn) return launch_cfg<128, 3, true, true, false, 128, false, true>(a, &none, &none, &none, num_sms, st);
     return tf32 ? launch_cfg<128, 3, true, true>(a, &none, &none, &none, num_sms, st)
                 : launch_cfg<128, 3, false, true>(a, &none, &none, &none, num_sms, st);
   }

@@ -31,7 +31,8 @@ constexpr int kThreads2 = 192;
 // TF32: Y planes transposed to N x K beforehand, so the Y tile is K-major
 // like X (one 128-row box per half tile); bf16: Y row-major, MN-major, in
 // 128-byte-wide column boxes.
-template <bool TF32>
+// TMN: tf32 Y planes row-major, read MN-major with the 32-byte-atom swizzle.
+template <bool TF32, bool TMN = false>
 struct Tc2Cfg {
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int RB = 128;                        // bytes of one swizzled smem row
@@ -39,7 +40,8 @@ struct Tc2Cfg {
   static constexpr int BN = 256;                        // N of the pair MMA (accumulator columns)
   static constexpr int BNH = BN / 2;                    // Y columns staged by each CTA
   static constexpr int A_BYTES = kBM * RB;              // one X half tile (K-major), 16 KB
-  static constexpr bool B_MN = !TF32;
+  static constexpr bool B_MN = !TF32 || TMN;
+  static constexpr int B_SWZ = TF32 ? 1 : 0;            // MN descriptor swizzle (tf32: 32-byte atoms)
   static constexpr int W = B_MN ? RB / ESZ : BNH;       // Y columns per TMA box
   static constexpr int NCHUNK = BNH / W;                // Y boxes per half tile
   static constexpr int CH_BYTES = B_MN ? BK * RB : BNH * RB;
@@ -61,11 +63,11 @@ struct Tc2Cfg {
 
 // GROUPED: items of several problems (GroupDesc array, tensor maps in global
 // memory), as in the single-CTA kernel's grouped mode.
-template <bool TF32, bool GROUPED>
+template <bool TF32, bool GROUPED, bool TMN>
 __global__ void __launch_bounds__(kThreads2, 1)
     leaf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
-  using Cfg = Tc2Cfg<TF32>;
+  using Cfg = Tc2Cfg<TF32, TMN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
@@ -211,8 +213,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
             const uint64_t a_lo = smem_desc_k<Cfg::RB>(st + Cfg::A_BYTES + aoff);
             uint64_t b_hi, b_lo;
             if constexpr (Cfg::B_MN) {
-              b_hi = smem_desc_mn<Cfg::RB>(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
-              b_lo = smem_desc_mn<Cfg::RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
+              b_hi = smem_desc_mn<Cfg::RB, Cfg::B_SWZ>(st + 2 * Cfg::A_BYTES + boff, Cfg::CH_BYTES);
+              b_lo = smem_desc_mn<Cfg::RB, Cfg::B_SWZ>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff, Cfg::CH_BYTES);
             } else {
               b_hi = smem_desc_k<Cfg::RB>(st + 2 * Cfg::A_BYTES + boff);
               b_lo = smem_desc_k<Cfg::RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
@@ -278,11 +280,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
   cluster_sync();
 }
 
-template <bool TF32, bool GROUPED>
+template <bool TF32, bool GROUPED, bool TMN = false>
 cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                     int num_sms, cudaStream_t st) {
-  using Cfg = Tc2Cfg<TF32>;
-  auto kern = leaf_tc2_kernel<TF32, GROUPED>;
+  using Cfg = Tc2Cfg<TF32, TMN>;
+  auto kern = leaf_tc2_kernel<TF32, GROUPED, TMN>;
   int64_t items;
   if constexpr (GROUPED) {
     if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
@@ -327,6 +329,7 @@ bool leaf_tc2_fits(const LeafTcArgs& a) { return a.L % 256 == 0; }
 cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                             const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t st) {
   if (!leaf_tc2_fits(a)) return cudaErrorInvalidValue;
+  if (tf32 && a.b_mn) return launch2<true, false, true>(a, tmA, tmB, tmC, num_sms, st);
   return tf32 ? launch2<true, false>(a, tmA, tmB, tmC, num_sms, st)
               : launch2<false, false>(a, tmA, tmB, tmC, num_sms, st);
 }
@@ -334,6 +337,7 @@ cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const C
 cudaError_t launch_leaf_tc2_grouped(const LeafTcArgs& a, bool tf32, int num_sms, cudaStream_t st) {
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
+  if (tf32 && a.b_mn) return launch2<true, true, true>(a, &none, &none, &none, num_sms, st);
   return tf32 ? launch2<true, true>(a, &none, &none, &none, num_sms, st)
               : launch2<false, true>(a, &none, &none, &none, num_sms, st);
 }

@@ -102,9 +102,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // the K-major X planes a box is a 128-byte K slice of box_rows M rows; for
 // the MN-major Y planes it is a 128-byte N chunk of box_rows K rows.
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows,
-                      int row_bytes) {
+                      int row_bytes, bool atom32) {
   auto fn = encode_fn();
-  if (!fn || (row_bytes != 128 && row_bytes != 64)) return false;
+  if (!fn || (row_bytes != 128 && row_bytes != 64) || (atom32 && row_bytes != 128)) return false;
   const int esz = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(L * esz), (cuuint64_t)(L * L * esz)};
@@ -112,7 +112,8 @@ bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t 
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  atom32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B
+                         : row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -456,14 +457,7 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
   }
   p->ws_bytes += 2 * bytes;
   p->P_ws = planes;
-  p->has_maps64 = false;
-  p->has_mapbp = false;
-  if (p->is_tc) {
-    const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
-    if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * planes, 128) ||
-        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * planes, tf32 ? p->bn : 64))
-      return STARK_EUNSUPPORTED;
-  }
+  if (stark_status st = plan_operand_maps(p, planes); st != STARK_OK) return st;
   if (p->int_tc && (!make_tmap_planes(&p->tmAi, p->X, false, p->L, planes, 128) ||
                     !make_tmap_planes(&p->tmBi, p->Y, false, p->L, planes, 64)))
     return STARK_EUNSUPPORTED;
@@ -640,13 +634,25 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bo
     // C cannot be a TMA target: combine into a staging copy with an aligned pitch
     if (stark_status e = plan_ensure_cstage(p); e != STARK_OK) return e;
   }
-  if (p->is_tc) {
-    const bool tf32 = dt == STARK_F32_SPLIT_TF32;
-    if (!make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * p->P, 128) ||
-        !make_tmap_planes(&p->tmB, p->Y, tf32, p->L, 2 * p->P, tf32 ? p->bn : 64))
-      return STARK_EUNSUPPORTED;
-  }
-  return STARK_OK;
+  return plan_operand_maps(p, p->P);
+}
+
+stark_status plan_operand_maps(stark_plan_s* p, int64_t planes) {
+  p->has_maps64 = false;
+  p->has_mapbp = false;
+  if (!p->is_tc) return STARK_OK;
+  const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
+  // X: K-major 128-byte rows.  Y: bf16 MN-major 64 x 64 boxes; tf32 either
+  // MN-major 32 x 32 boxes with the 32-byte-atom swizzle, or (transposed
+  // planes) K-major boxes of a whole tile's rows
+  bool ok = make_tmap_planes(&p->tmA, p->X, tf32, p->L, 2 * planes, 128);
+  if (!tf32)
+    ok = ok && make_tmap_planes(&p->tmB, p->Y, false, p->L, 2 * planes, 64);
+  else if (p->tf32_mn)
+    ok = ok && make_tmap_planes(&p->tmB, p->Y, true, p->L, 2 * planes, 32, 128, true);
+  else
+    ok = ok && make_tmap_planes(&p->tmB, p->Y, true, p->L, 2 * planes, p->bn);
+  return ok ? STARK_OK : STARK_EUNSUPPORTED;
 }
 
 void plan_release(stark_plan_s* p) {
@@ -699,7 +705,7 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
   if (st != STARK_OK) return st;
   st = to_status(launch_divide(db, depth, 1, in, om, s));
   if (st != STARK_OK) return st;
-  if (p->dt == STARK_F32_SPLIT_TF32)  // the 3xTF32 leaf GEMM takes B K-major (N x K planes)
+  if (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn)  // K-major tf32 B: N x K planes
     st = to_status(launch_transpose_planes(static_cast<float*>(p->Y), p->L, 2 * p->P_ws, s));
   return st;
 }
@@ -748,6 +754,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     }
     a.pair = (deterministic && p->pair_mode == 1) ? 0 : p->pair_mode;
     a.band = p->raster_band;
+    a.b_mn = p->tf32_mn;
     a.row_bytes = 128;
     if (p->deep_pipeline && p->dt == STARK_F32_SPLIT_BF16 && p->bn == 256) {
       a.pair = 0;  // the 64-byte-row schedule runs single CTAs
@@ -761,12 +768,12 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     }
     const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
     if (a.pair == 2 && p->bn == 256 && leaf_tc2_fits(a)) {
-      // CTA pairs on one 256 x 256 MMA; tf32 needs Y boxes of 128 rows
-      if (tf32 && !p->has_mapbp) {
+      // CTA pairs on one 256 x 256 MMA; K-major tf32 needs Y boxes of 128 rows
+      if (tf32 && !p->tf32_mn && !p->has_mapbp) {
         if (!make_tmap_planes(&p->tmBp, p->Y, true, p->L, 2 * p->P_ws, 128)) return STARK_EUNSUPPORTED;
         p->has_mapbp = true;
       }
-      st = to_status(launch_leaf_tc2(a, &p->tmA, tf32 ? &p->tmBp : &p->tmB, &tmC, tf32, p->num_sms, s));
+      st = to_status(launch_leaf_tc2(a, &p->tmA, (tf32 && !p->tf32_mn) ? &p->tmBp : &p->tmB, &tmC, tf32, p->num_sms, s));
     } else {
       st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA,
                                     a.row_bytes == 64 ? &p->tmB64 : &p->tmB, &tmC, tf32, p->bn, p->num_sms, s));
@@ -927,6 +934,14 @@ stark_status plan_copy_cstage(const stark_plan_s* p, void* C, cudaStream_t s) {
 }
 
 }  // namespace stark
+
+extern "C" stark_status stark_plan_set_tf32_layout(stark_plan_t p, int mn) {
+  if (!p || mn < 0 || mn > 1) return STARK_EINVAL;
+  if (p->dt != STARK_F32_SPLIT_TF32) return mn ? STARK_EUNSUPPORTED : STARK_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
+  p->tf32_mn = mn;
+  return plan_operand_maps(p, p->P_ws);
+}
 
 extern "C" stark_status stark_plan_operands(stark_plan_t p, const void* A, const void* B, void* stream,
                                             const void** X, const void** Y) {

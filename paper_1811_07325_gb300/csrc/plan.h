@@ -58,6 +58,7 @@ struct stark_plan_s {
   int pair_mode = 2;     // leaf schedule where the tiling allows (L % 256 == 0): 2 CTA pairs on one
                          // cta_group::2 MMA, 1 paired CTAs with multicast B tiles, 0 single CTAs
   CUtensorMap tmBp;      // tf32 Y map with 128-row boxes for the pair MMA
+  int tf32_mn = 1;       // tf32 Y planes row-major, read MN-major (0: transposed, K-major)
   bool has_mapbp = false;
   int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
   int raster_band = 0;   // tile columns per raster band of a leaf (0: row-major)
@@ -97,6 +98,8 @@ namespace stark {
 // finish the r = n - m edge rows/columns with classical products (when n is
 // already a multiple, or smaller than one tile granule, nothing is peeled).
 stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel = false);
+// Tensor maps of the split dtypes' operand planes (for `planes` leaves per half).
+stark_status plan_operand_maps(stark_plan_s* p, int64_t planes);
 // Side of the product the recursion covers (n minus the peeled edge).
 inline int64_t core_side(const stark_plan_s* p) { return p->n - p->peel; }
 void plan_release(stark_plan_s* p);

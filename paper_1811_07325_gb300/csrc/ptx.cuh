@@ -382,14 +382,18 @@ __device__ __forceinline__ uint64_t smem_desc_k(uint32_t saddr) {
   d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
   return d;
 }
-template <int RB>
+// MN-major: SWZ overrides the swizzle code (1 = 128-byte swizzle with 32-byte
+// atoms, the layout a 32-bit MN-major operand takes; 0 = from RB).  The
+// 32-byte-atom pattern repeats every 4 rows of 128 bytes, so its K-direction
+// group stride is 512 bytes (8 rows for the 16-byte-atom swizzles).
+template <int RB, int SWZ = 0>
 __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t chunk_stride_bytes) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((chunk_stride_bytes >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((8 * RB) >> 4) << 32;
+  d |= (uint64_t)(((SWZ == 1 ? 4 : 8) * RB) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
+  d |= (uint64_t)(SWZ != 0 ? SWZ : (RB == 128 ? 2 : 4)) << 61;
   return d;
 }
 

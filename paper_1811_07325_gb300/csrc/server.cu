@@ -213,8 +213,8 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       GroupDesc& g = slot.h_desc[k];
       std::memset(&g, 0, sizeof(g));
       g.tmA = p->tmA;
-      if (tf32) {
-        // 256-wide members run CTA pairs: each CTA loads 128 Y rows
+      if (tf32 && !p->tf32_mn) {
+        // K-major tf32 Y; 256-wide members run CTA pairs: each CTA loads 128 Y rows
         if (!make_tmap_planes(&g.tmB, p->Y, true, p->L, 2 * p->P, bn == 256 ? 128 : bn)) return STARK_EUNSUPPORTED;
       } else {
         g.tmB = p->tmB;
@@ -239,6 +239,7 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
         cudaSuccess)
       return STARK_ECUDA;
     LeafTcArgs a{};
+    a.b_mn = tf32 && tc[0]->ws->tf32_mn;  // every workspace has the plan default
     a.err = s->d_err;
     a.timeout_ns = kDefaultTimeoutNs;
     if (split > 0) {

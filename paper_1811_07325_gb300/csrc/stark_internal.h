@@ -134,6 +134,8 @@ struct LeafTcArgs {
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
   int32_t plane_base;  // leaf stored in workspace plane 0 (depth-first traversal); P = planes per half
+  int32_t b_mn;        // tf32: 1 = Y planes row-major (K x N) read MN-major with 32-byte-atom
+                       // swizzle; 0 = Y planes transposed to N x K, read K-major
   int32_t band;        // > 0: a leaf's tiles run in bands of `band` tile columns (row-major inside a
                        // band); 0 or not dividing the tile columns: row-major over the whole leaf
   // grouped launch (batch): when groups != nullptr the fields above that
@@ -184,8 +186,11 @@ cudaError_t launch_wait_selftest(int* err, uint64_t timeout_ns, cudaStream_t s);
 void count_launch(int k = 1);
 int device_sm_count();
 bool device_is_sm100_family();
+// [planes][L][L] operand planes, boxes of row_bytes x box_rows with the
+// matching swizzle; atom32: the 128-byte swizzle with 32-byte atoms (tf32
+// planes read MN-major).
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows,
-                      int row_bytes = 128);
+                      int row_bytes = 128, bool atom32 = false);
 // n x n fp32 row-major C with row pitch ld elements, 32 x 32 boxes,
 // 128-byte swizzle (reduction target).  Needs ld % 4 == 0 and a 16-byte
 // aligned base.

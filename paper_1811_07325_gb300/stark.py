@@ -70,6 +70,7 @@ _SIGS = {
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_pipeline": ([_vp, _ci], _ci),
     "stark_plan_set_raster": ([_vp, _ci], _ci),
+    "stark_plan_set_tf32_layout": ([_vp, _ci], _ci),
     "stark_plan_set_input_bound": ([_vp, _i64], _ci),
     "stark_plan_set_traversal": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
@@ -274,6 +275,10 @@ class Plan:
         CTA pairs sharing B tiles by multicast (3xBF16); 2 (default) CTA pairs
         on one cta_group::2 MMA of 256 x 256."""
         _check(_lib.stark_plan_set_pairing(self._h, int(mode)), "stark_plan_set_pairing")
+
+    def set_tf32_layout(self, mn: bool):
+        """3xTF32 B operand: MN-major planes (no transpose pass) or K-major."""
+        _check(_lib.stark_plan_set_tf32_layout(self._h, 1 if mn else 0), "stark_plan_set_tf32_layout")
 
     def set_raster(self, band: int):
         """Leaf tile order: bands of ``band`` tile columns (0: row-major)."""

@@ -139,19 +139,24 @@ def test_divide_split_bit_exact(S, dtype, n, d):
     B = synth.normal(n, 7 + d, 1)
     split = oracle.split_bf16 if dt == S.DType.F32_SPLIT_BF16 else oracle.split_tf32
     with S.Plan(n, d, dt) as p:
-        X, Y = p.operands(dev(A), dev(B))
-        torch.cuda.synchronize()
-        P = p.leaves
-        X = X.float().cpu().numpy()
-        Y = Y.float().cpu().numpy()
         xa = oracle.strassen_operands(A, p.n_pad, d, "A")
         yb = oracle.strassen_operands(B, p.n_pad, d, "B")
         xh, xl = split(xa)
         yh, yl = split(yb)
-        assert np.array_equal(X[:P], xh) and np.array_equal(X[P:], xl)
-        if dt == S.DType.F32_SPLIT_TF32:  # stored N x K for the K-major TF32 operand
-            Y = Y.transpose(0, 2, 1)
-        assert np.array_equal(Y[:P], yh) and np.array_equal(Y[P:], yl)
+        P = p.leaves
+        # TF32: row-major Y planes (MN-major operand, the default), then the
+        # transposed planes of the K-major layout
+        for kmajor in ((False, True) if dt == S.DType.F32_SPLIT_TF32 else (False,)):
+            if kmajor:
+                p.set_tf32_layout(False)
+            X, Y = p.operands(dev(A), dev(B))
+            torch.cuda.synchronize()
+            X = X.float().cpu().numpy()
+            Y = Y.float().cpu().numpy()
+            assert np.array_equal(X[:P], xh) and np.array_equal(X[P:], xl)
+            if kmajor:  # stored N x K
+                Y = Y.transpose(0, 2, 1)
+            assert np.array_equal(Y[:P], yh) and np.array_equal(Y[P:], yl)
 
 
 @pytest.mark.parametrize("n,d", [(200, 1), (300, 2), (513, 3), (999, 4)])
@@ -434,6 +439,36 @@ def test_leaf_partition_sums_to_product(S):
         for a, b in zip(cuts[:-1], cuts[1:]):
             total += p.mul_leaves(dA, dB, a, b)
         assert np.array_equal(total.cpu().numpy(), oracle.gemm_classical(A, B))
+
+
+@pytest.mark.parametrize("n,d,dfs,combine", [(1000, 1, False, 0), (2048, 2, False, 0), (777, 1, False, 2),
+                                             (1536, 0, False, 0), (2048, 2, True, 0), (1300, 2, False, 1)])
+def test_tf32_mn_major_layout_matches(S, n, d, dfs, combine):
+    # 3xTF32 with the Y planes read MN-major (32-byte-atom swizzle, no
+    # transpose pass; the default) and K-major (transposed planes): both
+    # against the FP64 oracle and each other; pair kernel (L a multiple of
+    # 256) and single-CTA kernel (otherwise)
+    A = synth.normal(n, 66, 0)
+    B = synth.normal(n, 66, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType.F32_SPLIT_TF32) as p:
+        p.set_combine(combine)
+        if dfs:
+            p.set_traversal(True)
+        Cm = p.mul(dA, dB).cpu().numpy()  # default: MN-major
+        p.set_tf32_layout(False)
+        Ck = p.mul(dA, dB).cpu().numpy()
+        check_split(Ck, want, an, bn, "F32_SPLIT_TF32", L=p.leaf)
+        p.set_tf32_layout(True)
+        assert np.array_equal(p.mul(dA, dB).cpu().numpy(), Cm) or combine != 2
+        p.check()
+        check_split(Cm, want, an, bn, "F32_SPLIT_TF32", L=p.leaf)
+    assert np.abs(Cm - Ck).max() <= 1e-5 * np.abs(want).max()
+    with S.Plan(64, 0, S.DType.F32_SPLIT_BF16) as q:
+        with pytest.raises(S.StarkError):
+            q.set_tf32_layout(True)
 
 
 # ----------------------------------------------------------------- peeling
