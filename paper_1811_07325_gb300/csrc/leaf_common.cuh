@@ -116,8 +116,14 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
     tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc_col + (uint32_t)(chunk * 32), r);
     tmem_ld_wait();
     if constexpr (INT1) {
-      // exact integers held in fp32: signed 64-bit adds into C (wrap mod 2^64)
+      // exact integers held in fp32: signed 64-bit adds into C (wrap mod
+      // 2^64).  A whole, 16-byte-aligned row segment goes as one bulk
+      // add-reduction of 256 bytes from this thread's slot of `ebuf`
+      // (staged once per sign); ragged or unaligned segments use atomics.
       unsigned long long* Ci = reinterpret_cast<unsigned long long*>(it.C);
+      const uint32_t slot = ebuf + (uint32_t)lane * 256u;
+      const bool aligned = ((reinterpret_cast<uintptr_t>(it.C) & 15) == 0) && ((it.ldc & 1) == 0);
+      int staged = 0;  // sign of the values in the slot (0: none)
 #pragma unroll 1
       for (int t = 0; t < nt; ++t) {
         const CTarget c = tg[t];
@@ -126,12 +132,34 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
         if (grow >= it.n || gcol >= it.n) continue;
         unsigned long long* dst = Ci + grow * it.ldc + gcol;
         const int64_t lim = it.n - gcol;
+        if (aligned && lim >= 32) {
+          if (staged != c.sign) {
+            bulk_wait_group_read<0>();  // the previous reduction has read the slot
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long v = __float2ll_rn(__uint_as_float(r[j]));
-          if (j < lim && v != 0) atomicAdd(dst + j, (unsigned long long)(c.sign > 0 ? v : -v));
+            for (int w = 0; w < 16; ++w) {
+              long long v0 = __float2ll_rn(__uint_as_float(r[2 * w]));
+              long long v1 = __float2ll_rn(__uint_as_float(r[2 * w + 1]));
+              if (c.sign < 0) {
+                v0 = -v0;
+                v1 = -v1;
+              }
+              asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(slot + 16u * (uint32_t)w), "l"(v0), "l"(v1)
+                           : "memory");
+            }
+            fence_proxy_async_smem();
+            staged = c.sign;
+          }
+          bulk_reduce_add_u64(dst, slot, 256u);
+          bulk_commit_group();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const long long v = __float2ll_rn(__uint_as_float(r[j]));
+            if (j < lim && v != 0) atomicAdd(dst + j, (unsigned long long)(c.sign > 0 ? v : -v));
+          }
         }
       }
+      bulk_wait_group_read<0>();  // the slot is free for the next chunk
     } else if (p.store_m) {
       // unfused, deterministic combine: this leaf's tile goes to its M
       // plane (tmC maps the M planes here); the combine kernel adds later

@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     // every bulk reduction issued by this warp completes before the CTA exits
-    if (lane == 0) bulk_wait_group<0>();
+    // (each lane waits for its own; lanes that issued none return at once)
+    bulk_wait_group<0>();
   }
 
   tc_fence_before();

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         acc_phase ^= 1;
       }
     }
-    if (lane == 0) bulk_wait_group<0>();
+    bulk_wait_group<0>();  // each lane's own bulk reductions
   }
 
   tc_fence_before();

@@ -203,6 +203,15 @@ __device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* m, int32_t 
       : "memory");
 }
 
+// Non-tensor bulk add-reduction of `bytes` (a multiple of 16) 64-bit
+// integers from shared memory into global memory (at L2; wraps modulo
+// 2^64).  Both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_reduce_add_u64(void* gdst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(gdst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+
 // 3-D tiled bulk tensor store shared -> global.
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, int32_t c0, int32_t c1, int32_t c2, uint32_t src) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
