@@ -16,13 +16,26 @@ namespace stark {
 namespace {
 
 __host__ __device__ constexpr int pow4i(int k) { return k <= 0 ? 1 : 4 * pow4i(k - 1); }
-__host__ __device__ constexpr int pow7i_(int k) { return k <= 0 ? 1 : 7 * pow7i_(k - 1); }
+
+// Targets of product M_m (m = 0..6 for M1..M7) at one level: the C
+// quadrants (0 = C11, 1 = C12, 2 = C21, 3 = C22) it is added to, with signs
+// (Alg. 1 with C22 = M1 - M2 + M3 + M6).  Constant folding of these, with
+// the loops below fully unrolled, fixes every accumulator index at compile
+// time, so the 4^d partial sums stay in registers.
+__host__ __device__ constexpr int tgt_n(int m) { return m >= 5 ? 1 : 2; }
+__host__ __device__ constexpr int tgt_q(int m, int a) {
+  // M1: 11 22, M2: 21 22, M3: 12 22, M4: 11 21, M5: 11 12, M6: 22, M7: 11
+  return m == 0 ? (a ? 3 : 0) : m == 1 ? (a ? 3 : 2) : m == 2 ? (a ? 3 : 1) : m == 3 ? (a ? 2 : 0)
+       : m == 4 ? (a ? 1 : 0) : m == 5 ? 3 : 0;
+}
+__host__ __device__ constexpr int tgt_s(int m, int a) { return (m == 1 && a == 1) || (m == 4 && a == 0) ? -1 : 1; }
 
 template <int D, int VEC>
 __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ M, int64_t L, int64_t npad, int64_t n,
                                                       float* __restrict__ C, int64_t ldc) {
+  static_assert(D <= 3, "depth");
   constexpr int Q = pow4i(D);
-  constexpr int P = pow7i_(D);
+  constexpr int N1 = D >= 1 ? 7 : 1, N2 = D >= 2 ? 7 : 1, N3 = D >= 3 ? 7 : 1;
   const int64_t per_row = L / VEC;
   const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= L * per_row) return;
@@ -33,54 +46,53 @@ __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ 
 #pragma unroll
     for (int e = 0; e < VEC; ++e) out[q][e] = 0.f;
 
+  // leaves in ascending order: digits i1 (top level) .. i3, l = i1 i2 i3 in base 7
 #pragma unroll
-  for (int l = 0; l < P; ++l) {
-    float v[VEC];
-    const float* src = M + (int64_t)l * L * L + r * L + c;
-    if constexpr (VEC == 4) {
-      const float4 x = __ldcs(reinterpret_cast<const float4*>(src));
-      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    } else {
+  for (int i1 = 0; i1 < N1; ++i1)
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) v[e] = __ldcs(src + e);
-    }
-    // targets of leaf l: per level, product m feeds one or two C quadrants
-    int dig[D > 0 ? D : 1];
-    {
-      int x = l;
+    for (int i2 = 0; i2 < N2; ++i2)
 #pragma unroll
-      for (int k = D - 1; k >= 0; --k) {
-        dig[k] = x % 7;
-        x /= 7;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < (1 << D); ++t) {
-      int q = 0, sign = 1;
-      bool valid = true;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const int pick = (t >> (D - 1 - k)) & 1;  // first or second target at level k
-        int found = -1, count = 0;
-#pragma unroll
-        for (int cq = 0; cq < 4; ++cq)
-          if (coef_c(dig[k], cq) != 0) {
-            if (count == pick) found = cq;
-            ++count;
-          }
-        if (found < 0) {
-          valid = false;
+      for (int i3 = 0; i3 < N3; ++i3) {
+        const int l = (i1 * N2 + i2) * N3 + i3;
+        float v[VEC];
+        const float* src = M + (int64_t)l * L * L + r * L + c;
+        if constexpr (VEC == 4) {
+          const float4 x = __ldcs(reinterpret_cast<const float4*>(src));
+          v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
         } else {
-          q = q * 4 + found;
-          sign *= coef_c(dig[k], found);
-        }
-      }
-      if (valid) {
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) out[q][e] = sign > 0 ? out[q][e] + v[e] : out[q][e] - v[e];
+          for (int e = 0; e < VEC; ++e) v[e] = __ldcs(src + e);
+        }
+        // every combination of one target per level: quadrant path and sign
+#pragma unroll
+        for (int a1 = 0; a1 < 2; ++a1)
+#pragma unroll
+          for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+            for (int a3 = 0; a3 < 2; ++a3) {
+              if (D < 1 && a1) continue;
+              if (D < 2 && a2) continue;
+              if (D < 3 && a3) continue;
+              if (D >= 1 && a1 >= tgt_n(i1)) continue;
+              if (D >= 2 && a2 >= tgt_n(i2)) continue;
+              if (D >= 3 && a3 >= tgt_n(i3)) continue;
+              int q = 0, sign = 1;
+              if (D >= 1) {
+                q = tgt_q(i1, a1);
+                sign = tgt_s(i1, a1);
+              }
+              if (D >= 2) {
+                q = q * 4 + tgt_q(i2, a2);
+                sign *= tgt_s(i2, a2);
+              }
+              if (D >= 3) {
+                q = q * 4 + tgt_q(i3, a3);
+                sign *= tgt_s(i3, a3);
+              }
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) out[q][e] = sign > 0 ? out[q][e] + v[e] : out[q][e] - v[e];
+            }
       }
-    }
-  }
 
 #pragma unroll
   for (int q = 0; q < Q; ++q) {

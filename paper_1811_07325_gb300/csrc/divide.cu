@@ -12,10 +12,10 @@
 // (one contiguous 8- or 16-byte store per plane, coalesced across the warp).
 //
 // For depth <= 2 all 4^depth quadrant vectors sit in registers.  Deeper
-// trees walk the first depth-2 levels as an outer loop: for each prefix of
-// M-indices the 16 sub-quadrant sums are re-evaluated from global memory
-// (L2 hits), in the same level-by-level order, then the last two levels run
-// in registers.  Every sum is a two-term addition per level exactly as in
+// trees give each prefix of M-indices over the first depth-2 levels its own
+// grid row: the 16 sub-quadrant sums below the prefix are evaluated from
+// global memory in the same level-by-level order, then the last two levels
+// run in registers.  Every sum is a two-term addition per level exactly as in
 // Alg. 1, so results do not depend on evaluation order.
 // Padding to n_pad is virtual: reads beyond n return zero.
 #include <cuda_bf16.h>
@@ -311,17 +311,18 @@ __global__ void __launch_bounds__(256, 2) divide_kernel(DivideArgs a, int vec_ok
   if constexpr (F == 0) {
     leaf_block(nullptr, 0);
   } else {
-#pragma unroll 1
-    for (int p = 0; p < pow7c(F); ++p) {
-      int dig[F > 0 ? F : 1];
-      int x = p;
+    // one prefix of the outer levels per grid row: the blocks in flight at a
+    // time write the 2 * 7^R planes of one prefix (sequential write streams),
+    // at the price of reading each prefix's input quadrants again
+    const int p = (int)blockIdx.y;
+    int dig[F > 0 ? F : 1];
+    int x = p;
 #pragma unroll
-      for (int k = F - 1; k >= 0; --k) {
-        dig[k] = x % 7;
-        x /= 7;
-      }
-      leaf_block(dig, p);
+    for (int k = F - 1; k >= 0; --k) {
+      dig[k] = x % 7;
+      x /= 7;
     }
+    leaf_block(dig, p);
   }
 }
 
@@ -334,7 +335,8 @@ cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
   const int64_t threads = a.L * (a.L / VEC);
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  divide_kernel<Tin, OUT, D, SIDE, VEC, TOP><<<(unsigned)blocks, 256, 0, st>>>(a, vec_ok);
+  constexpr int F = D < 2 ? 0 : D - 2;  // outer levels: one grid row per prefix
+  divide_kernel<Tin, OUT, D, SIDE, VEC, TOP><<<dim3((unsigned)blocks, (unsigned)pow7c(F)), 256, 0, st>>>(a, vec_ok);
   count_launch();
   return cudaGetLastError();
 }

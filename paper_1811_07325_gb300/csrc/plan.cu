@@ -701,9 +701,31 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     da.out_lo = static_cast<char*>(p->X) + half;
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
-  stark_status st = to_status(launch_divide(da, depth, 0, in, om, s));
-  if (st != STARK_OK) return st;
-  st = to_status(launch_divide(db, depth, 1, in, om, s));
+  stark_status st = STARK_OK;
+  if (top < 0 && depth >= 3) {
+    // breadth first at depth >= 3: one launch per top-level product, each a
+    // depth-1 subtree read through that product's level-1 sum and written
+    // to its block of 7^(d-1) planes (the outer-prefix form of the deep
+    // kernel keeps too few loads in flight to stream at HBM bandwidth)
+    const int64_t sub = pow7i(depth - 1);
+    // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
+    // integers, tf32 in fp32 containers, else the input type
+    const size_t ehi = (p->dt == STARK_F32_SPLIT_BF16 || p->int_tc) ? 2 : p->dt == STARK_F32_SPLIT_TF32 ? 4 : 8;
+    const size_t plane = (size_t)p->L * p->L * ehi;
+    for (int t = 0; t < 7 && st == STARK_OK; ++t) {
+      for (int side = 0; side < 2 && st == STARK_OK; ++side) {
+        DivideArgs a = side ? db : da;
+        a.top = t;
+        a.npad = p->npad / 2;
+        a.out_hi = static_cast<char*>(a.out_hi) + (size_t)t * sub * plane;
+        if (a.out_lo) a.out_lo = static_cast<char*>(a.out_lo) + (size_t)t * sub * plane;
+        st = to_status(launch_divide(a, depth - 1, side, in, om, s));
+      }
+    }
+  } else {
+    st = to_status(launch_divide(da, depth, 0, in, om, s));
+    if (st == STARK_OK) st = to_status(launch_divide(db, depth, 1, in, om, s));
+  }
   if (st != STARK_OK) return st;
   if (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn)  // K-major tf32 B: N x K planes
     st = to_status(launch_transpose_planes(static_cast<float*>(p->Y), p->L, 2 * p->P_ws, s));
