@@ -111,6 +111,13 @@ struct stark_batch_s {
   int total_items = 0;
   int* d_err = nullptr;
   cudaStream_t cap = nullptr;  // private capture stream
+  // the members' clears and divides are captured on kForks side streams
+  // forked from `cap`, so the graph runs them concurrently (small members'
+  // kernels are launch- and latency-bound one after another)
+  static constexpr int kForks = 8;
+  cudaStream_t side[kForks] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kForks] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<int> caller_index;  // caller's index of each (size-sorted) member
   std::vector<const void*> last;  // pointers the graph was captured with
@@ -128,6 +135,11 @@ static void batch_free(stark_batch_s* b) {
   cudaFree(b->d_desc);
   cudaFree(b->d_err);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < stark_batch_s::kForks; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->join_ev[i]) cudaEventDestroy(b->join_ev[i]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   cudaGetLastError();
   delete b;
 }
@@ -216,8 +228,13 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
   if (st == STARK_OK && (cudaMalloc(&b->d_desc, sizeof(GroupDesc) * count) != cudaSuccess ||
                          cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess ||
                          cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess ||
-                         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess))
+                         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess))
     st = STARK_ENOMEM;
+  for (int i = 0; i < stark_batch_s::kForks && st == STARK_OK; ++i)
+    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      st = STARK_ENOMEM;
   if (st != STARK_OK) {
     batch_free(b);
     return st;
@@ -295,32 +312,56 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return STARK_ECUDA;
     stark_status st = STARK_OK;
+    // fork: members' clears and divides on the side streams, joined before
+    // the grouped leaf launches
+    constexpr int F = stark_batch_s::kForks;
+    if (cudaEventRecord(b->fork_ev, b->cap) != cudaSuccess) st = STARK_ECUDA;
+    for (int i = 0; i < F && st == STARK_OK; ++i)
+      if (cudaStreamWaitEvent(b->side[i], b->fork_ev, 0) != cudaSuccess) st = STARK_ECUDA;
     for (int k = 0; k < count && st == STARK_OK; ++k) {
       stark_plan_s* p = b->plans[k];
       const GroupDesc& g = b->host_desc[k];
-      if (cudaMemsetAsync(g.C, 0, (size_t)p->n * g.ldc * sizeof(float), b->cap) != cudaSuccess)
+      cudaStream_t sk = b->side[k % F];
+      if (cudaMemsetAsync(g.C, 0, (size_t)p->n * g.ldc * sizeof(float), sk) != cudaSuccess)
         st = STARK_ECUDA;
       else
-        st = plan_divide(p, ptrs[3 * k], ptrs[3 * k + 1], b->cap);
+        st = plan_divide(p, ptrs[3 * k], ptrs[3 * k + 1], sk);
     }
+    for (int i = 0; i < F; ++i)  // join (also after an error, so the capture can end)
+      if (cudaEventRecord(b->join_ev[i], b->side[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->cap, b->join_ev[i], 0) != cudaSuccess)
+        st = STARK_ECUDA;
     if (st == STARK_OK) {
       LeafTcArgs a{};
       a.err = b->d_err;
       a.timeout_ns = kDefaultTimeoutNs;
       const bool tf32 = b->dt == STARK_F32_SPLIT_TF32;
       a.b_mn = tf32 && b->plans[0]->tf32_mn;  // every member has the plan default
-      if (b->split > 0) {  // 256-wide members
+      // the two grouped launches on two branches of the graph: the second
+      // takes SMs as the first one's tail frees them
+      const bool both = b->split > 0 && b->split < count;
+      cudaStream_t s_wide = both ? b->side[0] : b->cap, s_narrow = both ? b->side[1] : b->cap;
+      if (both && (cudaEventRecord(b->fork_ev, b->cap) != cudaSuccess ||
+                   cudaStreamWaitEvent(s_wide, b->fork_ev, 0) != cudaSuccess ||
+                   cudaStreamWaitEvent(s_narrow, b->fork_ev, 0) != cudaSuccess))
+        st = STARK_ECUDA;
+      if (st == STARK_OK && b->split > 0) {  // 256-wide members
         a.groups = b->d_desc;
         a.ngroups = b->split;
         a.total_items = b->items_wide;
-        if (launch_leaf_tc2_grouped(a, tf32, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
+        if (launch_leaf_tc2_grouped(a, tf32, device_sm_count(), s_wide) != cudaSuccess) st = STARK_ECUDA;
       }
       if (st == STARK_OK && b->split < count) {  // 128-wide members
         a.groups = b->d_desc + b->split;
         a.ngroups = count - b->split;
         a.total_items = b->total_items;
-        if (launch_leaf_tc_grouped(a, tf32, 128, device_sm_count(), b->cap) != cudaSuccess) st = STARK_ECUDA;
+        if (launch_leaf_tc_grouped(a, tf32, 128, device_sm_count(), s_narrow) != cudaSuccess) st = STARK_ECUDA;
       }
+      if (both)
+        for (int i = 0; i < 2; ++i)
+          if (cudaEventRecord(b->join_ev[i], b->side[i]) != cudaSuccess ||
+              cudaStreamWaitEvent(b->cap, b->join_ev[i], 0) != cudaSuccess)
+            st = STARK_ECUDA;
       // members combined into a staging copy: move the result into C
       for (int k = 0; k < count && st == STARK_OK; ++k)
         if (b->host_desc[k].C != ptrs[3 * k + 2])
