@@ -518,6 +518,13 @@ def main():
                 "algorithmic_flops_per_launch": leaf_flops,
                 "launch_ms": phases["leaf_combine"]}
     divide_bytes = 2 * (n * n * 4) + plan.workspace_bytes  # read A, B; write every leaf operand (hi+lo)
+    # the whole path's roofline (phases serialize): leaf flops at the tensor
+    # peak + divide bytes and the clear and final write of C at HBM bandwidth
+    t_roof = leaf_flops / (pk["bf16_sustained"] * 1e12) + (divide_bytes + 2 * n * n * 4) / (pk["hbm_gbs"] * 1e9)
+    path_roofline = {"t_roof_ms": t_roof * 1e3, "t_ms": ms, "frac": t_roof * 1e3 / ms,
+                     "effective_tflops_at_roof": flops / t_roof / 1e12,
+                     "effective_over_bf16_peak": value / world / pk["bf16_sustained"],
+                     "model": "leaf 3*2*L^3*7^d flops / bf16 sustained + (divide bytes + C clear and write) / HBM"}
 
     comparators = None
     if not args.no_comparators and rank == 0:
@@ -672,7 +679,7 @@ def main():
                               tile=list(plan.tile)),
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
-               "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9,
+               "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9, "path_roofline": path_roofline,
                "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32, "int64": int64,
                "batch": batch, "serve": serve, "peel": peel,
                "cpu_baseline": cpu}
