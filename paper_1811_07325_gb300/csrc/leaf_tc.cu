@@ -9,17 +9,23 @@
 //   M ~= X_lo Y_hi + X_hi Y_lo + X_hi Y_hi
 // accumulates in fp32 in tensor memory (the lo*lo term is below fp32
 // resolution of the result and is dropped).  X planes (M x K, row-major) are
-// a K-major operand.  For bf16 the Y planes stay row-major (K x N) and are an
-// MN-major operand, loaded in 128-byte-wide N chunks; for tf32 they are
-// transposed in place to N x K beforehand and read K-major.
+// a K-major operand.  The Y planes stay row-major (K x N) and are an
+// MN-major operand, loaded in 128-byte-wide N chunks (bf16: 128-byte
+// swizzle; tf32: 128-byte swizzle of 32-byte atoms); the optional K-major
+// tf32 layout transposes them to N x K beforehand.
+//
+// This is the single-CTA form: leaf sides that are not a multiple of 256,
+// the 128-wide grouped launches of batches and the server, the exact int64
+// leaves, and the opt-in schedules (multicast pairs, 64-byte rows).  Leaf
+// sides that are multiples of 256 run on CTA pairs (leaf_tc2.cu).
 //
 // Persistent kernel, one CTA per SM, warp-specialised:
 //   warp 0      TMA producer: per k-block, 4 tiles (X_hi, X_lo, Y_hi, Y_lo)
-//               into a STAGES-deep shared-memory ring (128-byte swizzle)
+//               into a STAGES-deep shared-memory ring
 //   warp 1      TMEM allocator + single-thread MMA issuer (3 MMAs per K=16
 //               (bf16) or K=8 (tf32) step), double-buffered accumulators
-//   warps 2..5  epilogue: tcgen05.ld the accumulator, signed vector atomics
-//               into C for every target of the leaf
+//   warps 2..5  epilogue (leaf_common.cuh): tcgen05.ld the accumulator and
+//               add it into C for every target of the leaf
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // drains its in-flight copies and MMAs, frees TMEM and returns.
 #include <cstring>

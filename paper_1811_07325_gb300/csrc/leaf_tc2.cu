@@ -1,5 +1,5 @@
-// leaf_tc2.cu -- the 3xBF16 leaf products (Alg. 4) with the fused combine
-// (Alg. 5) on CTA pairs: the two CTAs of a cluster share one cta_group::2
+// leaf_tc2.cu -- the 3xBF16 / 3xTF32 leaf products (Alg. 4) with the fused
+// combine (Alg. 5) on CTA pairs: the two CTAs of a cluster share one cta_group::2
 // tcgen05 MMA of 256 x 256 per K step.  Each CTA stages its own 128 rows of
 // the X tile and its own 128 columns of the Y tile, so one CTA holds 64 KB
 // per pipeline stage instead of the 96 KB a single-CTA 128 x 256 tile needs
@@ -28,10 +28,11 @@ namespace {
 
 constexpr int kThreads2 = 192;
 
-// TF32: Y planes transposed to N x K beforehand, so the Y tile is K-major
-// like X (one 128-row box per half tile); bf16: Y row-major, MN-major, in
-// 128-byte-wide column boxes.
-// TMN: tf32 Y planes row-major, read MN-major with the 32-byte-atom swizzle.
+// Y tile layouts: bf16 and tf32 with TMN (the default) keep the Y planes
+// row-major and read them MN-major in 128-byte-wide column boxes (bf16:
+// 128-byte swizzle; tf32: 128-byte swizzle of 32-byte atoms); tf32 without
+// TMN reads planes transposed to N x K beforehand, K-major like X (one
+// 128-row box per half tile).
 template <bool TF32, bool TMN = false>
 struct Tc2Cfg {
   static constexpr int ESZ = TF32 ? 4 : 2;

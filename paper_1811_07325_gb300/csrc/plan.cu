@@ -98,9 +98,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // planes [planes][L][L] of bf16 (or fp32 holding tf32), row-major; box =
-// 128 bytes of a row x box_rows rows of one plane, 128-byte swizzle.  For
-// the K-major X planes a box is a 128-byte K slice of box_rows M rows; for
-// the MN-major Y planes it is a 128-byte N chunk of box_rows K rows.
+// row_bytes of a row x box_rows rows of one plane, with the matching
+// swizzle (128- or 64-byte; atom32: 128-byte with 32-byte atoms).  For the
+// K-major X planes a box is a K slice of box_rows M rows; for the MN-major
+// Y planes it is an N chunk of box_rows K rows.
 bool make_tmap_planes(CUtensorMap* m, void* base, bool tf32, int64_t L, int64_t planes, int box_rows,
                       int row_bytes, bool atom32) {
   auto fn = encode_fn();

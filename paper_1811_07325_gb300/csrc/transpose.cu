@@ -1,6 +1,6 @@
-// transpose.cu -- in-place transpose of square leaf planes.  The 3xTF32 leaf
-// GEMM reads its B operand K-major, so the TF32 B planes written row-major
-// (K x N) by the divide kernel are turned into N x K here.  Each block swaps
+// transpose.cu -- in-place transpose of square leaf planes, for the optional
+// K-major layout of the 3xTF32 B operand: the TF32 B planes written
+// row-major (K x N) by the divide kernel are turned into N x K here.  Each block swaps
 // a 32 x 32 tile with its mirror tile through shared memory (diagonal tiles
 // transpose in place); reads and writes are coalesced along rows.
 #include "stark_internal.h"
