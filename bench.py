@@ -672,10 +672,9 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "bf16" if args.dtype == "bf16" else "tf32",
+               "vs_baseline": None, "dtype": args.dtype,
                "dtype_detail": f"fp32 in/out; 3x{args.dtype} split tensor-core leaf products, fp32 accumulate; "
-                               "fp32 divide sums and combine"
-               if args.dtype == "bf16" else "f32 in/out, 3xtf32 tensor-core leaves, fp32 accumulate",
+                               "fp32 divide sums and combine",
                "data": "synthetic",
                "config": dict(workload_config(args, plan.depth), leaves=plan.leaves, leaf=plan.leaf,
                               tile=list(plan.tile)),
