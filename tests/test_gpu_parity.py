@@ -637,9 +637,12 @@ def test_auto_depth(S):
 
 # ----------------------------------------------------------------- full size, sampled rows
 @pytest.mark.slow
-@pytest.mark.parametrize("dtype,d", [("F32_SPLIT_BF16", 2), ("F32_SPLIT_BF16", 3), ("F32_SPLIT_TF32", 2),
-                                     ("F32_SPLIT_TF32", 3)])
-def test_full_size_sampled_rows(S, dtype, d):
+@pytest.mark.parametrize("dtype,d,combine", [("F32_SPLIT_BF16", 2, 0), ("F32_SPLIT_BF16", 3, 0),
+                                             ("F32_SPLIT_TF32", 2, 0), ("F32_SPLIT_TF32", 3, 0),
+                                             ("F32_SPLIT_BF16", 2, 2), ("F32_SPLIT_BF16", 3, 2)])
+def test_full_size_sampled_rows(S, dtype, d, combine):
+    # the bench workload in the bench's launch configuration (CTA pairs;
+    # fused combine, or the deterministic one of its second leg)
     n = 16384
     A = synth.normal(n, 2024, 0)
     B = synth.normal(n, 2024, 1)
@@ -648,6 +651,7 @@ def test_full_size_sampled_rows(S, dtype, d):
     an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
     dA, dB = dev(A), dev(B)
     with S.Plan(n, d, S.DType[dtype]) as p:
+        p.set_combine(combine)
         C = p.mul(dA, dB)
         p.check()
         got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
@@ -655,6 +659,28 @@ def test_full_size_sampled_rows(S, dtype, d):
     del C, dA, dB
     torch.cuda.empty_cache()
     check_split(got, want, an, bn, dtype, L=L)
+
+
+@pytest.mark.slow
+def test_full_size_host_pipeline(S):
+    # the bench's end-to-end leg: pinned host buffers through the enqueue
+    # pipeline, two products in flight, sampled rows of both results
+    n = 16384
+    rows = synth.sample_rows(n, 64, 2025)
+    with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
+        outs = []
+        for seed in (2025, 2026):
+            A = torch.from_numpy(synth.normal(n, seed, 0)).pin_memory()
+            B = torch.from_numpy(synth.normal(n, seed, 1)).pin_memory()
+            C = torch.empty((n, n), dtype=torch.float32).pin_memory()
+            p.mul_host_enqueue(A, B, C)
+            outs.append((A, B, C))
+        p.host_wait()
+    for A, B, C in outs:
+        a, b = A.numpy(), B.numpy()
+        want = oracle.gemm_rows(a, b, rows)
+        an, bn = np.linalg.norm(a.astype(np.float64)), np.linalg.norm(b.astype(np.float64))
+        check_split(C.numpy()[rows], want, an, bn, "F32_SPLIT_BF16", L=4096)
 
 
 def test_mul_sharded_single_rank_nccl(S, tmp_path):
