@@ -1,0 +1,98 @@
+"""Seeded sweep of random plan configurations against the CPU oracle.
+
+Each case draws a size, depth, dtype and a combination of plan options
+(combine mode, leaf schedule, raster, traversal, edge peeling, tf32 B
+layout), runs one product through the C ABI and compares every element with
+the oracle: bit-exact for int64, the split-precision bound for fp32, the
+Higham bound for fp64.  Options that do not apply to a draw (e.g. a tf32
+layout on a bf16 plan) are left at their defaults.
+"""
+import random
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1811_07325_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_BOUND = {"F32_SPLIT_BF16": 2.0 ** -12, "F32_SPLIT_TF32": 2.0 ** -16}
+MMA_K = {"F32_SPLIT_BF16": 16, "F32_SPLIT_TF32": 8}
+SPLIT_U2 = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22}
+
+
+def draw(rng):
+    dtype = rng.choice(["F32_SPLIT_BF16", "F32_SPLIT_BF16", "F32_SPLIT_TF32", "F64", "I64"])
+    n = rng.choice([1, 17, 64, 130, 257, 300, 513, 700, 777, 1024, 1100, 1300, 1500])
+    d = rng.randint(0, 3)
+    opts = {
+        "peel": rng.random() < 0.3,
+        "combine": rng.choice([0, 0, 1, 2]) if dtype.startswith("F32") else 0,
+        "pairing": rng.choice([0, 1, 2, 2]) if dtype.startswith("F32") else 2,
+        "raster": rng.choice([0, 0, 2, 4]),
+        "dfs": rng.random() < 0.3 and d >= 1,
+        "tf32_mn": rng.random() < 0.7,
+        "bound": dtype == "I64" and rng.random() < 0.5,
+    }
+    return dtype, n, d, opts
+
+
+CASES = [draw(random.Random(1000 + k)) for k in range(120)]
+
+
+@pytest.mark.parametrize("k", range(len(CASES)))
+def test_random_configuration(stark_lib, k):
+    S = stark_lib
+    dtype, n, d, o = CASES[k]
+    if dtype == "I64":
+        A = synth.integers(n, 500 + k, 0, -16, 16)
+        B = synth.integers(n, 500 + k, 1, -16, 16)
+    elif dtype == "F64":
+        A = synth.uniform(n, 500 + k, 0)
+        B = synth.uniform(n, 500 + k, 1)
+    else:
+        A = synth.normal(n, 500 + k, 0)
+        B = synth.normal(n, 500 + k, 1)
+    want = oracle.gemm_classical(A, B) if dtype == "I64" else \
+        oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    with S.Plan(n, d, S.DType[dtype], peel=o["peel"]) as p:
+        if o["bound"] and (p.leaf % 128 == 0):
+            try:
+                p.set_input_bound(16)
+            except S.StarkError:
+                pass  # bound outside the exact range at this depth: CUDA-core path
+        if o["combine"] and p.depth <= 3:
+            p.set_combine(o["combine"])
+        p.set_pairing(o["pairing"])
+        p.set_raster(o["raster"])
+        if dtype == "F32_SPLIT_TF32":
+            p.set_tf32_layout(o["tf32_mn"])
+        if o["dfs"] and o["combine"] != 2:
+            p.set_traversal(True)
+        C = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        L = p.leaf
+    if dtype == "I64":
+        assert np.array_equal(C, want), (dtype, n, d, o)
+        return
+    diff = C.astype(np.float64) - want
+    if dtype == "F64":
+        u = 2.0 ** -53
+        Lc = -(-n // 2 ** d)
+        bound = 2 * ((12 ** d * (Lc * Lc + 5 * Lc) - 5 * n) + n) * u * np.abs(A).max() * np.abs(B).max()
+        assert np.abs(diff).max() <= bound, (n, d, o)
+        return
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    if n >= 64:
+        assert np.abs(diff).max() / (an * bn) <= 1e-6, (dtype, n, d, o)
+        rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+        assert rel <= SPLIT_BOUND[dtype] + 3 * (L / MMA_K[dtype]) * 2.0 ** -24, (dtype, n, d, o, rel)
+    else:
+        absAB = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+        tol = (3 * SPLIT_U2[dtype] + n * 2.0 ** -23) * 3 ** d * absAB
+        assert np.all(np.abs(diff) <= tol), (dtype, n, d, o)
