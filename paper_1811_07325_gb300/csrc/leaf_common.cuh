@@ -236,4 +236,35 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
   }
 }
 
+// Persistent launch of a leaf kernel on clusters of two CTAs: as many
+// clusters as can be resident at once (at most one per SM pair), never more
+// than there are work items (items > 0).
+template <typename Kern>
+cudaError_t launch_cta_pairs(Kern kern, int threads, int smem, int64_t items, int num_sms, cudaStream_t st,
+                             const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmC,
+                             const LeafTcArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = num_sms / 2;
+  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+  int active = 0;
+  if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && active < clusters)
+    clusters = active;
+  cudaGetLastError();
+  if (items < clusters) clusters = (int)items;
+  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, tmC, a);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace stark

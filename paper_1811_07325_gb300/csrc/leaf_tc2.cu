@@ -297,28 +297,7 @@ cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorM
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kThreads2, 1, 1);
-  cfg.dynamicSmemBytes = Cfg::SMEM;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int clusters = num_sms / 2;
-  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-  int active = 0;
-  if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && active < clusters)
-    clusters = active;
-  cudaGetLastError();
-  if (items < clusters) clusters = (int)items;
-  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-  e = cudaLaunchKernelEx(&cfg, kern, *tmA, *tmB, *tmC, a);
-  count_launch();
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return launch_cta_pairs(kern, kThreads2, Cfg::SMEM, items, num_sms, st, *tmA, *tmB, *tmC, a);
 }
 
 }  // namespace
