@@ -233,8 +233,8 @@ STARK_API stark_status stark_plan_set_tf32_layout(stark_plan_t plan, int mn);
  * combine's addition order. */
 STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
 
-/* Traversal of the recursion tree (SURVEY's memory-lean next step; the
- * paper names the O(3^l N^2) space growth as Stark's drawback, Sec. VI).
+/* Traversal of the recursion tree (memory-lean form; the paper names the
+ * O(3^l N^2) space growth as Stark's drawback, Sec. VI).
  * depth_first = 0 (default): breadth first, one divide for all 7^d leaves
  * and one leaf launch.  1: depth first over the top level: for each of the
  * seven top-level products, divide only its subtree (reading A and B
