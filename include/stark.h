@@ -56,7 +56,7 @@ typedef enum {
   STARK_OK = 0,
   STARK_EINVAL = 1,      /* bad argument (null pointer, n < 0, depth out of range, ...) */
   STARK_ENOMEM = 2,      /* device or host allocation failed, or over the memory budget */
-  STARK_EUNSUPPORTED = 3,/* valid request this build or device cannot serve            */
+  STARK_EUNSUPPORTED = 3,/* valid request the library or device cannot serve          */
   STARK_ETIMEOUT = 4,    /* a bounded device-side wait expired; results are invalid    */
   STARK_EBUSY = 5,       /* the request is still queued or running                      */
   STARK_ENOTFOUND = 6,   /* unknown request id                                           */

@@ -30,7 +30,7 @@ bool device_is_sm100_family() {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  return major == 10 && minor == 3;  // this build carries sm_103a code only
+  return major == 10 && minor == 3;  // the library carries sm_103a code only
 }
 
 // ------------------------------------------------------------------ tables
