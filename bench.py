@@ -387,7 +387,7 @@ def main():
     ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
-    ap.add_argument("--traversal", type=int, default=0, help="1: depth first over the top level")
+    ap.add_argument("--traversal", type=int, default=0, help="k > 0: depth first over the top k levels")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-oracle-timings", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -430,7 +430,7 @@ def main():
     if args.raster >= 0:
         plan.set_raster(args.raster)
     if args.traversal:
-        plan.set_traversal(True)
+        plan.set_traversal(args.traversal)
     stream = torch.cuda.current_stream()
 
     def barrier():

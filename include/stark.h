@@ -235,19 +235,21 @@ STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
 
 /* Traversal of the recursion tree (memory-lean form; the paper names the
  * O(3^l N^2) space growth as Stark's drawback, Sec. VI).
- * depth_first = 0 (default): breadth first, one divide for all 7^d leaves
- * and one leaf launch.  1: depth first over the top level: for each of the
- * seven top-level products, divide only its subtree (reading A and B
- * through that product's level-1 sum on the fly) and launch its 7^(d-1)
- * leaves; the workspace shrinks 7x (the plan reallocates it), the divide
- * reads A and B seven times.  Results agree within the combine's rounding
- * order (bit-identical for int64).  Errors: EUNSUPPORTED (depth 0, or the
- * deterministic combine mode), ENOMEM, ECUDA.  stark_plan_operands is not
- * available in depth-first mode. */
-STARK_API stark_status stark_plan_set_traversal(stark_plan_t plan, int depth_first);
+ * levels = 0 (default): breadth first, one divide for all 7^d leaves and
+ * one leaf launch.  levels = k (1, or 2 for the split-fp32 dtypes): depth
+ * first over the top k levels: for each of the 7^k products there, divide
+ * only its subtree (reading A and B through that product's level-1..k
+ * operand sums, formed on the fly in the order of Alg. 1) and launch its
+ * 7^(d-k) leaves; the workspace shrinks 7^k-fold (the plan reallocates it),
+ * the divide reads A and B 3^k times over.  Results agree within the
+ * combine's rounding order (bit-identical for int64).  Errors: EINVAL
+ * (levels outside 0..2), EUNSUPPORTED (levels > depth, depth > 3, levels =
+ * 2 on an F64/I64 plan, or the deterministic combine mode), ENOMEM, ECUDA.
+ * stark_plan_operands is not available in depth-first mode. */
+STARK_API stark_status stark_plan_set_traversal(stark_plan_t plan, int levels);
 
 /* Exact integer leaves on the tensor cores for an I64 plan whose inputs
- * satisfy |A_ij|, |B_ij| <= max_abs (the integer path of the benchmark spec;
+ * satisfy |A_ij|, |B_ij| <= max_abs (the exact integer path;
  * the paper itself is FP64-only).  A depth-d leaf operand is a sum of 2^d
  * inputs, so with b = max_abs * 2^d the plan multiplies in bf16 (exact for
  * integers up to 256) with fp32 accumulation (exact while every partial sum

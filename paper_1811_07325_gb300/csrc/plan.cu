@@ -465,15 +465,17 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
   return STARK_OK;
 }
 
-stark_status stark_plan_set_traversal(stark_plan_t p, int depth_first) {
-  if (!p || depth_first < 0 || depth_first > 1) return STARK_EINVAL;
-  if (depth_first == (p->dfs ? 1 : 0) || p->n == 0) {
-    p->dfs = depth_first == 1;
+stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
+  if (!p || levels < 0 || levels > 2) return STARK_EINVAL;
+  // the subtree below `levels` is at most 2 (one level) or 1 (two levels) deep
+  if (levels && (p->depth < levels || p->depth > 3 || p->combine_mode == 2)) return STARK_EUNSUPPORTED;
+  if (levels == 2 && !p->is_tc) return STARK_EUNSUPPORTED;  // two-level loader: split dtypes
+  if (levels == p->dfs || p->n == 0) {
+    p->dfs = levels;
     return STARK_OK;
   }
-  if (depth_first && (p->depth < 1 || p->combine_mode == 2)) return STARK_EUNSUPPORTED;
-  const stark_status st = plan_alloc_operands(p, depth_first ? p->P / 7 : p->P);
-  p->dfs = st == STARK_OK && depth_first == 1;
+  const stark_status st = plan_alloc_operands(p, p->P / pow7i(levels));
+  p->dfs = st == STARK_OK ? levels : 0;
   return st;
 }
 
@@ -689,11 +691,13 @@ static stark_status to_status(cudaError_t e) {
 // first); top = i1: only the subtree below top-level product M_{i1+1}
 // (depth-first traversal), its leaves in planes 0..7^(d-1)-1.
 stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top) {
-  const int64_t npad = top >= 0 ? p->npad / 2 : p->npad;
-  const int depth = top >= 0 ? p->depth - 1 : p->depth;
+  // depth first: the subtree below p->dfs levels along the M-index path `top`
+  const int64_t npad = top >= 0 ? p->npad >> p->dfs : p->npad;
+  const int depth = top >= 0 ? p->depth - p->dfs : p->depth;
   // the core of A and B (all of them unless an edge is peeled), row stride n
   DivideArgs da{A, core_side(p), npad, p->L, p->X, nullptr, p->d_err, top, p->n};
   DivideArgs db{B, core_side(p), npad, p->L, p->Y, nullptr, p->d_err, top, p->n};
+  da.top_levels = db.top_levels = top >= 0 ? p->dfs : 0;
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
   if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
@@ -703,8 +707,8 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
   stark_status st = STARK_OK;
-  if (top < 0 && depth >= 3) {
-    // breadth first at depth >= 3: one launch per top-level product, each a
+  if (top < 0 && depth == 3) {
+    // breadth first at depth 3: one launch per top-level product, each a
     // depth-1 subtree read through that product's level-1 sum and written
     // to its block of 7^(d-1) planes (the outer-prefix form of the deep
     // kernel keeps too few loads in flight to stream at HBM bandwidth)
@@ -717,6 +721,7 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
       for (int side = 0; side < 2 && st == STARK_OK; ++side) {
         DivideArgs a = side ? db : da;
         a.top = t;
+        a.top_levels = 1;
         a.npad = p->npad / 2;
         a.out_hi = static_cast<char*>(a.out_hi) + (size_t)t * sub * plane;
         if (a.out_lo) a.out_lo = static_cast<char*>(a.out_lo) + (size_t)t * sub * plane;
@@ -887,11 +892,13 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     if (ev) cudaEventRecord(ev[2], s);
     st = plan_leaves(p, C, lb, le, 0, s);
   } else {
-    // depth-first over the top level: one subtree's operands at a time
-    // (divide and leaves interleave; the phase timer reports them together)
+    // depth-first over the top p->dfs levels: one subtree's operands at a
+    // time (divide and leaves interleave; the phase timer reports them
+    // together)
     if (ev) cudaEventRecord(ev[2], s);
+    const int tops = (int)pow7i(p->dfs);
     int last = -1;
-    for (int top = 0; top < 7; ++top)
+    for (int top = 0; top < tops; ++top)
       if (std::max<int64_t>(lb, top * p->P_ws) < std::min<int64_t>(le, (top + 1) * p->P_ws)) last = top;
     for (int top = 0; top <= last && st == STARK_OK; ++top) {
       const int64_t b0 = top * p->P_ws, b1 = b0 + p->P_ws;

@@ -32,7 +32,7 @@ int autotune_depth(int64_t n, stark_dtype dt);
 struct stark_plan_s {
   int64_t n = 0, npad = 0, L = 0, P = 1;
   int64_t P_ws = 1;   // leaves whose operands the workspace holds (P, or P / 7 depth-first)
-  bool dfs = false;   // depth-first over the top recursion level
+  int dfs = 0;        // depth-first over this many top recursion levels (0: breadth first)
   int depth = 0;
   stark_dtype dt = STARK_F64;
   bool is_tc = false;  // tensor-core (split) path

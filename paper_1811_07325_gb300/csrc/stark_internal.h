@@ -65,14 +65,19 @@ struct DivideArgs {
   void* out_lo;       // planes [P][L][L] (split: lo part; plain: unused)
   int* range_flag;    // bf16-exact output: set to kDevIntRange when |value| > 256
   int top;            // >= 0: depth-first subtree; the input is read through the
-                      // level-1 sum of product `top` (M1..M7 = 0..6) and npad is
-                      // the subproblem's side (half the full padded side)
+                      // operand sums of the top `top_levels` levels along the
+                      // M-index path `top` (base 7, top level most significant;
+                      // M1..M7 = 0..6) and npad is the subproblem's side (the
+                      // full padded side >> top_levels)
   int64_t ld;         // row stride of X in elements (>= n)
+  int top_levels;     // levels above the subtree (1, or 2 for the split dtypes) when top >= 0
 };
 
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
+// The same for a depth-first subtree (a.top >= 0); launch_divide forwards.
+cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
 // elements) on the CUDA cores: the edges of a peeled product.  Element type
 // float (fp32 accumulate), double or int64 (wrapping); accumulate = 0

@@ -288,9 +288,11 @@ class Plan:
         """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
         _check(_lib.stark_plan_set_pipeline(self._h, 1 if deep else 0), "stark_plan_set_pipeline")
 
-    def set_traversal(self, depth_first: bool):
-        """Depth-first over the top level (7x less workspace) or breadth-first."""
-        _check(_lib.stark_plan_set_traversal(self._h, 1 if depth_first else 0), "stark_plan_set_traversal")
+    def set_traversal(self, levels):
+        """Depth first over the top ``levels`` recursion levels (0: breadth
+        first; True means 1; 2 for the split dtypes): the workspace holds one
+        subtree's leaves."""
+        _check(_lib.stark_plan_set_traversal(self._h, int(levels)), "stark_plan_set_traversal")
         info = PlanInfo()
         _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
         self.workspace_bytes = info.workspace_bytes

@@ -387,9 +387,13 @@ def test_pair_mma_matches_oracle(S, dtype, n, d, combine, dfs):
         assert np.abs(C1 - C2).max() <= 1e-5 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("n,d,dtype", [(2048, 2, "F32_SPLIT_BF16"), (1001, 3, "F32_SPLIT_BF16"),
-                                       (777, 1, "F32_SPLIT_TF32")])
-def test_depth_first_traversal_matches(S, n, d, dtype):
+@pytest.mark.parametrize("n,d,dtype,levels", [(2048, 2, "F32_SPLIT_BF16", 1), (1001, 3, "F32_SPLIT_BF16", 1),
+                                              (777, 1, "F32_SPLIT_TF32", 1), (2048, 2, "F32_SPLIT_BF16", 2),
+                                              (1001, 3, "F32_SPLIT_BF16", 2), (1300, 3, "F32_SPLIT_TF32", 2),
+                                              (900, 2, "F32_SPLIT_TF32", 2)])
+def test_depth_first_traversal_matches(S, n, d, dtype, levels):
+    # depth first over the top 1 or 2 levels: the divide reads A and B
+    # through the prefix sums of each subtree; same products as breadth first
     A = synth.normal(n, 64, 0)
     B = synth.normal(n, 64, 1)
     want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
@@ -398,12 +402,28 @@ def test_depth_first_traversal_matches(S, n, d, dtype):
     with S.Plan(n, d, S.DType[dtype]) as p:
         ws_bfs = p.workspace_bytes
         Cb = p.mul(dA, dB).cpu().numpy()
-        p.set_traversal(True)
-        assert p.workspace_bytes < ws_bfs * 0.5  # one subtree's operands instead of all
+        p.set_traversal(levels)
+        # the leaf operands shrink to one subtree's (the tables and a staging
+        # copy of C, if any, stay)
+        operands = 2 * p.leaves * p.leaf ** 2 * (4 if dtype == "F32_SPLIT_BF16" else 8)
+        assert ws_bfs - p.workspace_bytes == operands - operands // 7 ** levels
         Cd = p.mul(dA, dB).cpu().numpy()
         p.check()
         check_split(Cd, want, an, bn, dtype, L=p.leaf)
+        p.set_traversal(0)
+        assert p.workspace_bytes == ws_bfs
     assert np.abs(Cd - Cb).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_depth_first_levels_rejected_where_unsupported(S):
+    with S.Plan(500, 1, S.DType.F32_SPLIT_BF16) as p:
+        with pytest.raises(S.StarkError):
+            p.set_traversal(2)  # more levels than the depth
+        with pytest.raises(S.StarkError):
+            p.set_traversal(3)
+    with S.Plan(500, 2, S.DType.I64) as p:
+        with pytest.raises(S.StarkError):
+            p.set_traversal(2)  # the two-level loader serves the split dtypes
 
 
 @pytest.mark.parametrize("bound", [0, 16])
