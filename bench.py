@@ -266,6 +266,34 @@ def run_peel(args, stark, synth, torch):
     return out
 
 
+def run_traversal(args, stark, synth, torch, A, B, C):
+    """The bench product depth first over the top 1 and 2 levels (smaller
+    workspace, one subtree's operands at a time) beside breadth first."""
+    out = {"n": args.n, "depth": args.depth}
+    for levels in (0, 1, 2):
+        with stark.Plan(args.n, args.depth, stark.DType.F32_SPLIT_BF16) as p:
+            try:
+                p.set_traversal(levels)
+            except stark.StarkError as e:
+                out[f"levels{levels}"] = {"unsupported": str(e)}
+                continue
+            for _ in range(2):
+                p.mul(A, B, C)
+            p.check()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                p.mul(A, B, C)
+            e1.record()
+            torch.cuda.synchronize()
+            p.check()
+            ms = e0.elapsed_time(e1) / 5
+            out[f"levels{levels}"] = {"ms": ms, "tflops": 2.0 * args.n ** 3 / (ms * 1e-3) / 1e12,
+                                      "workspace_bytes": p.workspace_bytes}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_serve(args, stark, synth, torch):
     """Served form: Poisson arrivals (200/s), n log-uniform in [256, 8192],
     FP32 N(0,1), 3xBF16, device budget 150 GB; latency from submission to
@@ -663,8 +691,11 @@ def main():
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, stark, synth, torch)
     peel = None
+    traversal = None
     if rank == 0 and not args.no_batch:
         peel = run_peel(args, stark, synth, torch)
+        if args.dtype == "bf16" and args.depth <= 3:
+            traversal = run_traversal(args, stark, synth, torch, A, B, C)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -685,7 +716,7 @@ def main():
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9, "path_roofline": path_roofline,
                "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32, "int64": int64,
-               "batch": batch, "serve": serve, "peel": peel,
+               "batch": batch, "serve": serve, "peel": peel, "traversal": traversal,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     plan.close()
