@@ -266,10 +266,11 @@ def run_peel(args, stark, synth, torch):
     return out
 
 
-def run_traversal(args, stark, synth, torch, A, B, C):
+def run_traversal(args, stark, synth, torch, A, B):
     """The bench product depth first over the top 1 and 2 levels (smaller
     workspace, one subtree's operands at a time) beside breadth first."""
     out = {"n": args.n, "depth": args.depth}
+    C = torch.empty_like(A)
     for levels in (0, 1, 2):
         with stark.Plan(args.n, args.depth, stark.DType.F32_SPLIT_BF16) as p:
             try:
@@ -290,6 +291,7 @@ def run_traversal(args, stark, synth, torch, A, B, C):
             ms = e0.elapsed_time(e1) / 5
             out[f"levels{levels}"] = {"ms": ms, "tflops": 2.0 * args.n ** 3 / (ms * 1e-3) / 1e12,
                                       "workspace_bytes": p.workspace_bytes}
+    del C
     torch.cuda.empty_cache()
     return out
 
@@ -695,7 +697,7 @@ def main():
     if rank == 0 and not args.no_batch:
         peel = run_peel(args, stark, synth, torch)
         if args.dtype == "bf16" and args.depth <= 3:
-            traversal = run_traversal(args, stark, synth, torch, A, B, C)
+            traversal = run_traversal(args, stark, synth, torch, A, B)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
