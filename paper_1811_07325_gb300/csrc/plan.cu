@@ -448,14 +448,35 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
   const int64_t bytes = planes * p->L * p->L * per;
   if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
   const int64_t old = p->P_ws * p->L * p->L * per;
-  cudaFree(p->X);
-  cudaFree(p->Y);
-  p->X = p->Y = nullptr;
-  p->ws_bytes -= 2 * old;
-  if (cudaMalloc(&p->X, (size_t)bytes) != cudaSuccess || cudaMalloc(&p->Y, (size_t)bytes) != cudaSuccess) {
+  // the new workspace first, so that on failure the plan keeps the old one;
+  // when shrinking on a nearly full device, release the old one first
+  void* X = nullptr;
+  void* Y = nullptr;
+  bool ok = cudaMalloc(&X, (size_t)bytes) == cudaSuccess && cudaMalloc(&Y, (size_t)bytes) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
-    return STARK_ENOMEM;
+    cudaFree(X);
+    cudaFree(Y);
+    X = Y = nullptr;
+    if (bytes > old) return STARK_ENOMEM;  // the plan keeps its workspace and traversal
+    cudaFree(p->X);
+    cudaFree(p->Y);
+    p->X = p->Y = nullptr;
+    p->ws_bytes -= 2 * old;
+    p->P_ws = 0;
+    if (cudaMalloc(&X, (size_t)bytes) != cudaSuccess || cudaMalloc(&Y, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(X);
+      cudaFree(Y);
+      return STARK_ENOMEM;  // no workspace: products report ENOMEM until a traversal change succeeds
+    }
+  } else {
+    cudaFree(p->X);
+    cudaFree(p->Y);
+    p->ws_bytes -= 2 * old;
   }
+  p->X = X;
+  p->Y = Y;
   p->ws_bytes += 2 * bytes;
   p->P_ws = planes;
   if (stark_status st = plan_operand_maps(p, planes); st != STARK_OK) return st;
@@ -474,8 +495,11 @@ stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
     p->dfs = levels;
     return STARK_OK;
   }
+  const int prev = p->dfs;
   const stark_status st = plan_alloc_operands(p, p->P / pow7i(levels));
-  p->dfs = st == STARK_OK ? levels : 0;
+  // the traversal follows the workspace that exists (on a failed growth the
+  // plan keeps its previous one)
+  p->dfs = p->P_ws == p->P / pow7i(levels) ? levels : prev;
   return st;
 }
 
@@ -691,6 +715,7 @@ static stark_status to_status(cudaError_t e) {
 // first); top = i1: only the subtree below top-level product M_{i1+1}
 // (depth-first traversal), its leaves in planes 0..7^(d-1)-1.
 stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top) {
+  if (!p->X || !p->Y) return STARK_ENOMEM;  // no workspace (failed reallocation)
   // depth first: the subtree below p->dfs levels along the M-index path `top`
   const int64_t npad = top >= 0 ? p->npad >> p->dfs : p->npad;
   const int depth = top >= 0 ? p->depth - p->dfs : p->depth;
@@ -881,6 +906,7 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
                                  cudaStream_t s) {
   if (p->n == 0) return STARK_OK;
   if (!A || !B || !C) return STARK_EINVAL;
+  if (!p->X || !p->Y) return STARK_ENOMEM;  // a failed workspace reallocation left none
   cudaEvent_t* ev = (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
                         ? &p->ev[(size_t)(p->timing_used - 1) * 4]
                         : nullptr;
