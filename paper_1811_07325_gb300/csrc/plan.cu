@@ -326,20 +326,35 @@ stark_status stark_mul_leaves(stark_plan_t p, const void* A, const void* B, void
 
 // Staging buffers and pipeline streams for the host entry points.
 static stark_status ensure_host_pipeline(stark_plan_t p) {
-  if (p->s_in) return STARK_OK;
+  if (p->ev_out[1]) return STARK_OK;  // created last: the whole pipeline exists
+  // all or nothing: on any failure release what this call created
   const size_t bytes = (size_t)p->n * p->n * p->esz;
   void** bufs[6] = {&p->stage_A, &p->stage_B, &p->stage_C, &p->stage2[0], &p->stage2[1], &p->stage2[2]};
+  cudaStream_t* streams[3] = {&p->s_in, &p->s_comp, &p->s_out};
+  cudaEvent_t* events[6] = {&p->ev_in[0], &p->ev_comp[0], &p->ev_out[0], &p->ev_in[1], &p->ev_comp[1], &p->ev_out[1]};
+  stark_status st = STARK_OK;
   for (void** b : bufs)
-    if (cudaMalloc(b, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return STARK_ENOMEM;
+    if (st == STARK_OK && cudaMalloc(b, bytes) != cudaSuccess) st = STARK_ENOMEM;
+  for (cudaStream_t* x : streams)
+    if (st == STARK_OK && cudaStreamCreateWithFlags(x, cudaStreamNonBlocking) != cudaSuccess) st = STARK_ECUDA;
+  for (cudaEvent_t* e : events)
+    if (st == STARK_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) st = STARK_ECUDA;
+  if (st != STARK_OK) {
+    cudaGetLastError();
+    for (void** b : bufs) {
+      cudaFree(*b);
+      *b = nullptr;
     }
-  for (cudaStream_t* st : {&p->s_in, &p->s_comp, &p->s_out})
-    if (cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) return STARK_ECUDA;
-  for (int i = 0; i < 2; ++i)
-    for (cudaEvent_t* e : {&p->ev_in[i], &p->ev_comp[i], &p->ev_out[i]})
-      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return STARK_ECUDA;
-  return STARK_OK;
+    for (cudaStream_t* x : streams) {
+      if (*x) cudaStreamDestroy(*x);
+      *x = nullptr;
+    }
+    for (cudaEvent_t* e : events) {
+      if (*e) cudaEventDestroy(*e);
+      *e = nullptr;
+    }
+  }
+  return st;
 }
 
 // The host pipeline: copies in on s_in, products on s_comp, copies out on
