@@ -228,9 +228,11 @@ STARK_API stark_status stark_plan_set_raster(stark_plan_t plan, int band);
 STARK_API stark_status stark_plan_set_tf32_layout(stark_plan_t plan, int mn);
 
 /* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1
- * stages K = 32 per step in four 48 KB buffers (64-byte swizzle), 0 stages
- * K = 64 in two 96 KB buffers (128-byte swizzle).  Same results up to the
- * combine's addition order. */
+ * runs single CTAs that stage K = 32 per step in four 48 KB buffers
+ * (64-byte swizzle), in place of the leaf schedule of
+ * stark_plan_set_pairing; 0 (default) keeps that schedule (CTA pairs: K = 64
+ * in three 64 KB buffers per CTA; single CTAs: two 96 KB buffers).  Same
+ * results up to the combine's addition order.  Errors: EINVAL. */
 STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
 
 /* Traversal of the recursion tree (memory-lean form; the paper names the

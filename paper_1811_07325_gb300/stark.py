@@ -285,7 +285,9 @@ class Plan:
         _check(_lib.stark_plan_set_raster(self._h, int(band)), "stark_plan_set_raster")
 
     def set_pipeline(self, deep: bool):
-        """3xBF16 operand pipeline: four 48 KB stages (deep) or two 96 KB ones."""
+        """3xBF16: ``deep=True`` runs the single-CTA schedule with four 48 KB
+        stages of 64-byte rows (it replaces the CTA pairs); False restores the
+        plan's leaf schedule."""
         _check(_lib.stark_plan_set_pipeline(self._h, 1 if deep else 0), "stark_plan_set_pipeline")
 
     def set_traversal(self, levels):
