@@ -329,7 +329,7 @@ STARK_API stark_status stark_batch_check(stark_batch_t batch, void *stream);
 typedef struct stark_server_s *stark_server_t;
 
 /* Continuous-batching request server on the current device (the serving
- * form of the benchmark spec; the paper has no serving layer).  One dispatcher
+ * form of the product; the paper has no serving layer).  One dispatcher
  * thread admits queued requests in arrival order while a stream slot is free
  * and their workspace fits `hbm_budget_bytes` (device bytes the server may
  * own for workspaces; idle workspaces are evicted least recently used first
@@ -337,14 +337,21 @@ typedef struct stark_server_s *stark_server_t;
  * requests and runs their divides plus ONE grouped leaf launch (as
  * stark_batch_mul), so requests arriving while others run overlap with them
  * on the device.  Workspaces are cached per padded size and stay resident.
- * Thread-safe.  Errors: EINVAL (budget 0, slots outside 1..64),
+ * A size whose breadth-first workspace (the operands of all 7^depth leaves)
+ * exceeds the budget gets a depth-first workspace instead, holding the
+ * operands of one subtree below the top 1 or 2 recursion levels (1/7 or 1/49
+ * of the bytes; the fewest levels that fit; as stark_plan_set_traversal);
+ * its requests run alone, subtree by subtree, not in the grouped launch.
+ * When no traversal fits at the automatic depth, the fitting depth that the
+ * cost model ranks fastest serves the request.  Thread-safe.  Errors: EINVAL (budget 0, slots outside 1..64),
  * EUNSUPPORTED, ENOMEM. */
 STARK_API stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_server_t *out);
 
 /* Queue C = A*B (device pointers, n x n row-major, element type of dtype)
  * and return its id at once.  A, B, C must stay valid and unmodified until
- * stark_poll reports the request done.  ENOMEM: the request alone does not
- * fit the budget (it could never be admitted); EINVAL: bad arguments. */
+ * stark_poll reports the request done.  ENOMEM: the request alone fits the
+ * budget at no depth, even depth first (it could never be admitted); EINVAL:
+ * bad arguments. */
 STARK_API stark_status stark_submit(stark_server_t server, int64_t n, stark_dtype dtype, const void *A,
                                     const void *B, void *C, uint64_t *req_id);
 

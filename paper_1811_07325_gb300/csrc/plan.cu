@@ -503,9 +503,7 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
 
 stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
   if (!p || levels < 0 || levels > 2) return STARK_EINVAL;
-  // the subtree below `levels` is at most 2 (one level) or 1 (two levels) deep
-  if (levels && (p->depth < levels || p->depth > 3 || p->combine_mode == 2)) return STARK_EUNSUPPORTED;
-  if (levels == 2 && !p->is_tc) return STARK_EUNSUPPORTED;  // two-level loader: split dtypes
+  if (!traversal_supported(p->depth, p->dt, levels) || (levels && p->combine_mode == 2)) return STARK_EUNSUPPORTED;
   if (levels == p->dfs || p->n == 0) {
     p->dfs = levels;
     return STARK_OK;
@@ -619,7 +617,15 @@ stark_status stark_selftest_bounded_wait(uint64_t timeout_ns) {
 // ====================================================================== plan internals
 namespace stark {
 
-stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel) {
+bool traversal_supported(int depth, stark_dtype dt, int levels) {
+  if (levels == 0) return true;
+  // the subtree below `levels` is at most 2 (one level) or 1 (two levels) deep
+  if (levels < 0 || levels > 2 || depth < levels || depth > 3) return false;
+  return levels == 1 || dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+}
+
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel, int dfs) {
+  if (!traversal_supported(depth, dt, dfs)) return STARK_EUNSUPPORTED;
   p->n = n;
   p->depth = depth;
   p->dt = dt;
@@ -631,13 +637,14 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bo
   p->npad = padded_side(core, depth, dt);
   p->L = p->npad >> depth;
   p->P = pow7i(depth);
-  p->P_ws = p->P;
+  p->P_ws = p->P / pow7i(dfs);
+  p->dfs = dfs;
   p->bn = (p->L % 256 == 0) ? 256 : 128;
   cudaGetDevice(&p->device);
   p->num_sms = device_sm_count();
   if (p->L > 0x7FFFFFFF / 2) return STARK_EINVAL;
 
-  const int64_t ws = operand_bytes(core, depth, dt);
+  const int64_t ws = operand_bytes(core, depth, dt) / pow7i(dfs);
   if (cudaMalloc(&p->X, (size_t)(ws / 2)) != cudaSuccess || cudaMalloc(&p->Y, (size_t)(ws / 2)) != cudaSuccess) {
     cudaGetLastError();
     return STARK_ENOMEM;
@@ -676,7 +683,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bo
     // C cannot be a TMA target: combine into a staging copy with an aligned pitch
     if (stark_status e = plan_ensure_cstage(p); e != STARK_OK) return e;
   }
-  return plan_operand_maps(p, p->P);
+  return plan_operand_maps(p, p->P_ws);
 }
 
 stark_status plan_operand_maps(stark_plan_s* p, int64_t planes) {

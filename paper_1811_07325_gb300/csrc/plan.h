@@ -97,7 +97,14 @@ namespace stark {
 // peel: run the recursion on the largest m <= n that the tiling divides and
 // finish the r = n - m edge rows/columns with classical products (when n is
 // already a multiple, or smaller than one tile granule, nothing is peeled).
-stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel = false);
+// dfs: allocate the workspace for the depth-first traversal over that many
+// top levels (one subtree's operands) from the start; traversal_supported
+// must hold for it.
+stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel = false, int dfs = 0);
+// Whether the depth-first traversal over `levels` top levels exists for this
+// depth and dtype (subtree loaders cover depth <= 3; two levels only for the
+// split dtypes).  0 (breadth first) always does.
+bool traversal_supported(int depth, stark_dtype dt, int levels);
 // Tensor maps of the split dtypes' operand planes (for `planes` leaves per half).
 stark_status plan_operand_maps(stark_plan_s* p, int64_t planes);
 // Side of the product the recursion covers (n minus the peeled edge).

@@ -6,6 +6,13 @@
 //     workspace for its (n_pad, depth, dtype) bucket is idle in the cache, or
 //     a new one fits the device-memory budget (idle workspaces of other
 //     buckets are evicted, least recently used first, to make room);
+//   * a bucket whose breadth-first workspace (all 7^d leaves' operands) is
+//     larger than the whole budget gets a depth-first one instead: the
+//     operands of one subtree below the top 1 or 2 recursion levels, 1/7 or
+//     1/49 of the bytes (the fewest levels that fit); its requests run alone,
+//     subtree after subtree, instead of in the grouped launch.  When no
+//     traversal fits at the chosen depth, the fitting depth that the cost
+//     model ranks fastest serves the request;
 //   * every free stream slot takes a micro-batch of the admitted requests:
 //     their C zeroing and divides, then ONE grouped leaf launch over all
 //     their leaf products (the same kernel as stark_batch_mul), then an
@@ -78,7 +85,7 @@ struct stark_server_s {
   std::unordered_map<uint64_t, stark::Request*> live;  // queued or running
   std::unordered_map<uint64_t, std::pair<stark_status, double>> finished;  // not yet reaped
   std::unordered_map<uint64_t, double> latency;                          // every finished request
-  std::map<std::tuple<int64_t, int, int>, std::vector<stark::Workspace>> cache;  // (npad, depth, dt)
+  std::map<std::tuple<int64_t, int, int, int>, std::vector<stark::Workspace>> cache;  // (npad, depth, dt, dfs)
   std::vector<stark::Slot> slots;
   std::thread worker;
   bool stop = false;
@@ -97,22 +104,52 @@ int depth_for(int64_t n, stark_dtype dt) {
   return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
 }
 
-// Find or make an idle workspace for request r (server mutex held).
-stark_plan_s* acquire_workspace(stark_server_s* s, const Request& r, stark_status* err) {
-  const int d = depth_for(r.n, r.dt);
-  const int64_t npad = padded_side(r.n, d, r.dt);
-  auto key = std::make_tuple(npad, d, (int)r.dt);
-  auto& pool = s->cache[key];
-  for (auto& w : pool)
-    if (!w.busy) {
-      w.busy = true;
-      w.last_used = Clock::now();
-      return w.plan;
+// Device bytes of a workspace for side npad over `levels` depth-first levels
+// (the quadrant tables and error word fit in the 1 MB margin).
+size_t workspace_need(int64_t npad, int d, stark_dtype dt, int levels) {
+  return (size_t)(operand_bytes(npad, d, dt) / pow7i(levels)) + (1u << 20);
+}
+
+// Split dtypes combine a C that TMA cannot address (n % 4 != 0) in the
+// workspace's staging copy of side npad.
+bool needs_stage(int64_t n, stark_dtype dt, const void* C) {
+  return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) && !c_is_tma_target(C, n);
+}
+size_t stage_bytes(int64_t npad) { return (size_t)npad * (size_t)staged_ld(npad) * sizeof(float); }
+
+// Traversal of a bucket's workspace: breadth first when it (plus `extra`
+// bytes) fits the budget, else the fewest depth-first levels that fit; -1
+// when none does.
+int admit_levels(int64_t npad, int d, stark_dtype dt, size_t extra, size_t budget) {
+  for (int levels = 0; levels <= 2; ++levels)
+    if (traversal_supported(d, dt, levels) && workspace_need(npad, d, dt, levels) + extra <= budget) return levels;
+  return -1;
+}
+
+// Depth and traversal of a request of side n: `first` (the dispatcher's
+// depth; -1 for none) with the fewest depth-first levels that fit the
+// budget, else the fitting depth the cost model ranks fastest.  false when
+// no depth fits.
+bool admission(int64_t n, stark_dtype dt, bool staged, size_t budget, int first, int* depth, int* levels) {
+  std::vector<std::pair<double, int>> order;
+  for (int d = 0; d <= kMaxDepth; ++d) order.emplace_back(d == first ? -1.0 : model_seconds(n, d, dt), d);
+  std::sort(order.begin(), order.end());
+  for (const auto& c : order) {
+    const int64_t npad = padded_side(n, c.second, dt);
+    const int l = admit_levels(npad, c.second, dt, staged ? stage_bytes(npad) : 0, budget);
+    if (l >= 0) {
+      *depth = c.second;
+      *levels = l;
+      return true;
     }
-  // a new workspace: how big, and does it fit once idle ones are evicted?
-  const size_t need = (size_t)operand_bytes(npad, d, r.dt) + (1u << 20);
+  }
+  return false;
+}
+
+// Evict idle workspaces, least recently used first, until `need` more bytes
+// fit the budget; false when the busy ones alone leave no room.
+bool make_room(stark_server_s* s, size_t need) {
   while (s->owned + need > s->budget) {
-    // evict the least recently used idle workspace of any bucket
     Workspace* victim = nullptr;
     std::vector<Workspace>* vpool = nullptr;
     for (auto& kv : s->cache)
@@ -121,21 +158,62 @@ stark_plan_s* acquire_workspace(stark_server_s* s, const Request& r, stark_statu
           victim = &w;
           vpool = &kv.second;
         }
-    if (!victim) {
-      *err = STARK_EBUSY;  // wait for running requests to free memory
-      return nullptr;
-    }
+    if (!victim) return false;
     s->owned -= (size_t)victim->plan->ws_bytes;
     plan_release(victim->plan);
     delete victim->plan;
     vpool->erase(vpool->begin() + (victim - vpool->data()));
   }
-  auto* p = new (std::nothrow) stark_plan_s();
+  return true;
+}
+
+void release_workspace(stark_server_s* s, stark_plan_s* p);
+
+// Find or make an idle workspace for request r, with its staging copy of C
+// where it needs one (server mutex held).  EBUSY: it fits the budget once
+// running requests free their workspaces.
+stark_plan_s* acquire_workspace(stark_server_s* s, const Request& r, stark_status* err) {
+  const bool staged = needs_stage(r.n, r.dt, r.C);
+  int d = 0, levels = 0;
+  if (!admission(r.n, r.dt, staged, s->budget, depth_for(r.n, r.dt), &d, &levels)) {
+    *err = STARK_ENOMEM;
+    return nullptr;
+  }
+  const int64_t npad = padded_side(r.n, d, r.dt);
+  const size_t stage = staged ? stage_bytes(npad) : 0;
+  auto key = std::make_tuple(npad, d, (int)r.dt, levels);
+  stark_plan_s* p = nullptr;
+  for (auto& w : s->cache[key])
+    if (!w.busy) {
+      w.busy = true;
+      w.last_used = Clock::now();
+      p = w.plan;  // the entry itself may move while room is made below
+      break;
+    }
+  if (p) {
+    if (stage && !p->cstage) {
+      const int64_t before = p->ws_bytes;
+      if (!make_room(s, stage) || plan_ensure_cstage(p) != STARK_OK) {
+        release_workspace(s, p);
+        *err = STARK_EBUSY;
+        return nullptr;
+      }
+      s->owned += (size_t)(p->ws_bytes - before);
+    }
+    return p;
+  }
+  // a new workspace: does it fit once idle ones are evicted?
+  if (!make_room(s, workspace_need(npad, d, r.dt, levels) + stage)) {
+    *err = STARK_EBUSY;  // wait for running requests to free memory
+    return nullptr;
+  }
+  p = new (std::nothrow) stark_plan_s();
   if (!p) {
     *err = STARK_ENOMEM;
     return nullptr;
   }
-  stark_status st = plan_init(p, npad, d, r.dt);  // sized for the whole bucket
+  stark_status st = plan_init(p, npad, d, r.dt, false, levels);  // sized for the whole bucket
+  if (st == STARK_OK && stage) st = plan_ensure_cstage(p);
   if (st != STARK_OK) {
     plan_release(p);
     delete p;
@@ -171,27 +249,25 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
   cudaStream_t st = slot.stream;
   std::vector<Request*> tc;
   for (Request* r : reqs) {
+    const bool split = r->dt == STARK_F32_SPLIT_BF16 || r->dt == STARK_F32_SPLIT_TF32;
+    // C that TMA cannot address is combined in the workspace's staging copy
+    // (allocated at admission, inside the budget)
+    const bool staged = needs_stage(r->n, r->dt, r->C);
+    if (staged && !r->ws->cstage) return STARK_ENOMEM;
     stark_plan_s view = *r->ws;  // the bucket workspace, bounds of this request
     view.n = r->n;
     view.ev.clear();
     view.timing_cap = 0;
     stark_status e;
-    if (r->dt == STARK_F32_SPLIT_BF16 || r->dt == STARK_F32_SPLIT_TF32) {
-      // C that TMA cannot address (n % 4 != 0) is combined in the bucket's staging copy
-      if (!c_is_tma_target(r->C, r->n)) {
-        const int64_t before = r->ws->ws_bytes;
-        if (plan_ensure_cstage(r->ws) != STARK_OK) return STARK_ENOMEM;
-        s->owned += (size_t)(r->ws->ws_bytes - before);
-        r->target = r->ws->cstage;
-        r->ld = staged_ld(r->n);
-      } else {
-        r->target = r->C;
-        r->ld = r->n;
-      }
+    if (split && !r->ws->dfs) {
+      r->target = staged ? r->ws->cstage : r->C;
+      r->ld = staged ? staged_ld(r->n) : r->n;
       if (cudaMemsetAsync(r->target, 0, (size_t)r->n * r->ld * sizeof(float), st) != cudaSuccess) return STARK_ECUDA;
       e = plan_divide(&view, r->A, r->B, st);
       tc.push_back(r);
     } else {
+      // plain dtypes, and depth-first workspaces (one subtree's operands at a
+      // time): the plan's own sequence on this slot's stream
       e = plan_run(&view, r->A, r->B, r->C, 0, view.P, st);
     }
     if (e != STARK_OK) return e;
@@ -398,8 +474,8 @@ stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const voi
   if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
     return STARK_EINVAL;
   if (n > 0 && (!A || !B || !C)) return STARK_EINVAL;
-  const int d = choose_depth(n, dt);
-  if ((size_t)operand_bytes(padded_side(n, d, dt), d, dt) + (1u << 20) > s->budget) return STARK_ENOMEM;
+  int d = 0, levels = 0;
+  if (!admission(n, dt, needs_stage(n, dt, C), s->budget, -1, &d, &levels)) return STARK_ENOMEM;  // no depth fits
   auto* r = new (std::nothrow) Request();
   if (!r) return STARK_ENOMEM;
   r->n = n;

@@ -144,6 +144,95 @@ def test_server_admission_under_small_budget(stark_lib):
         assert np.array_equal(dC[i].cpu().numpy(), oracle.gemm_classical(As[i], Bs[i])), n
 
 
+def _dispatch_depth(S, dtype, candidates):
+    """First candidate size whose automatic depth (the one the dispatcher takes:
+    measured for the split dtypes and cached per process, the cost model
+    otherwise) has a depth-first traversal, with that depth and leaf side."""
+    for n in candidates:
+        with S.Plan(n, -1, dtype) as p:
+            d, L = p.depth, p.leaf
+        if 1 <= d <= 3:
+            return n, d, L
+    pytest.skip("no candidate size with a depth the depth-first traversal serves")
+
+
+@pytest.mark.parametrize("dtype,candidates", [("F32_SPLIT_BF16", (4096, 3072, 2048, 6144)),
+                                              ("F64", (1024, 1536, 768)),
+                                              ("I64", (1024, 1536, 768))])
+def test_server_admits_depth_first_beyond_breadth_first_budget(stark_lib, dtype, candidates):
+    S = stark_lib
+    dt = getattr(S.DType, dtype)
+    n, d, L = _dispatch_depth(S, dt, candidates)
+    per = 4 if dtype == "F32_SPLIT_BF16" else 8  # hi+lo bf16, or one 8-byte value per operand element
+    breadth_first = 2 * 7 ** d * L * L * per
+    budget = breadth_first // 2  # the breadth-first workspace never fits; one subtree's does
+    sizes = [n, n - 3, n - 64]   # one padded bucket; n - 3 is not a TMA target (staged C)
+    if dtype == "F32_SPLIT_BF16":
+        As = [synth.normal(m, 700 + i, 0) for i, m in enumerate(sizes)]
+        Bs = [synth.normal(m, 700 + i, 1) for i, m in enumerate(sizes)]
+        tdt = torch.float32
+    elif dtype == "F64":
+        As = [synth.uniform(m, 700 + i, 0) for i, m in enumerate(sizes)]
+        Bs = [synth.uniform(m, 700 + i, 1) for i, m in enumerate(sizes)]
+        tdt = torch.float64
+    else:
+        As = [synth.integers(m, 700 + i, 0, -(1 << 20), 1 << 20) for i, m in enumerate(sizes)]
+        Bs = [synth.integers(m, 700 + i, 1, -(1 << 20), 1 << 20) for i, m in enumerate(sizes)]
+        tdt = torch.int64
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    dC = [torch.full((m, m), 7, dtype=tdt, device="cuda") for m in sizes]  # overwritten
+    torch.cuda.synchronize()
+    with S.Server(budget, slots=2) as srv:
+        ids = [srv.submit(dA[i], dB[i], dC[i], dt) for i in range(len(sizes))]
+        status = wait_all(srv, ids)
+        assert all(st == S.Status.OK for st in status.values()), status
+        st = srv.stats()
+        assert 0 < st["owned_bytes"] <= budget < breadth_first
+    for i, m in enumerate(sizes):
+        got = dC[i].cpu().numpy()
+        if dtype == "I64":
+            assert np.array_equal(got, oracle.gemm_classical(As[i], Bs[i])), m
+            continue
+        with S.Plan(m, d, dt) as p:  # breadth first, alone
+            solo = p.mul(dA[i], dB[i])
+            p.check()
+        # same leaf kernels; only the order of the combine's additions differs
+        assert (dC[i] - solo).abs().max().item() <= 1e-5 * solo.abs().max().item(), m
+        rows = np.unique(np.concatenate([np.arange(0, m, 97), [m - 1]]))
+        want = oracle.gemm_rows(As[i], Bs[i], rows)
+        ratio = np.abs(got[rows].astype(np.float64) - want).max() / (
+            np.linalg.norm(As[i].astype(np.float64)) * np.linalg.norm(Bs[i].astype(np.float64)))
+        assert ratio <= (1e-6 if dtype == "F32_SPLIT_BF16" else 1e-12), (m, ratio)
+
+
+def test_server_falls_back_to_a_depth_that_fits(stark_lib):
+    S = stark_lib
+    # FP64, side 1024: at depth 1 one subtree's operands are 2 x 512^2 x 8 B =
+    # 4 MiB (+ 1 MiB margin for the tables).  Deeper or breadth-first
+    # workspaces are larger, so under this budget every request runs at depth
+    # 1 depth first, one workspace at a time
+    budget = (5 << 20) + (512 << 10)
+    sizes = [1024, 1021, 1024]
+    As = [synth.uniform(m, 800 + i, 0) for i, m in enumerate(sizes)]
+    Bs = [synth.uniform(m, 800 + i, 1) for i, m in enumerate(sizes)]
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    dC = [torch.empty((m, m), dtype=torch.float64, device="cuda") for m in sizes]
+    torch.cuda.synchronize()
+    with S.Server(budget, slots=3) as srv:
+        ids = [srv.submit(dA[i], dB[i], dC[i], S.DType.F64) for i in range(len(sizes))]
+        status = wait_all(srv, ids)
+        assert all(st == S.Status.OK for st in status.values()), status
+        st = srv.stats()
+        assert st["cached_workspaces"] == 1 and 0 < st["owned_bytes"] <= budget
+        with pytest.raises(S.StarkError) as e:  # below one subtree at any depth
+            srv.submit(*[torch.zeros((2048, 2048), dtype=torch.float64, device="cuda")] * 3, S.DType.F64)
+        assert e.value.status == S.Status.ENOMEM
+    for i, m in enumerate(sizes):
+        A64, B64 = As[i], Bs[i]
+        diff = dC[i].cpu().numpy() - oracle.gemm_classical(A64, B64)
+        assert np.abs(diff).max() / (np.linalg.norm(A64) * np.linalg.norm(B64)) <= 1e-12, m
+
+
 def test_server_unknown_id(stark_lib):
     S = stark_lib
     with S.Server(1 << 30, slots=1) as srv:
