@@ -157,10 +157,11 @@ def cpu_baseline(n, seed, budget_s=12.0, rows_cap=4096):
 
 def oracle_timings(seed):
     """The oracle's own times at the smaller configurations, beside the GPU:
-    the classical FP64 product on all host cores (n = 1024, 4096) and the
-    serial FP64 Strassen recursion (Alg. 1) on one core (n = 1024 at depth 3,
-    n = 2048 at depth 3), the latter scaled to n = 16384 at depth 6 (the same
-    leaf side, 256) by 7^3 and labelled as extrapolated."""
+    the classical FP64 product on all host cores (n = 1024, 4096) and on one
+    core (n = 1024), and the serial FP64 Strassen recursion (Alg. 1) on one
+    core (n = 1024 at depth 3, n = 2048 at depth 3), the latter scaled to
+    n = 16384 at depth 6 (the same leaf side, 256) by 7^3 and labelled as
+    extrapolated."""
     import oracle
     from paper_1811_07325_gb300 import synth
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -175,6 +176,16 @@ def oracle_timings(seed):
         t = timed(lambda: oracle.gemm_classical(A, B))
         out[f"classical_n{n}_s"] = t
         out[f"classical_n{n}_tflops"] = 2.0 * n ** 3 / t / 1e12
+    # one core: a child process, so that OpenMP starts with a single thread
+    code = ("import time, oracle\nfrom paper_1811_07325_gb300 import synth\n"
+            f"A, B = synth.uniform(1024, {int(seed)}, 0), synth.uniform(1024, {int(seed)}, 1)\n"
+            "t0 = time.perf_counter()\noracle.gemm_classical(A, B)\nprint(time.perf_counter() - t0)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"),
+                       capture_output=True, text=True, timeout=900)
+    if r.returncode == 0:
+        t = float(r.stdout.split()[-1])
+        out["classical_n1024_1core_s"] = t
+        out["classical_n1024_1core_tflops"] = 2.0 * 1024 ** 3 / t / 1e12
     for n in (1024, 2048):
         A, B = synth.uniform(n, seed, 0), synth.uniform(n, seed, 1)
         t = timed(lambda: oracle.strassen(A, B, 3))
