@@ -347,6 +347,22 @@ typedef struct stark_server_s *stark_server_t;
  * EUNSUPPORTED, ENOMEM. */
 STARK_API stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_server_t *out);
 
+/* How a server with `hbm_budget_bytes` would hold a request of side n, on
+ * the host alone (no device work): the recursion depth, the depth-first
+ * levels of its workspace (0: breadth first) and the device bytes the server
+ * counts against its budget for it: the leaf operand planes (2 * 7^depth *
+ * L^2 * 4 bytes for 3xBF16, * 8 for 3xTF32, F64, I64; L = n_pad / 2^depth),
+ * divided by 7^levels, plus 1 MiB for the quadrant tables, plus the staging
+ * copy of C (n_pad^2 * 4 bytes) when `staged` is non-zero and the dtype is a
+ * split one (its C is one TMA cannot address: n % 4 != 0 or not 16-byte
+ * aligned).  The depth is the cost model's choice, or the fitting depth the
+ * cost model ranks fastest; for F64 and I64 that is the dispatcher's choice,
+ * for the split dtypes the dispatcher tries its measured depth first.  Any
+ * output pointer may be NULL.  ENOMEM: no depth fits (stark_submit refuses
+ * such a request); EINVAL: n outside 0..2^20 or an unknown dtype. */
+STARK_API stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dtype dtype, int staged,
+                                              int32_t *depth, int32_t *levels, int64_t *bytes);
+
 /* Queue C = A*B (device pointers, n x n row-major, element type of dtype)
  * and return its id at once.  A, B, C must stay valid and unmodified until
  * stark_poll reports the request done.  ENOMEM: the request alone fits the

@@ -468,6 +468,21 @@ stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_s
   return STARK_OK;
 }
 
+stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dtype dt, int staged, int32_t* depth,
+                                    int32_t* levels, int64_t* bytes) {
+  if (n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
+  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
+    return STARK_EINVAL;
+  const bool split = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+  int d = 0, l = 0;
+  if (!admission(n, dt, split && staged, hbm_budget_bytes, choose_depth(n, dt), &d, &l)) return STARK_ENOMEM;
+  const int64_t npad = padded_side(n, d, dt);
+  if (depth) *depth = d;
+  if (levels) *levels = l;
+  if (bytes) *bytes = (int64_t)(workspace_need(npad, d, dt, l) + (split && staged ? stage_bytes(npad) : 0));
+  return STARK_OK;
+}
+
 stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const void* A, const void* B, void* C,
                           uint64_t* req_id) {
   if (!s || !req_id || n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;

@@ -93,6 +93,8 @@ _SIGS = {
     "stark_request_latency": ([_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], _ci),
     "stark_server_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
     "stark_server_destroy": ([_vp], _ci),
+    "stark_server_admission": ([ctypes.c_size_t, _i64, _ci, _ci, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_i64)], _ci),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -432,6 +434,16 @@ class Server:
         _check(_lib.stark_server_stats(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(q)),
                "stark_server_stats")
         return {"cached_workspaces": w.value, "owned_bytes": b.value, "queued": q.value}
+
+
+def server_admission(hbm_budget_bytes: int, n: int, dtype: DType = DType.F32_SPLIT_BF16, staged: bool = False):
+    """How a server with this budget holds a request of side n (host only):
+    {"depth", "levels" (depth-first levels; 0 breadth first), "bytes"}.
+    Raises StarkError (ENOMEM) when no depth fits."""
+    d, l, b = _i32(), _i32(), _i64()
+    _check(_lib.stark_server_admission(int(hbm_budget_bytes), int(n), int(dtype), 1 if staged else 0,
+                                       ctypes.byref(d), ctypes.byref(l), ctypes.byref(b)), "stark_server_admission")
+    return {"depth": d.value, "levels": l.value, "bytes": b.value}
 
 
 def quadrant_table(depth: int, side: int):
