@@ -149,7 +149,7 @@ def cpu_baseline(n, seed, budget_s=12.0, rows_cap=4096):
     t0 = time.perf_counter()
     oracle.gemm_rows(A, B, idx)
     t = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = min(int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), rows)  # one row per thread at most
     return {"value": 2.0 * n * n * rows / t / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"classical FP64 row products (C rows = A rows . B), {rows} of {n} rows, "
                       f"{t:.1f} s on {threads} OpenMP threads"}
@@ -377,14 +377,22 @@ def run_reference(args, rank, world):
     """--impl reference: the CPU oracle, timed on the host cores, rank 0 only."""
     if rank != 0:
         return None
+    if world > 1:
+        # the launcher gives every rank one OpenMP thread; rank 0 alone works
+        # here, so it takes the host's cores (set before the oracle's OpenMP
+        # runtime loads)
+        os.environ["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
     import oracle
     from paper_1811_07325_gb300 import synth
     n = args.n
     A = synth.normal(n, args.seed, 0)
     B = synth.normal(n, args.seed, 1)
-    rows_per_step = args.ref_rows
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # the oracle spreads rows over its OpenMP threads: one row per thread by default
+    rows_per_step = max(1, min(n, args.ref_rows if args.ref_rows > 0 else threads))
+    cores = min(threads, rows_per_step)
     for w in range(args.warmup):
-        oracle.gemm_rows(A, B, np.arange(rows_per_step) + w * rows_per_step)
+        oracle.gemm_rows(A, B, (np.arange(rows_per_step) + w * rows_per_step) % n)
     times = []
     for k in range(args.steps):
         idx = (np.arange(rows_per_step) + k * rows_per_step) % n
@@ -393,15 +401,14 @@ def run_reference(args, rank, world):
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     value = 2.0 * n * n * rows_per_step / t / 1e12
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"classical FP64 oracle, {rows_per_step} of {n} rows of C per step"
+    sample = f"classical FP64 oracle, {rows_per_step} of {n} rows of C per step on {cores} OpenMP threads"
     return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(args, args.depth), reference_arm="CPU oracle (classical FP64), "
                            "row-sampled: each step computes a bounded sample of rows of this product"),
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -417,7 +424,8 @@ def main():
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=12)
-    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="--impl reference: rows of C per step (0: one per OpenMP thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-check", action="store_true")

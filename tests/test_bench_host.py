@@ -1,7 +1,8 @@
 """Host-side logic of bench.py, without a GPU: the gate that attaches a
 measured DRAM traffic figure only when the committed ncu summary was taken
 on the current kernel source and workload, the peak fallback, the workload
-description, and the CPU-baseline record (on a tiny sample)."""
+description, the CPU-baseline record (on a tiny sample), and the reference
+arm's line (the CPU oracle) alone and under torchrun."""
 import json
 import os
 import sys
@@ -64,3 +65,33 @@ def test_cpu_baseline_record_on_a_tiny_sample():
     rec = bench.cpu_baseline(64, 7, budget_s=0.01, rows_cap=16)
     assert rec["kind"] == "oracle" and rec["unit"] == "TFLOP/s" and rec["value"] > 0 and rec["cores"] >= 1
     assert "of 64 rows" in rec["sample"]
+
+
+def _run_reference(cmd, env_extra=None):
+    import subprocess
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    pytest.importorskip("oracle")
+    (out,) = _run_reference([sys.executable, "bench.py", "--impl", "reference", "--n", "256", "--steps", "2",
+                             "--warmup", "3"], {"OMP_NUM_THREADS": "3"})
+    assert out["impl"] == "reference" and out["n_gpus"] == 1 and out["steps"] == 2 and out["warmup"] == 3
+    assert out["value"] > 0 and out["e2e"]["value"] == out["value"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
+    # one row of C per OpenMP thread, and the record says how many threads worked
+    assert out["cpu_baseline"]["cores"] == 3 and "3 of 256 rows" in out["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_under_torchrun_prints_once_on_all_cores():
+    pytest.importorskip("oracle")
+    outs = _run_reference([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                           "--master-addr", "127.0.0.1", "--master-port", "29561", "bench.py", "--impl",
+                           "reference", "--gpus", "2", "--steps", "2", "--warmup", "3"])  # (torchrun reads --n as its own)
+    assert len(outs) == 1 and outs[0]["n_gpus"] == 2  # rank 0 alone
+    # the launcher's one thread per rank does not bind the one rank that works
+    assert outs[0]["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
