@@ -349,8 +349,10 @@ STARK_API stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slot
 
 /* How a server with `hbm_budget_bytes` would hold a request of side n, on
  * the host alone (no device work): the recursion depth, the depth-first
- * levels of its workspace (0: breadth first) and the device bytes the server
- * counts against its budget for it: the leaf operand planes (2 * 7^depth *
+ * levels of its workspace (0: breadth first; the limited-memory traversal
+ * against the O(3^l N^2) space growth of Sec. VI) and the device bytes the
+ * server counts against its budget for it: the leaf operand planes that the
+ * divide (Alg. 3) writes for the 7^depth leaves of Alg. 1 (2 * 7^depth *
  * L^2 * 4 bytes for 3xBF16, * 8 for 3xTF32, F64, I64; L = n_pad / 2^depth),
  * divided by 7^levels, plus 1 MiB for the quadrant tables, plus the staging
  * copy of C (n_pad^2 * 4 bytes) when `staged` is non-zero and the dtype is a
