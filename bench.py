@@ -180,12 +180,15 @@ def oracle_timings(seed):
     code = ("import time, oracle\nfrom paper_1811_07325_gb300 import synth\n"
             f"A, B = synth.uniform(1024, {int(seed)}, 0), synth.uniform(1024, {int(seed)}, 1)\n"
             "t0 = time.perf_counter()\noracle.gemm_classical(A, B)\nprint(time.perf_counter() - t0)\n")
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"),
-                       capture_output=True, text=True, timeout=900)
-    if r.returncode == 0:
-        t = float(r.stdout.split()[-1])
-        out["classical_n1024_1core_s"] = t
-        out["classical_n1024_1core_tflops"] = 2.0 * 1024 ** 3 / t / 1e12
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=900)
+        if r.returncode == 0:
+            t = float(r.stdout.split()[-1])
+            out["classical_n1024_1core_s"] = t
+            out["classical_n1024_1core_tflops"] = 2.0 * 1024 ** 3 / t / 1e12
+    except (subprocess.SubprocessError, OSError, ValueError, IndexError):
+        pass  # the bench line stands without this figure
     for n in (1024, 2048):
         A, B = synth.uniform(n, seed, 0), synth.uniform(n, seed, 1)
         t = timed(lambda: oracle.strassen(A, B, 3))
