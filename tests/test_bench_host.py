@@ -95,3 +95,16 @@ def test_reference_arm_under_torchrun_prints_once_on_all_cores():
     assert len(outs) == 1 and outs[0]["n_gpus"] == 2  # rank 0 alone
     # the launcher's one thread per rank does not bind the one rank that works
     assert outs[0]["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+
+
+def test_error_record_normwise_rms_and_componentwise():
+    import numpy as np
+    want = np.array([[1.0, -2.0], [0.0, 4.0]])
+    got = np.array([[1.5, -2.0], [0.0, 4.0]], np.float32)
+    abs_prod = np.array([[4.0, 8.0], [0.0, 5.0]])  # a zero row of |A||B|: C is exactly zero there
+    e = bench.error_vs_fp64(got, want, abs_prod, 2.0, 3.0)
+    assert e["max_abs_over_normA_normB"] == 0.5 / 6.0
+    assert abs(e["rel_rms"] - np.sqrt(0.25 / 4) / np.sqrt(21.0 / 4)) < 1e-15
+    assert e["componentwise_max"] == 0.5 / 4.0
+    exact = bench.error_vs_fp64(want, want, abs_prod, 2.0, 3.0)
+    assert exact["max_abs_over_normA_normB"] == 0.0 and exact["componentwise_max"] == 0.0
