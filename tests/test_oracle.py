@@ -172,6 +172,19 @@ def test_strassen_int_equals_classical(n, depths):
         assert np.array_equal(oracle.strassen(A, B, d), C), d
 
 
+def test_strassen_int_equals_classical_every_size_to_256():
+    """Every n <= 256 at every depth the GPU path supports (0..4, while 2^d
+    does not exceed the padded side); for n <= 32 also every deeper depth,
+    down to 1 x 1 leaves.  Exact integers leave one correct answer."""
+    for n in range(1, 257):
+        A = synth.integers(n, 900 + n, 0, -16, 16)
+        B = synth.integers(n, 900 + n, 1, -16, 16)
+        C = oracle.gemm_classical(A, B)
+        top = max(1, math.ceil(math.log2(max(n, 2))))
+        for d in range(0, (top if n <= 32 else min(4, top)) + 1):
+            assert np.array_equal(oracle.strassen(A, B, d), C), (n, d)
+
+
 def test_strassen_int_depth0_is_classical():
     A = synth.integers(10, 1, 0, -5, 5)
     B = synth.integers(10, 1, 1, -5, 5)
