@@ -1,5 +1,6 @@
 """The C-ABI library: loads without a GPU, exports every declared entry
-point, and its quadrant-index table (the block tags of Sec. III-B) encodes
+point, its header is plain C that a C program links against, and its
+quadrant-index table (the block tags of Sec. III-B) encodes
 Strassen's identity at every depth.  No kernel runs here."""
 import itertools
 import os
@@ -91,3 +92,26 @@ def test_table_level1_is_alg1(stark_lib):
 def test_table_rejects_bad_depth(stark_lib):
     with pytest.raises(stark_lib.StarkError):
         stark_lib.quadrant_table(5, 0)
+
+
+def test_header_is_plain_c_and_links(stark_lib, tmp_path):
+    """include/stark.h compiles as pedantic C99 and a C program links
+    libstark.so and calls its host-only entry points."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    lib = stark_lib.library_path()
+    exe = str(tmp_path / "abi_client")
+    subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_client.c"), "-o", exe, lib,
+                    "-Wl,-rpath," + os.path.dirname(lib)], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split(maxsplit=12)
+    # C targets per product at depth 1: M1 -> C11, C22; M2 -> C21, C22; M3 -> C12, C22;
+    # M4 -> C11, C21; M5 -> C11, C12; M6 -> C22; M7 -> C11
+    assert out[0] == "0" and [int(v) for v in out[1:8]] == [2, 2, 2, 2, 2, 1, 1]
+    status, depth, levels, nbytes = (int(v) for v in out[8:12])
+    assert status == 0 and levels == 0 and 0 <= depth <= 4
+    g = (1 << depth) * 64
+    npad = -(-1024 // g) * g
+    assert nbytes == 2 * 7 ** depth * (npad >> depth) ** 2 * 8 + (1 << 20)
+    assert out[12].strip() == stark_lib.strerror(stark_lib.Status.ENOMEM)
