@@ -449,7 +449,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tf32", action="store_true")
     ap.add_argument("--pairing", type=int, default=-1,
-                    help="leaf schedule: 0 single CTAs, 1 multicast pairs, 2 cta_group::2 pairs")
+                    help="leaf schedule: 0 single CTAs, 2 cta_group::2 pairs")
     ap.add_argument("--combine", type=int, default=0)
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")

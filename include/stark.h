@@ -117,7 +117,11 @@ STARK_API stark_status stark_plan_destroy(stark_plan_t plan);
 
 STARK_API stark_status stark_plan_get_info(stark_plan_t plan, stark_plan_info *info);
 
-/* C = A * B.  A, B, C: device pointers to n x n matrices of the plan's
+/* C = A * B: Strassen's recursion (Alg. 1, Sec. III-A) run as Stark runs it,
+ * every level at once (Alg. 2, Sec. III-C): the divide (Alg. 3) forms every
+ * leaf operand sum, the leaf products (Alg. 4) multiply them, and the
+ * combine (Alg. 5) adds each product into C with its signs.
+ * A, B, C: device pointers to n x n matrices of the plan's
  * element type (double, float, float, int64_t).  C is overwritten; it may not
  * alias A or B.  Enqueues: zero C, divide A, divide B, one leaf-product launch
  * whose epilogue accumulates every leaf into C with the combine signs.
@@ -201,14 +205,13 @@ STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 /* Leaf launch schedule of the split-fp32 paths (Alg. 4 leaf products), for leaf
  * sides that allow it (256-wide tiles, L a multiple of 256):
  *   0  single CTAs, each a 128 x 256 tile;
- *   1  CTA pairs (thread-block clusters of 2) on vertically adjacent tiles
- *      that share one B tile, fetched once and multicast to both (3xBF16
- *      only);
  *   2  CTA pairs sharing one 256 x 256 tensor-core MMA (cta_group::2): each
  *      CTA stages half of the A rows and half of the B columns (3xBF16 and
  *      3xTF32; the default).
- * Other leaf sides run mode 0.  Results agree within fp32 rounding of the
- * combine's order.  Errors: EINVAL (null plan, mode outside 0..2). */
+ * Other leaf sides run mode 0.  Mode 1 (tiles shared between the CTAs of a
+ * cluster by multicast loads) is not offered.  Results agree within fp32
+ * rounding of the combine's order.  Errors: EINVAL (null plan, mode outside
+ * 0..2), EUNSUPPORTED (mode 1; the plan keeps its schedule). */
 STARK_API stark_status stark_plan_set_pairing(stark_plan_t plan, int enable);
 
 /* Order of a leaf's output tiles in the split-fp32 leaf launch: band > 0

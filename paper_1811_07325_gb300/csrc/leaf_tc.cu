@@ -16,8 +16,9 @@
 //
 // This is the single-CTA form: leaf sides that are not a multiple of 256,
 // the 128-wide grouped launches of batches and the server, the exact int64
-// leaves, and the opt-in schedules (multicast pairs, 64-byte rows).  Leaf
-// sides that are multiples of 256 run on CTA pairs (leaf_tc2.cu).
+// leaves, and the opt-in schedules (single CTAs on 256-wide tiles, 64-byte
+// rows).  Leaf sides that are multiples of 256 run on CTA pairs
+// (leaf_tc2.cu).
 //
 // Persistent kernel, one CTA per SM, warp-specialised:
 //   warp 0      TMA producer: per k-block, 4 tiles (X_hi, X_lo, Y_hi, Y_lo)
@@ -67,12 +68,12 @@ struct TcCfg {
   static constexpr uint32_t IDESC = make_idesc<kBM, BN, TF32, B_MN>();
 };
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR, int RB, bool INT1, bool TMN>
+template <int BN, int STAGES, bool TF32, bool GROUPED, int RB, bool INT1, bool TMN>
 __global__ void __launch_bounds__(kThreads, 1)
     leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
   using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1, TMN>;
-  static_assert(!INT1 || (!TF32 && !GROUPED && !PAIR), "integer mode: bf16, single problem");
+  static_assert(!INT1 || (!TF32 && !GROUPED), "integer mode: bf16, single problem");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -90,17 +91,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
 
-  // PAIR: clusters of two CTAs; each B tile is fetched once, multicast to both
-  const uint32_t cta_rank = PAIR ? cluster_ctarank() : 0u;
-  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-  const int num_items = GROUPED ? p.total_items
-                                : (p.leaf_end - p.leaf_begin) * (p.L / kBM / (PAIR ? 2 : 1)) * (p.L / BN);
+  const uint32_t cta_rank = 0u;
+  const int unit = (int)blockIdx.x;
+  const int units = (int)gridDim.x;
+  const int num_items = GROUPED ? p.total_items : (p.leaf_end - p.leaf_begin) * (p.L / kBM) * (p.L / BN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), PAIR ? 2 : 1);  // PAIR: both CTAs' MMAs must be done with it
+      mbar_init(empty_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(accf_bar(a), 1);
@@ -113,7 +112,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (p.use_tma_c) prefetch_tmap(&tmC);
     }
   }
-  if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before any multicast lands
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
     tmem_relinquish();
@@ -135,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t armed = 0, armed_phase = 0;  // per-stage: ever armed / parity of last arming
       bool ok = true;
       for (int item = unit; ok && item < num_items; item += units) {
-        const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
+        const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, false>(item, p, &tmA, &tmB, &tmC, cta_rank);
         // plane of this leaf in the workspace (depth-first traversal keeps
         // one subtree's leaves, numbered from plane_base)
         const int leaf = GROUPED ? it.leaf : it.leaf - p.plane_base;
@@ -150,16 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = kb * Cfg::BK;
           tma_load_3d(st, it.tA, k0, m0, leaf, full_bar(s), pol_a);
           if constexpr (!INT1) tma_load_3d(st + Cfg::A_BYTES, it.tA, k0, m0, it.P + leaf, full_bar(s), pol_a);
-          if constexpr (PAIR) {
-            // this CTA fetches its half of the B chunks for both CTAs
-#pragma unroll
-            for (int c = (int)cta_rank * (Cfg::NCHUNK / 2); c < ((int)cta_rank + 1) * (Cfg::NCHUNK / 2); ++c) {
-              tma_load_3d_mc(st + Cfg::NHALF * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf,
-                             full_bar(s), 0x3, pol_b);
-              tma_load_3d_mc(st + Cfg::NHALF * Cfg::A_BYTES + Cfg::B_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0,
-                             it.P + leaf, full_bar(s), 0x3, pol_b);
-            }
-          } else if constexpr (Cfg::B_MN) {
+          if constexpr (Cfg::B_MN) {
 #pragma unroll
             for (int c = 0; c < Cfg::NCHUNK; ++c) {
               tma_load_3d(st + Cfg::NHALF * Cfg::A_BYTES + c * Cfg::CH_BYTES, it.tB, n0 + c * Cfg::W, k0, leaf, full_bar(s),
@@ -184,15 +173,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let every copy already issued land before the CTA can exit
         for (int t = 0; t < STAGES; ++t)
           if (armed & (1u << t)) mbar_wait_bounded(full_bar(t), (armed_phase >> t) & 1, nullptr, 0, 200000000ull);
-      } else if constexpr (PAIR) {
-        // every arrival the peer owes our empty barriers has landed before exit
-        for (int t = 0; t < STAGES; ++t) {
-          if (!mbar_wait_bounded(empty_bar(s), phase ^ 1, p.err, kDevTimeoutEmpty, p.timeout_ns)) break;
-          if (++s == STAGES) {
-            s = 0;
-            phase ^= 1;
-          }
-        }
       }
     }
   } else if (warp == 1) {
@@ -205,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       bool issued = false;
       for (int item = unit; ok && item < num_items; item += units) {
-        const int kblocks = GROUPED ? decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank).kblocks
+        const int kblocks = GROUPED ? decode_item<BN, Cfg::BK, GROUPED, false>(item, p, &tmA, &tmB, &tmC, cta_rank).kblocks
                                     : p.L / Cfg::BK;
         if (!mbar_wait_bounded(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
           ok = false;
@@ -248,10 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           issued = true;
-          if constexpr (PAIR)
-            mma_commit_mc(empty_bar(s), 0x3);  // both CTAs' producers learn the stage is read here
-          else
-            mma_commit(empty_bar(s));  // stage free once these MMAs have read it
+          mma_commit(empty_bar(s));  // stage free once these MMAs have read it
           if (++s == STAGES) {
             s = 0;
             phase ^= 1;
@@ -283,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int item = unit; item < num_items; item += units) {
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
-      const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, PAIR>(item, p, &tmA, &tmB, &tmC, cta_rank);
+      const ItemInfo it = decode_item<BN, Cfg::BK, GROUPED, false>(item, p, &tmA, &tmB, &tmC, cta_rank);
       epilogue_item<BN, INT1>(it, p, tmem_base, (uint32_t)(acc * BN), quarter, lane, ebuf, pol_c);
       tc_fence_before();
       mbar_arrive(acce_bar(acc));
@@ -301,55 +278,42 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
-  if constexpr (PAIR) cluster_sync();  // no CTA leaves while its peer may still write to it
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR = false, int RB = 128, bool INT1 = false,
-          bool TMN = false>
+template <int BN, int STAGES, bool TF32, bool GROUPED, int RB = 128, bool INT1 = false, bool TMN = false>
 cudaError_t launch_cfg(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                        int num_sms, cudaStream_t st) {
   using Cfg = TcCfg<BN, STAGES, TF32, RB, INT1, TMN>;
   static_assert(Cfg::B_BYTES == BN * RB, "B tile size");
-  static_assert(!PAIR || (!GROUPED && Cfg::B_MN && Cfg::NCHUNK % 2 == 0), "paired mode: bf16, single problem");
   int64_t items;
   if constexpr (GROUPED) {
     items = a.total_items;
     if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
   } else {
     if (a.L % kBM != 0 || a.L % BN != 0 || a.L % Cfg::BK != 0) return cudaErrorInvalidValue;
-    if (PAIR && (a.L / kBM) % 2 != 0) return cudaErrorInvalidValue;
-    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM / (PAIR ? 2 : 1)) * (a.L / BN);
+    items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / kBM) * (a.L / BN);
   }
-  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, PAIR, RB, INT1, TMN>;
+  auto kern = leaf_tc_kernel<BN, STAGES, TF32, GROUPED, RB, INT1, TMN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  if constexpr (PAIR) {
-    return launch_cta_pairs(kern, kThreads, Cfg::SMEM, items, num_sms, st, *tmA, *tmB, *tmC, a);
-  } else {
-    const int grid = (int)(items < num_sms ? items : num_sms);
-    kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, *tmC, a);
-    count_launch();
-    return cudaGetLastError();
-  }
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  kern<<<grid, kThreads, Cfg::SMEM, st>>>(*tmA, *tmB, *tmC, a);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_leaf_tc(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                            const CUtensorMap* tmC, bool tf32, int bn, int num_sms, cudaStream_t st) {
-  // bf16 with 256-wide tiles and an even number of tile rows: paired CTAs
-  // sharing each B tile through TMA multicast (pair == 1; the cta_group::2
-  // pairs of pair == 2 are launched by launch_leaf_tc2)
-  if (bn == 256 && !tf32 && a.pair == 1 && (a.L / kBM) % 2 == 0)
-    return launch_cfg<256, 2, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
   // bf16, 256-wide tiles, 64-byte rows: four 48 KB stages instead of two 96 KB
   if (bn == 256 && !tf32 && a.row_bytes == 64)
-    return launch_cfg<256, 4, false, false, false, 64>(a, tmA, tmB, tmC, num_sms, st);
+    return launch_cfg<256, 4, false, false, 64>(a, tmA, tmB, tmC, num_sms, st);
   if (tf32 && a.b_mn) {
-    if (bn == 256) return launch_cfg<256, 2, true, false, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
-    if (bn == 128) return launch_cfg<128, 3, true, false, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
+    if (bn == 256) return launch_cfg<256, 2, true, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
+    if (bn == 128) return launch_cfg<128, 3, true, false, 128, false, true>(a, tmA, tmB, tmC, num_sms, st);
     return cudaErrorInvalidValue;
   }
   if (bn == 256) {
@@ -367,8 +331,8 @@ cudaError_t launch_leaf_tc_int(const LeafTcArgs& a, const CUtensorMap* tmA, cons
                                int num_sms, cudaStream_t st) {
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  if (bn == 256) return launch_cfg<256, 4, false, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
-  if (bn == 128) return launch_cfg<128, 6, false, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
+  if (bn == 256) return launch_cfg<256, 4, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
+  if (bn == 128) return launch_cfg<128, 6, false, false, 128, true>(a, tmA, tmB, &none, num_sms, st);
   return cudaErrorInvalidValue;
 }
 
@@ -377,7 +341,7 @@ cudaError_t launch_leaf_tc_grouped(const LeafTcArgs& a, bool tf32, int bn, int n
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
   if (bn == 128) {
-    if (tf32 && a.b_mn) return launch_cfg<128, 3, true, true, false, 128, false, true>(a, &none, &none, &none, num_sms, st);
+    if (tf32 && a.b_mn) return launch_cfg<128, 3, true, true, 128, false, true>(a, &none, &none, &none, num_sms, st);
     return tf32 ? launch_cfg<128, 3, true, true>(a, &none, &none, &none, num_sms, st)
                 : launch_cfg<128, 3, false, true>(a, &none, &none, &none, num_sms, st);
   }

@@ -539,6 +539,7 @@ stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
 
 stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
   if (!p || enable < 0 || enable > 2) return STARK_EINVAL;
+  if (enable == 1) return STARK_EUNSUPPORTED;  // no schedule shares tiles between CTAs by multicast
   p->pair_mode = enable;
   return STARK_OK;
 }
@@ -827,7 +828,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       a.use_tma_c = 0;
       tmC = p->tmM;
     }
-    a.pair = (deterministic && p->pair_mode == 1) ? 0 : p->pair_mode;
+    a.pair = p->pair_mode;
     a.band = p->raster_band;
     a.b_mn = p->tf32_mn;
     a.row_bytes = 128;

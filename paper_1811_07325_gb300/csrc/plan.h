@@ -56,7 +56,7 @@ struct stark_plan_s {
   void* m_planes = nullptr;  // [P][L][L] fp32 leaf products (combine mode 2)
   CUtensorMap tmM;
   int pair_mode = 2;     // leaf schedule where the tiling allows (L % 256 == 0): 2 CTA pairs on one
-                         // cta_group::2 MMA, 1 paired CTAs with multicast B tiles, 0 single CTAs
+                         // cta_group::2 MMA, 0 single CTAs
   CUtensorMap tmBp;      // tf32 Y map with 128-row boxes for the pair MMA
   int tf32_mn = 1;       // tf32 Y planes row-major, read MN-major (0: transposed, K-major)
   bool has_mapbp = false;

@@ -156,18 +156,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* m, 
       : "memory");
 }
 
-// The same load multicast to every CTA of the cluster named in cta_mask: the
-// data lands at the same shared-memory offset in each of them and each one's
-// mbarrier at `bar`'s offset receives the byte count.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* m, int32_t c0, int32_t c1,
-                                               int32_t c2, uint32_t bar, uint16_t cta_mask, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6, %7;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(cta_mask), "l"(policy)
-      : "memory");
-}
-
 // The load of a CTA pair that feeds one cta_group::2 MMA: the data lands in
 // this CTA's shared memory, the byte count goes to the mbarrier at
 // `cluster_bar` (a shared::cluster address, here the even CTA's barrier).
@@ -341,15 +329,6 @@ __device__ __forceinline__ void mma2_commit_mc(uint32_t bar, uint16_t cta_mask) 
 // thread has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-// Arrive on the mbarrier at `bar`'s offset in every CTA of cta_mask once the
-// previously issued MMAs of this thread have completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t cta_mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   bar),
-               "h"(cta_mask)
                : "memory");
 }
 

@@ -135,7 +135,7 @@ struct LeafTcArgs {
   int* err;
   uint64_t timeout_ns;
   int32_t use_tma_c;   // 1: combine by TMA bulk add-reductions through tmC
-  int32_t pair;        // 1: paired CTAs share B tiles by multicast; 2: cta_group::2 pair MMA
+  int32_t pair;        // 2: cta_group::2 pair MMA where the tiling allows; 0: single CTAs
   int32_t row_bytes;   // swizzled smem row of the operand tiles: 128 or 64 (tensor maps must match)
   int32_t store_m;     // 1: store each leaf tile to the M planes (tmC = their map) instead of combining
   int32_t plane_base;  // leaf stored in workspace plane 0 (depth-first traversal); P = planes per half

@@ -273,9 +273,9 @@ class Plan:
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
 
     def set_pairing(self, mode):
-        """Leaf schedule of the split-fp32 paths: 0 single CTAs; 1 (or True)
-        CTA pairs sharing B tiles by multicast (3xBF16); 2 (default) CTA pairs
-        on one cta_group::2 MMA of 256 x 256."""
+        """Leaf schedule of the split-fp32 paths: 0 single CTAs; 2 (default)
+        CTA pairs on one cta_group::2 MMA of 256 x 256 (mode 1 is refused
+        with EUNSUPPORTED)."""
         _check(_lib.stark_plan_set_pairing(self._h, int(mode)), "stark_plan_set_pairing")
 
     def set_tf32_layout(self, mn: bool):

@@ -326,16 +326,15 @@ def test_deterministic_combine_is_bitwise_reproducible(S, n, d, dtype):
 
 @pytest.mark.parametrize("n,d", [(2048, 1), (4096, 2), (1536, 0)])
 def test_leaf_schedules_agree(S, n, d):
-    # clusters of two CTAs sharing B tiles by multicast, one CTA per tile, the
-    # four-stage 64-byte-row pipeline and CTA pairs on one cta_group::2 MMA:
-    # same products
+    # one CTA per tile, the four-stage 64-byte-row pipeline and CTA pairs on
+    # one cta_group::2 MMA (row-major and banded rasters): same products
     A = synth.normal(n, 62, 0)
     B = synth.normal(n, 62, 1)
     rows = synth.sample_rows(n, 64, 62)
     want = oracle.gemm_rows(A, B, rows)
     an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
     out = []
-    for pair, deep, band in ((1, False, 0), (0, False, 0), (0, True, 0), (2, False, 0), (2, False, 2), (0, False, 2)):
+    for pair, deep, band in ((0, False, 0), (0, True, 0), (2, False, 0), (2, False, 2), (0, False, 2)):
         with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
             p.set_pairing(pair)
             p.set_pipeline(deep)
@@ -348,10 +347,25 @@ def test_leaf_schedules_agree(S, n, d):
             assert np.abs(diff).max() / (an * bn) <= 1e-6
             rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
             assert rel <= SPLIT_BOUND["F32_SPLIT_BF16"] + 3 * (p.leaf / 16) * 2.0 ** -24
-    assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
-    assert np.abs(out[2] - out[1]).max() <= 1e-5 * np.abs(want).max()
-    for k in (3, 4, 5):
-        assert np.abs(out[k] - out[1]).max() <= 1e-5 * np.abs(want).max()
+    for k in (1, 2, 3, 4):
+        assert np.abs(out[k] - out[0]).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_multicast_pairing_is_refused(S):
+    # no leaf schedule shares tiles between the CTAs of a cluster by
+    # multicast loads: mode 1 is refused and the plan keeps its schedule
+    n = 512
+    A = synth.normal(n, 63, 0)
+    B = synth.normal(n, 63, 1)
+    with S.Plan(n, 1, S.DType.F32_SPLIT_BF16) as p:
+        with pytest.raises(S.StarkError) as e:
+            p.set_pairing(1)
+        assert e.value.status == S.Status.EUNSUPPORTED
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        p.check()
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    assert np.abs(C - want).max() / (an * bn) <= 1e-6
 
 
 @pytest.mark.parametrize("dtype,n,d,combine,dfs", [

@@ -31,7 +31,7 @@ def draw(rng):
     opts = {
         "peel": rng.random() < 0.3,
         "combine": rng.choice([0, 0, 1, 2]) if dtype.startswith("F32") else 0,
-        "pairing": rng.choice([0, 1, 2, 2]) if dtype.startswith("F32") else 2,
+        "pairing": rng.choice([0, 0, 2, 2]) if dtype.startswith("F32") else 2,
         "raster": rng.choice([0, 0, 2, 4]),
         "dfs": rng.random() < 0.3 and d >= 1,
         "tf32_mn": rng.random() < 0.7,
