@@ -414,16 +414,56 @@ STARK_API stark_status stark_server_destroy(stark_server_t server);
  * (e.g. n <= 2048 fits at depth 0 or 1, n <= 1024 at depth 2).
  * A, B, C: device pointers to n x n row-major fp32 matrices; C is
  * overwritten.  depth: 0..3 (no automatic choice).  Asynchronous on
- * `stream`; nothing is allocated, and no device-side timeout is reported
- * (the error word lives in the shared scratch).
+ * `stream`; nothing is allocated.  Each call rebuilds its C-target table in
+ * the array with a kernel on `stream`, so no enqueued work reads host memory.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and must come before any stream capture.  Every
  * call reuses the same array: calls that overlap on the GPU (other streams
- * or threads) race and must be ordered by the caller.
+ * or threads) race and must be ordered by the caller.  A bounded device
+ * wait that gave up is kept in the array's error word until
+ * stark_noalloc_check reports it (later calls may then stop early too).
  * Errors: EINVAL (bad n or depth, null pointer), ENOMEM (over the scratch
  * size), EUNSUPPORTED (not a GB300), ECUDA. */
 STARK_API stark_status stark_mul_noalloc(int64_t n, int depth, const void *A, const void *B, void *C,
                                          void *stream);
+
+/* Synchronise `stream`, then report and clear a device-side timeout recorded
+ * by stark_mul_noalloc calls on the current device since the last check
+ * (STARK_ETIMEOUT: the products of those calls are invalid).  Allocates
+ * nothing.  Errors: ECUDA. */
+STARK_API stark_status stark_noalloc_check(void *stream);
+
+/* ----------------------------------------------------------------- accuracy */
+
+/* FP64 error statistics of a product, reduced on the device. */
+typedef struct {
+  double norm_a, norm_b;    /* ||A||_F, ||B||_F (sums of squares in fp64)                */
+  double max_abs_err;       /* max |C_ij - ref_ij| over the compared entries              */
+  double sum_sq_err;        /* sum (C_ij - ref_ij)^2                                       */
+  double sum_sq_ref;        /* sum ref_ij^2 (relative RMS = sqrt(sum_sq_err / sum_sq_ref)) */
+  double max_componentwise; /* max |C_ij - ref_ij| / absprod_ij over absprod_ij > 0        */
+  int64_t compared;         /* entries compared: nrows * n                                 */
+} stark_error_report;
+
+/* The accuracy statement of a product on the device in FP64.  The paper runs
+ * its products in FP64 and states no error (Sec. V); the split-precision
+ * leaves are judged by the normwise ratio max|dC| / (||A||_F ||B||_F) and the
+ * relative RMS error against FP64 reference rows, which this call reduces:
+ * the Frobenius norms of A and B over all n^2 entries, and over `nrows`
+ * sampled rows of C (row rows[r] of C against row r of `want`) the largest
+ * absolute error, the sums of squares of the error and of the reference,
+ * and, when `absprod` is not NULL, the largest componentwise ratio
+ * |dC_ij| / (|A||B|)_ij.  Deterministic: fixed-order two-pass reductions.
+ * A, B, C: device pointers to n x n row-major matrices of `dtype`'s element
+ * type (fp32 for the split dtypes, fp64, int64 converted to fp64); rows:
+ * device array of nrows row indices in [0, n); want, absprod: device arrays
+ * of nrows x n fp64 (row-major).  nrows = 0 reduces the norms only (C, rows,
+ * want may be NULL).  Synchronous on `stream`; allocates a few KB of device
+ * memory per call.  Errors: EINVAL (bad sizes, NULL where data is needed),
+ * ENOMEM, ECUDA. */
+STARK_API stark_status stark_error_norms(int64_t n, stark_dtype dtype, const void *A, const void *B, const void *C,
+                                         const int64_t *rows, int64_t nrows, const double *want,
+                                         const double *absprod, stark_error_report *out, void *stream);
 
 /* ----------------------------------------------------------------- tables */
 

@@ -185,6 +185,11 @@ struct Loader {
         const Tin* t = reinterpret_cast<const Tin*>(&raw);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)t[e];
+      } else if constexpr (sizeof(Tin) * VEC == 8) {
+        const int2 raw = __ldcs(reinterpret_cast<const int2*>(p));
+        const Tin* t = reinterpret_cast<const Tin*>(&raw);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)t[e];
       } else {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)__ldcs(p + e);

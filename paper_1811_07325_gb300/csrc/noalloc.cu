@@ -3,10 +3,10 @@
 // runs where a memory allocator must not be entered, or a host that hands
 // this library a fixed device-memory budget it may not grow).
 //
-// The workspace (leaf operand planes, the C-target table, the error word)
-// lives in one file-scope __device__ array of fixed size, kNoallocScratch
-// bytes.  Every device that loads this file's module holds that array until
-// the process exits (with CUDA's lazy module loading the module, and so the
+// The workspace (error word, C-target table, leaf operand planes) lives in
+// one file-scope __device__ array of fixed size, kNoallocScratch bytes.
+// Every device that loads this file's module holds that array until the
+// process exits (with CUDA's lazy module loading the module, and so the
 // array, is loaded by the first call of this entry point on the device).
 //
 // In host code `g_scratch` names a host-side stand-in, not device memory: a
@@ -15,13 +15,15 @@
 // that device current) asks the runtime for the array's device address with
 // cudaGetSymbolAddress, checks the result and caches it per device; every
 // kernel receives that address.  Do that first call before any stream
-// capture.  All calls share the one array and it keeps the contents of the
-// last call: the error word is cleared on every call, and calls that overlap
-// on the GPU (different streams, or different host threads) race on the
-// array, so callers must order them.
+// capture.  Each call rebuilds the C-target table in the array with a small
+// kernel on the caller's stream (no host-to-device copy), so nothing a call
+// enqueues refers to host memory.  All calls share the one array and it
+// keeps the contents of the last call; calls that overlap on the GPU
+// (different streams, or different host threads) race on the array, so
+// callers must order them.  The error word at the start of the array keeps a
+// device-side timeout until stark_noalloc_check reads and clears it.
 #include <cuda_runtime.h>
 
-#include <cstring>
 #include <mutex>
 
 #include "plan.h"
@@ -54,42 +56,59 @@ cudaError_t scratch_address(int dev, void** out) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// C targets of every leaf (Alg. 5 with the C22 = M1 - M2 + M3 + M6 sign),
-// written into fixed host arrays (no heap use on this path).
-void c_targets(int depth, int64_t npad, CTarget* tab, int32_t* count) {
+// Offsets of the quadrant path q (base 4, top level most significant) in a
+// padded side npad: each level halves the block (device form of the plan's
+// quadrant_offsets).
+__device__ void quadrant_offset(int depth, int64_t npad, int q, int64_t* row, int64_t* col) {
+  int64_t r = 0, c = 0;
+  for (int k = 1; k <= depth; ++k) {
+    const int digit = (q >> (2 * (depth - k))) & 3;
+    r += (int64_t)(digit >> 1) * (npad >> k);
+    c += (int64_t)(digit & 1) * (npad >> k);
+  }
+  *row = r;
+  *col = c;
+}
+
+// C targets of every leaf (Alg. 5 with the C22 = M1 - M2 + M3 + M6 sign):
+// one thread per leaf l (base-7 M-index path, top level most significant)
+// expands the product over levels of the C coefficients of its digits.
+__global__ void noalloc_table_kernel(int depth, int64_t npad, CTarget* tab, int32_t* count) {
   int64_t P = 1;
   for (int k = 0; k < depth; ++k) P *= 7;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= P) return;
   const int maxT = 1 << depth;
-  for (int64_t l = 0; l < P; ++l) {
-    int dig[kNoallocMaxDepth + 1] = {0};
-    int64_t x = l;
-    for (int k = depth - 1; k >= 0; --k) {
-      dig[k] = (int)(x % 7);
-      x /= 7;
-    }
-    int q[16] = {0}, s[16] = {1};
-    int cnt = 1;
-    for (int k = 0; k < depth; ++k) {
-      int q2[16], s2[16], c2 = 0;
-      for (int e = 0; e < cnt; ++e)
-        for (int cq = 0; cq < 4; ++cq) {
-          const int c = coef_c(dig[k], cq);
-          if (c != 0) {
-            q2[c2] = q[e] * 4 + cq;
-            s2[c2] = s[e] * c;
-            ++c2;
-          }
+  int dig[kNoallocMaxDepth + 1] = {0};
+  int64_t x = l;
+  for (int k = depth - 1; k >= 0; --k) {
+    dig[k] = (int)(x % 7);
+    x /= 7;
+  }
+  int q[8] = {0}, sg[8] = {1};
+  int cnt = 1;
+  for (int k = 0; k < depth; ++k) {
+    int q2[8], s2[8], c2 = 0;
+    for (int e = 0; e < cnt; ++e)
+      for (int cq = 0; cq < 4; ++cq) {
+        const int c = coef_c(dig[k], cq);
+        if (c != 0 && c2 < 8) {
+          q2[c2] = q[e] * 4 + cq;
+          s2[c2] = sg[e] * c;
+          ++c2;
         }
-      cnt = c2;
-      std::memcpy(q, q2, sizeof(int) * (size_t)c2);
-      std::memcpy(s, s2, sizeof(int) * (size_t)c2);
+      }
+    cnt = c2;
+    for (int e = 0; e < c2; ++e) {
+      q[e] = q2[e];
+      sg[e] = s2[e];
     }
-    count[l] = cnt;
-    for (int t = 0; t < cnt; ++t) {
-      int64_t r = 0, c = 0;
-      quadrant_offsets(depth, npad, q[t], &r, &c);
-      tab[l * maxT + t] = CTarget{(int32_t)r, (int32_t)c, (int32_t)s[t], 0};
-    }
+  }
+  count[l] = cnt;
+  for (int t = 0; t < cnt; ++t) {
+    int64_t r = 0, c = 0;
+    quadrant_offset(depth, npad, q[t], &r, &c);
+    tab[l * maxT + t] = CTarget{(int32_t)r, (int32_t)c, (int32_t)sg[t], 0};
   }
 }
 
@@ -106,14 +125,14 @@ extern "C" stark_status stark_mul_noalloc(int64_t n, int depth, const void* A, c
   if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
   const stark_dtype dt = STARK_F32_SPLIT_BF16;
 
-  // scratch layout: X planes | Y planes | C-target table | counts | error word
+  // scratch layout: error word | C-target table | counts | X planes | Y planes
   const int64_t ws = operand_bytes(n, depth, dt);
   const int64_t P = pow7i(depth);
   const int maxT = 1 << depth;
-  const size_t off_tab = align_up((size_t)ws, 256);
+  const size_t off_tab = 256;
   const size_t off_cnt = align_up(off_tab + (size_t)(P * maxT) * sizeof(CTarget), 256);
-  const size_t off_err = align_up(off_cnt + (size_t)P * sizeof(int32_t), 256);
-  if (off_err + 256 > kNoallocScratch) return STARK_ENOMEM;  // over the fixed scratch size
+  const size_t off_x = align_up(off_cnt + (size_t)P * sizeof(int32_t), 4096);
+  if (off_x + (size_t)ws > kNoallocScratch) return STARK_ENOMEM;  // over the fixed scratch size
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return STARK_ECUDA;
@@ -139,27 +158,36 @@ extern "C" stark_status stark_mul_noalloc(int64_t n, int depth, const void* A, c
   p.bn = (p.L % 256 == 0) ? 256 : 128;
   p.device = dev;
   p.num_sms = device_sm_count();
-  p.X = sb;
-  p.Y = sb + ws / 2;
+  p.X = sb + off_x;
+  p.Y = sb + off_x + ws / 2;
   p.ws_bytes = 0;
   p.d_ctab = reinterpret_cast<CTarget*>(sb + off_tab);
   p.d_ccount = reinterpret_cast<int32_t*>(sb + off_cnt);
-  p.d_err = reinterpret_cast<int*>(sb + off_err);
+  p.d_err = reinterpret_cast<int*>(sb);
   p.maxT = maxT;
 
-  // the table of this (n_pad, depth), and a cleared error word
-  CTarget tab[343 * 8];
-  int32_t cnt[343];
-  c_targets(depth, p.npad, tab, cnt);
-  if (cudaMemcpyAsync(p.d_ctab, tab, (size_t)(P * maxT) * sizeof(CTarget), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(p.d_ccount, cnt, (size_t)P * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(p.d_err, 0, sizeof(int), s) != cudaSuccess) {
-    cudaGetLastError();
-    return STARK_ECUDA;
-  }
+  // the C-target table of this (n_pad, depth), built on the device
+  noalloc_table_kernel<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(depth, p.npad, p.d_ctab, p.d_ccount);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return STARK_ECUDA;
   if (!make_tmap_planes(&p.tmA, p.X, false, p.L, 2 * p.P, 128) ||
       !make_tmap_planes(&p.tmB, p.Y, false, p.L, 2 * p.P, 64))
     return STARK_EUNSUPPORTED;
   return plan_run(&p, A, B, C, 0, p.P, s);
+}
+
+extern "C" stark_status stark_noalloc_check(void* stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STARK_ECUDA;
+  int e = 0;
+  if (cudaMemcpyFromSymbol(&e, g_scratch, sizeof(int), 0, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ECUDA;
+  }
+  if (e == 0) return STARK_OK;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_scratch, &zero, sizeof(int), 0, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return STARK_ECUDA;
+  }
+  return STARK_ETIMEOUT;
 }

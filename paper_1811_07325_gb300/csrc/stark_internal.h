@@ -76,6 +76,9 @@ struct DivideArgs {
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
+// Breadth-first depth 3 in one pass for fp32 input and 3xBF16 output (every
+// input element read once); other dtypes use launch_divide per top product.
+cudaError_t launch_divide3(const DivideArgs& a, int side, OutMode out, cudaStream_t s);
 // The same for a depth-first subtree (a.top >= 0); launch_divide forwards.
 cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in

@@ -52,6 +52,12 @@ class PlanInfo(ctypes.Structure):
                 ("peel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class ErrorReport(ctypes.Structure):
+    _fields_ = [("norm_a", ctypes.c_double), ("norm_b", ctypes.c_double), ("max_abs_err", ctypes.c_double),
+                ("sum_sq_err", ctypes.c_double), ("sum_sq_ref", ctypes.c_double),
+                ("max_componentwise", ctypes.c_double), ("compared", ctypes.c_int64)]
+
+
 _i64, _i32, _vp, _ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int
 _SIGS = {
     "stark_plan": ([_i64, _ci, _ci, ctypes.POINTER(_vp)], _ci),
@@ -95,6 +101,7 @@ _SIGS = {
     "stark_server_destroy": ([_vp], _ci),
     "stark_server_admission": ([ctypes.c_size_t, _i64, _ci, _ci, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                 ctypes.POINTER(_i64)], _ci),
+    "stark_error_norms": ([_i64, _ci, _vp, _vp, _vp, _vp, _i64, _vp, _vp, ctypes.POINTER(ErrorReport), _vp], _ci),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -455,6 +462,47 @@ def quadrant_table(depth: int, side: int):
     _check(_lib.stark_quadrant_table(int(depth), int(side), count.ctypes.data, quad.ctypes.data,
                                      sign.ctypes.data), "stark_quadrant_table")
     return count, quad, sign
+
+
+def error_norms(A, B, C=None, rows=None, want=None, absprod=None, stream=None) -> dict:
+    """FP64 error statistics on the device (``stark_error_norms``): the
+    Frobenius norms of A and B and, when rows are given, the error of rows
+    ``rows`` of C against ``want`` (nrows x n reference rows) and, with
+    ``absprod`` (the rows of |A||B|), the largest componentwise ratio.
+    A, B, C: square CUDA tensors of one dtype (float32, float64, int64);
+    rows / want / absprod: numpy arrays or tensors (copied to the device).
+    Returns the report as a dict with the derived normwise ratio and
+    relative RMS."""
+    import torch
+    dt = {torch.float32: DType.F32_SPLIT_BF16, torch.float64: DType.F64, torch.int64: DType.I64}[A.dtype]
+    n = A.shape[0]
+    for t, name in ((A, "A"), (B, "B")) + (((C, "C"),) if C is not None else ()):
+        if not t.is_cuda or t.dtype != A.dtype or tuple(t.shape) != (n, n) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {n}x{n} CUDA tensor of {A.dtype}")
+    keep = []
+
+    def dev(x, dtype):
+        if x is None:
+            return None, None
+        t = torch.as_tensor(np.ascontiguousarray(x) if isinstance(x, np.ndarray) else x, dtype=dtype,
+                            device=A.device).contiguous()
+        keep.append(t)
+        return t, ctypes.c_void_p(t.data_ptr())
+    r_t, r_p = dev(rows, torch.int64)
+    nrows = 0 if r_t is None else int(r_t.numel())
+    w_t, w_p = dev(want, torch.float64)
+    a_t, a_p = dev(absprod, torch.float64)
+    if nrows and (C is None or w_t is None or w_t.numel() != nrows * n or (a_t is not None and a_t.numel() != nrows * n)):
+        raise ValueError("C, rows and want (nrows x n) are needed together")
+    rep = ErrorReport()
+    _check(_lib.stark_error_norms(n, int(dt), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                  ctypes.c_void_p(C.data_ptr()) if C is not None else None, r_p, nrows, w_p, a_p,
+                                  ctypes.byref(rep), _stream_handle(stream)), "stark_error_norms")
+    out = {f: getattr(rep, f) for f, _ in ErrorReport._fields_}
+    if nrows:
+        out["max_abs_over_normA_normB"] = rep.max_abs_err / (rep.norm_a * rep.norm_b)
+        out["rel_rms"] = float(np.sqrt(rep.sum_sq_err / rep.sum_sq_ref)) if rep.sum_sq_ref > 0 else 0.0
+    return out
 
 
 def selftest_bounded_wait(timeout_ns: int = 20_000_000) -> Status:

@@ -1,8 +1,11 @@
 """stark_mul_noalloc: the 3xBF16 product for callers that cannot allocate
 device memory (code that may not enter an allocator, or that has a fixed
 device-memory budget).  Through the C ABI, it must match stark_mul within
-the tolerance the other split tests use, on two calls in a row, allocate
-nothing, and reject problems larger than its fixed scratch array.
+the tolerance the other split tests use, on two calls in a row, match the
+FP64 oracle within the split bounds (including a size whose C the combine
+reaches only by scalar atomics), allocate nothing, report device errors
+through stark_noalloc_check, and reject problems larger than its fixed
+scratch array.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -11,6 +14,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1811_07325_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -23,6 +27,9 @@ def lib(stark_lib):
     fn.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                    ctypes.c_void_p]
     fn.restype = ctypes.c_int
+    chk = stark_lib._lib.stark_noalloc_check
+    chk.argtypes = [ctypes.c_void_p]
+    chk.restype = ctypes.c_int
     return stark_lib, fn
 
 
@@ -77,3 +84,40 @@ def test_noalloc_rejects_oversize_and_bad_args(lib):
     assert run_noalloc(fn, n, 1, A, A, A) == S.Status.ENOMEM
     assert run_noalloc(fn, 64, 4, A, A, A) == S.Status.EINVAL
     assert fn(64, 1, None, None, None, None) == S.Status.EINVAL
+
+
+@pytest.mark.parametrize("n,d", [(1001, 1), (256, 0), (512, 3), (1000, 2)])
+def test_noalloc_matches_oracle(lib, n, d):
+    # every element against the FP64 oracle, with the bars of the other split
+    # tests: normwise max|dC| / (||A||_F ||B||_F) <= 1e-6 and the relative RMS
+    # bug signal 2^-12 + 3 (L / 16) 2^-24.  n = 1001 (not a multiple of 4):
+    # no staging copy of C exists here, so the combine adds by scalar atomics
+    S, fn = lib
+    A = synth.normal(n, 80 + n + d, 0)
+    B = synth.normal(n, 80 + n + d, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.full((n, n), float("nan"), device="cuda")
+    assert run_noalloc(fn, n, d, dA, dB, C) == 0
+    assert S._lib.stark_noalloc_check(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    got = C.cpu().numpy().astype(np.float64)
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    diff = got - want
+    assert np.isfinite(got).all()
+    assert np.abs(diff).max() / (an * bn) <= 1e-6
+    L = (-(-n // (128 << d)) * (128 << d)) >> d
+    rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+    assert rel <= 2.0 ** -12 + 3 * (L / 16) * 2.0 ** -24
+
+
+def test_noalloc_check_reports_nothing_after_good_calls(lib):
+    S, fn = lib
+    n, d = 384, 1
+    A = torch.from_numpy(synth.normal(n, 74, 0)).cuda()
+    B = torch.from_numpy(synth.normal(n, 74, 1)).cuda()
+    C = torch.empty((n, n), device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        assert run_noalloc(fn, n, d, A, B, C) == 0
+    assert S._lib.stark_noalloc_check(s) == 0
+    assert S._lib.stark_noalloc_check(s) == 0  # nothing left to report
