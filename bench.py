@@ -244,13 +244,14 @@ def link_bandwidth(torch, A_h, B_h, A, B, C, C_h, e2e_s):
 
 def run_depth_sweep(args, stark, synth, torch, A, B):
     """The bench product at depths 0 (one classical 3xBF16 product through
-    the same leaf kernel) to 3 with the default combine, and with the
-    deterministic combine at depths 2 and 3: ms per product, effective
-    TFLOP/s and the phases."""
+    the same leaf kernel) to 3 with the default combine, with the
+    deterministic combine at depths 2 and 3 and with the sibling-folded
+    combine at depths 1 to 3: ms per product, effective TFLOP/s and the
+    phases."""
     n = args.n
     C = torch.empty_like(A)
     out = {"n": n, "dtype": args.dtype}
-    runs = [(d, 0) for d in range(4)] + [(2, 2), (3, 2)]
+    runs = [(d, 0) for d in range(4)] + [(2, 2), (3, 2), (1, 3), (2, 3), (3, 3)]
     for d, combine in runs:
         key = f"d{d}" + ("" if combine == 0 else f"_combine{combine}")
         try:
@@ -392,61 +393,69 @@ def run_traversal(args, stark, synth, torch, A, B):
 
 
 def run_serve(args, stark, synth, torch):
-    """Served form: Poisson arrivals (200/s), n log-uniform in [256, 8192],
-    FP32 N(0,1), 3xBF16, device budget 150 GB; latency from submission to
-    observed completion.  A first pass over the same sizes warms the
-    workspace cache (not measured)."""
-    import threading as th
+    """Served form: Poisson arrivals at 200 req/s (the workload) and, as a
+    rate sweep toward capacity, at 2000 and 8000 req/s; n log-uniform in
+    [256, 8192], FP32 N(0,1), 3xBF16, device budget 150 GB, 4 stream slots.
+    Latency of a request runs from its scheduled arrival to the dispatcher's
+    observation of its completion: the host's delay from the scheduled time
+    to the return of the submit call plus the server's own submit-to-
+    completion time (an over-estimate by the length of the call).  Output
+    buffers are allocated before any clock starts; a first pass at 200 req/s
+    warms the workspace cache (not measured)."""
     count = args.serve_requests
     sizes = synth.loguniform_sizes(count, args.seed + 21, 256, 8192)
     nmax = max(sizes)
     poolA = torch.from_numpy(synth.normal(nmax, args.seed + 22, 0)).cuda().reshape(-1)
     poolB = torch.from_numpy(synth.normal(nmax, args.seed + 22, 1)).cuda().reshape(-1)
+    As = [poolA[:n * n].view(n, n) for n in sizes]
+    Bs = [poolB[:n * n].view(n, n) for n in sizes]
+    Cs = [torch.empty((n, n), device="cuda") for n in sizes]
+    flops = sum(2.0 * n ** 3 for n in sizes)
     srv = stark.Server(150 * 10 ** 9, slots=4)
 
     def one_pass(gaps):
-        Cs, ids, lock = {}, [], th.Lock()
+        ids, late = [], []
+        torch.cuda.synchronize()
         start = time.perf_counter()
-
-        def producer():
-            t = start
-            for n, g in zip(sizes, gaps):
-                t += g
-                while True:
-                    now = time.perf_counter()
-                    if now >= t:
-                        break
-                    time.sleep(min(t - now, 0.0005))
-                C = torch.empty((n, n), device="cuda")
-                rid = srv.submit(poolA[:n * n].view(n, n), poolB[:n * n].view(n, n), C)
-                with lock:
-                    Cs[rid] = C
-                    ids.append(rid)
-
-        thr = th.Thread(target=producer)
-        thr.start()
-        thr.join()
+        t = start
+        for i, g in enumerate(gaps):
+            t += g
+            while True:
+                now = time.perf_counter()
+                if now >= t:
+                    break
+                if t - now > 0.0003:
+                    time.sleep(t - now - 0.0002)
+            ids.append(srv.submit(As[i], Bs[i], Cs[i]))
+            late.append(time.perf_counter() - t)  # scheduled arrival -> submit returned
         srv.drain()
-        end = time.perf_counter()
+        wall = time.perf_counter() - start
         lat = []
-        for rid in ids:
+        for rid, lt in zip(ids, late):
             done, st = srv.poll(rid)
             assert done and st == stark.Status.OK, st
-            lat.append(srv.latency(rid))
-        return np.array(lat), end - start
+            lat.append(srv.latency(rid) + lt)
+        return np.array(lat), wall
 
-    rate = 200.0
-    torch.cuda.synchronize()
-    one_pass(synth.exponential_gaps(count, args.seed + 23, rate))           # warm the workspace cache
-    lat, wall = one_pass(synth.exponential_gaps(count, args.seed + 24, rate))
+    one_pass(synth.exponential_gaps(count, args.seed + 23, 200.0))  # warm the workspace cache
+    sweep = []
+    for k, rate in enumerate((200.0, 2000.0, 8000.0)):
+        before = srv.load()
+        lat, wall = one_pass(synth.exponential_gaps(count, args.seed + 24 + k, rate))
+        after = srv.load()
+        sweep.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                      "aggregate_tflops": flops / wall / 1e12, "offered_tflops": flops / (count / rate) / 1e12,
+                      "wall_s": wall, "max_queued": after["max_queued"],
+                      "deferred_admissions": after["deferred"] - before["deferred"]})
     stats = srv.stats()
     srv.close()
-    flops = sum(2.0 * n ** 3 for n in sizes)
+    base = sweep[0]
     return {"workload": f"Poisson 200 req/s, {count} requests, n log-uniform [256, 8192], fp32 N(0,1), 3xbf16, "
-                        f"budget 150 GB, 4 slots",
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "aggregate_tflops": flops / wall / 1e12,
-            "offered_tflops": flops / (count / rate) / 1e12, "wall_s": wall,
+                        f"budget 150 GB, 4 slots; latency from scheduled arrival",
+            "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "mean_ms": base["mean_ms"],
+            "aggregate_tflops": base["aggregate_tflops"], "offered_tflops": base["offered_tflops"],
+            "wall_s": base["wall_s"], "rate_sweep": sweep,
             "cached_workspaces": stats["cached_workspaces"], "workspace_bytes": stats["owned_bytes"]}
 
 

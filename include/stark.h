@@ -197,9 +197,19 @@ STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, con
  * (allocating [leaves][L][L] fp32 planes) and a separate pass writes each C
  * element once as its signed sum in ascending leaf order, so results are
  * bitwise reproducible run to run (depth <= 3; stark_mul_leaves keeps the
- * fused path).  Modes 0 and 1 agree with mode 2 within fp32 rounding (the
- * order of the additions differs).  Errors: EINVAL, EUNSUPPORTED (mode 2 on
- * an fp64/int64 plan or depth > 3), ENOMEM. */
+ * fused path); mode 3 folds the last recursion level on the way: the CTA
+ * pairs run the seven children of one parent product back to back at one
+ * tile position, and each child's tile is stored (first child of a
+ * quadrant) or added (the others) into that quadrant of the parent's
+ * product, held in [leaves/7][2L][2L] fp32 planes that stay in L2 while the
+ * siblings run; an ordered pass then combines the parent products into C as
+ * mode 2 does one level up (C written once; bitwise reproducible).  Mode 3
+ * needs depth >= 1, a leaf side that is a multiple of 256, breadth-first
+ * traversal and (3xTF32) the MN-major layout; a product it cannot serve
+ * (stark_mul_leaves, another pairing or pipeline) runs the fused path.
+ * All modes agree within fp32 rounding (the order of the additions
+ * differs).  Errors: EINVAL, EUNSUPPORTED (mode 2 on an fp64/int64 plan or
+ * depth > 3; mode 3 outside its conditions), ENOMEM. */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
 /* Leaf launch schedule of the split-fp32 paths (Alg. 4 leaf products), for leaf
@@ -393,6 +403,14 @@ STARK_API stark_status stark_request_latency(stark_server_t server, uint64_t req
  * pointer may be NULL). */
 STARK_API stark_status stark_server_stats(stark_server_t server, int64_t *cached_workspaces, int64_t *owned_bytes,
                                           int64_t *queued);
+
+/* Load counters since the server was created (any pointer may be NULL):
+ * the most requests waiting in the queue at once, the requests whose
+ * admission had to wait for device memory at least once (every workspace of
+ * their size busy and no new one fitting the budget while others ran), and
+ * the requests finished. */
+STARK_API stark_status stark_server_load(stark_server_t server, int64_t *max_queued, int64_t *deferred,
+                                         int64_t *finished);
 
 /* Drains, stops the dispatcher and frees everything the server owns. */
 STARK_API stark_status stark_server_destroy(stark_server_t server);

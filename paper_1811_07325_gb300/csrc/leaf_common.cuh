@@ -20,7 +20,81 @@ struct ItemInfo {
   float* C;
   int64_t n, ldc;
   int use_tma_c;
+  int sib;     // sibling-folded combine: this leaf's M-index digit at the last level (0..6 = M1..M7)
+  int parent;  // and its parent's plane (relative to leaf_begin / 7)
+  bool valid;  // false: a padding item of the sibling-major order (no work)
 };
+
+// Sibling-major order of the CTA-pair items (LeafTcArgs::sib): with U pairs
+// launched and T pair tiles per leaf, item k*U + u is tile position
+// tp = (k / 7) * U + u of the parents' tile grid (parent tp / T, tile tp % T)
+// for sibling k % 7.  Pair u (which takes items u, u + U, ...) so runs the
+// seven children of one parent at one tile position back to back (their
+// parent-quadrant tiles stay in L2 between them), while the U pairs at one
+// step share a sibling leaf, as in the leaf-major order.
+__device__ __forceinline__ int64_t sib_items(const LeafTcArgs& p, int BN, int units) {
+  const int64_t T = (int64_t)(p.L / (2 * kBM)) * (p.L / BN);
+  const int64_t tp = (int64_t)(p.leaf_end - p.leaf_begin) / 7 * T;
+  return (tp + units - 1) / units * 7 * units;
+}
+
+template <int BN, int BK>
+__device__ __forceinline__ ItemInfo decode_sib(int item, const LeafTcArgs& p, const CUtensorMap* tmA,
+                                               const CUtensorMap* tmB, const CUtensorMap* tmC, uint32_t rank,
+                                               int units) {
+  ItemInfo it;
+  const int tiles_n = p.L / BN;
+  const int T = (p.L / (2 * kBM)) * tiles_n;
+  const int parents = (p.leaf_end - p.leaf_begin) / 7;
+  const int k = item / units, u = item % units;
+  const int64_t tp = (int64_t)(k / 7) * units + u;
+  it.valid = tp < (int64_t)parents * T;
+  it.sib = k % 7;
+  it.parent = it.valid ? (int)(tp / T) : 0;
+  const int tile = it.valid ? (int)(tp % T) : 0;
+  it.tA = tmA;
+  it.tB = tmB;
+  it.tC = tmC;
+  it.leaf = p.leaf_begin + it.parent * 7 + it.sib;
+  it.P = p.P;
+  it.m0 = ((tile / tiles_n) * 2 + (int)rank) * kBM;
+  it.n0 = (tile % tiles_n) * BN;
+  it.kblocks = p.L / BK;
+  it.tg = nullptr;
+  it.nt = 0;
+  it.C = p.C;
+  it.n = p.n;
+  it.ldc = p.ldc;
+  it.use_tma_c = 0;
+  return it;
+}
+
+// First and last sibling (product M_{m+1}) that adds into quadrant q of the
+// parent (C11 = M1+M4-M5+M7, C12 = M3+M5, C21 = M2+M4, C22 = M1-M2+M3+M6):
+// the first stores its tile (its sign is + in every quadrant), the others add.
+__host__ __device__ constexpr int sib_first(int q) {
+  return coef_c(0, q) ? 0 : coef_c(1, q) ? 1 : coef_c(2, q) ? 2 : 3;
+}
+__host__ __device__ constexpr int sib_last(int q) {
+  return coef_c(6, q) ? 6 : coef_c(5, q) ? 5 : coef_c(4, q) ? 4 : 3;
+}
+static_assert(coef_c(sib_first(0), 0) > 0 && coef_c(sib_first(1), 1) > 0 && coef_c(sib_first(2), 2) > 0 &&
+                  coef_c(sib_first(3), 3) > 0,
+              "the first contribution to each quadrant is a plain store");
+
+// coef_c for a sibling index known only at run time, from bit masks (one
+// byte per quadrant: which products add into it, and which of them with a
+// minus sign), so no table is read from memory.
+__host__ __device__ constexpr int sib_coef(int m, int q) {
+  constexpr uint32_t nz = 0x59u | (0x14u << 8) | (0x0Au << 16) | (0x27u << 24);
+  constexpr uint32_t ng = (1u << 4) | (1u << 25);
+  const uint32_t bit = 1u << (q * 8 + m);
+  return (nz & bit) ? ((ng & bit) ? -1 : 1) : 0;
+}
+__host__ __device__ constexpr bool sib_coef_matches(int k = 0) {
+  return k == 28 || (sib_coef(k % 7, k / 7) == coef_c(k % 7, k / 7) && sib_coef_matches(k + 1));
+}
+static_assert(sib_coef_matches(), "the bit masks encode the combine table");
 
 template <int BN, int BK, bool GROUPED, bool PAIR>
 __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, const CUtensorMap* tmA,
@@ -87,6 +161,9 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
     it.ldc = p.ldc;
     it.use_tma_c = p.use_tma_c;
   }
+  it.sib = -1;
+  it.parent = 0;
+  it.valid = true;
   return it;
 }
 
@@ -110,6 +187,9 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
   bool has_pos = false, has_neg = false;
   for (int t = 0; t < nt; ++t) (tg[t].sign > 0 ? has_pos : has_neg) = true;
   const bool vec_ok = ((reinterpret_cast<uintptr_t>(it.C) & 15) == 0) && ((it.ldc & 3) == 0);
+  // sibling-folded combine: the previous sibling's stores and reductions
+  // into the same parent boxes (issued by this lane) have completed
+  if (it.sib >= 0 && lane == 0) bulk_wait_group<0>();
 #pragma unroll 1
   for (int chunk = 0; chunk < BN / 32; ++chunk) {
     uint32_t r[32];
@@ -160,6 +240,49 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
         }
       }
       bulk_wait_group_read<0>();  // the slot is free for the next chunk
+    } else if (it.sib >= 0) {
+      // sibling-folded combine: the tile goes into the parent's quadrants
+      // with the sign of W (a plain store from the first sibling of each
+      // quadrant, add-reductions after it).  The same lane issues every
+      // operation on these boxes, sibling after sibling; the wait at the
+      // start of the item (below) orders them.
+      if (lane == 0) bulk_wait_group_read<0>();
+      __syncwarp();
+      const bool any_neg = sib_coef(it.sib, 0) < 0 || sib_coef(it.sib, 1) < 0 || sib_coef(it.sib, 2) < 0 ||
+                           sib_coef(it.sib, 3) < 0;
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        if (sg == 1 && !any_neg) continue;
+        const uint32_t row_addr = ebuf + (uint32_t)sg * 4096u + (uint32_t)lane * 128u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float4 v = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                 __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+          if (sg == 1) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+          const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                       "f"(v.w)
+                       : "memory");
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        const uint64_t keep = policy_evict_last();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int w = sib_coef(it.sib, q);
+          if (w == 0) continue;
+          const int32_t x = n0 + chunk * 32 + (q & 1) * p.L;
+          const int32_t y = m0 + quarter * 32 + (q >> 1) * p.L;
+          const uint64_t pol = it.sib == sib_last(q) ? pol_c : keep;
+          if (it.sib == sib_first(q))
+            tma_store_3d_hint(it.tC, x, y, it.parent, ebuf, pol);
+          else
+            tma_reduce_add_3d(it.tC, x, y, it.parent, ebuf + (w > 0 ? 0u : 4096u), pol);
+        }
+        bulk_commit_group();
+      }
     } else if (p.store_m) {
       // unfused, deterministic combine: this leaf's tile goes to its M
       // plane (tmC maps the M planes here); the combine kernel adds later

@@ -63,8 +63,9 @@ struct Tc2Cfg {
 };
 
 // GROUPED: items of several problems (GroupDesc array, tensor maps in global
-// memory), as in the single-CTA kernel's grouped mode.
-template <bool TF32, bool GROUPED, bool TMN>
+// memory), as in the single-CTA kernel's grouped mode.  SIB: sibling-major
+// item order with the sibling-folded combine (LeafTcArgs::sib).
+template <bool TF32, bool GROUPED, bool TMN, bool SIB>
 __global__ void __launch_bounds__(kThreads2, 1)
     leaf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
@@ -88,8 +89,15 @@ __global__ void __launch_bounds__(kThreads2, 1)
   const bool leader = rank == 0;
   const int unit = (int)(blockIdx.x >> 1);
   const int units = (int)(gridDim.x >> 1);
-  const int num_items =
-      GROUPED ? p.total_items : (p.leaf_end - p.leaf_begin) * (p.L / (2 * kBM)) * (p.L / Cfg::BN);
+  const int num_items = GROUPED ? p.total_items
+                        : SIB   ? (int)sib_items(p, Cfg::BN, units)
+                                : (p.leaf_end - p.leaf_begin) * (p.L / (2 * kBM)) * (p.L / Cfg::BN);
+  auto decode = [&](int item) {
+    if constexpr (SIB)
+      return decode_sib<Cfg::BN, Cfg::BK>(item, p, &tmA, &tmB, &tmC, rank, units);
+    else
+      return decode_item<Cfg::BN, Cfg::BK, GROUPED, true>(item, p, &tmA, &tmB, &tmC, rank);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -104,7 +112,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     if (!GROUPED) {
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
-      if (p.use_tma_c || p.store_m) prefetch_tmap(&tmC);
+      if (p.use_tma_c || p.store_m || SIB) prefetch_tmap(&tmC);
     }
   }
   if (warp == 1) {
@@ -126,7 +134,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
       uint32_t armed = 0, armed_phase = 0;
       bool ok = true;
       for (int item = unit; ok && item < num_items; item += units) {
-        const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, GROUPED, true>(item, p, &tmA, &tmB, &tmC, rank);
+        const ItemInfo it = decode(item);
+        if (!it.valid) continue;
         const int leaf = GROUPED ? it.leaf : it.leaf - p.plane_base;  // workspace plane
         const int m0 = it.m0;                                 // this CTA's 128 rows
         const int nb = it.n0 + (int)rank * Cfg::BNH;          // this CTA's 128 columns
@@ -191,8 +200,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
       bool ok = true;
       bool issued = false;
       for (int item = unit; ok && item < num_items; item += units) {
-        const int kblocks = GROUPED ? decode_item<Cfg::BN, Cfg::BK, true, true>(item, p, &tmA, &tmB, &tmC, rank).kblocks
-                                    : p.L / Cfg::BK;
+        if (SIB && !decode(item).valid) continue;
+        const int kblocks = GROUPED ? decode(item).kblocks : p.L / Cfg::BK;
         // both CTAs' epilogues have drained this accumulator
         if (!mbar_wait_bounded_cluster(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
           ok = false;
@@ -259,9 +268,10 @@ __global__ void __launch_bounds__(kThreads2, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int item = unit; item < num_items; item += units) {
+      const ItemInfo it = decode(item);
+      if (!it.valid) continue;
       if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
       tc_fence_after();
-      const ItemInfo it = decode_item<Cfg::BN, Cfg::BK, GROUPED, true>(item, p, &tmA, &tmB, &tmC, rank);
       epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(acc * Cfg::BN), quarter, lane, ebuf, pol_c);
       tc_fence_before();
       __syncwarp();
@@ -281,16 +291,19 @@ __global__ void __launch_bounds__(kThreads2, 1)
   cluster_sync();
 }
 
-template <bool TF32, bool GROUPED, bool TMN = false>
+template <bool TF32, bool GROUPED, bool TMN = false, bool SIB = false>
 cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                     int num_sms, cudaStream_t st) {
   using Cfg = Tc2Cfg<TF32, TMN>;
-  auto kern = leaf_tc2_kernel<TF32, GROUPED, TMN>;
+  auto kern = leaf_tc2_kernel<TF32, GROUPED, TMN, SIB>;
   int64_t items;
   if constexpr (GROUPED) {
     if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
     items = a.total_items;
   } else {
+    if (SIB && (a.leaf_begin % 7 != 0 || (a.leaf_end - a.leaf_begin) % 7 != 0)) return cudaErrorInvalidValue;
+    // (sibling-major: the padded item count follows the pairs launched; the
+    // kernel derives it, and any count >= the pairs gives the same launch)
     items = (int64_t)(a.leaf_end - a.leaf_begin) * (a.L / (2 * kBM)) * (a.L / Cfg::BN);
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
@@ -309,6 +322,11 @@ bool leaf_tc2_fits(const LeafTcArgs& a) { return a.L % 256 == 0; }
 cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                             const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t st) {
   if (!leaf_tc2_fits(a)) return cudaErrorInvalidValue;
+  if (a.sib) {
+    if (tf32 && !a.b_mn) return cudaErrorInvalidValue;  // sibling fold: bf16 and MN-major tf32 only
+    return tf32 ? launch2<true, false, true, true>(a, tmA, tmB, tmC, num_sms, st)
+                : launch2<false, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
+  }
   if (tf32 && a.b_mn) return launch2<true, false, true>(a, tmA, tmB, tmC, num_sms, st);
   return tf32 ? launch2<true, false>(a, tmA, tmB, tmC, num_sms, st)
               : launch2<false, false>(a, tmA, tmB, tmC, num_sms, st);

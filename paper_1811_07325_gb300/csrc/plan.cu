@@ -439,7 +439,23 @@ stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* 
 }
 
 stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
-  if (!p || mode < 0 || mode > 2) return STARK_EINVAL;
+  if (!p || mode < 0 || mode > 3) return STARK_EINVAL;
+  if (mode == 3) {
+    // sibling fold on the CTA-pair kernel: 256-wide tiles, breadth first
+    if (!p->is_tc || p->depth < 1 || p->dfs || p->L % 256 != 0 || (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn))
+      return STARK_EUNSUPPORTED;
+    if (!p->q_planes && p->n > 0) {
+      const int64_t parents = p->P / 7, side = 2 * p->L;
+      const size_t bytes = (size_t)parents * side * side * sizeof(float);
+      if (cudaMalloc(&p->q_planes, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->q_planes = nullptr;
+        return STARK_ENOMEM;
+      }
+      p->ws_bytes += (int64_t)bytes;
+      if (!make_tmap_mplanes(&p->tmQ, p->q_planes, side, parents)) return STARK_EUNSUPPORTED;
+    }
+  }
   if (mode == 2) {
     if (!p->is_tc || p->depth > 3 || p->dfs) return STARK_EUNSUPPORTED;
     if (!p->m_planes && p->n > 0) {
@@ -503,7 +519,7 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
 
 stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
   if (!p || levels < 0 || levels > 2) return STARK_EINVAL;
-  if (!traversal_supported(p->depth, p->dt, levels) || (levels && p->combine_mode == 2)) return STARK_EUNSUPPORTED;
+  if (!traversal_supported(p->depth, p->dt, levels) || (levels && p->combine_mode >= 2)) return STARK_EUNSUPPORTED;
   if (levels == p->dfs || p->n == 0) {
     p->dfs = levels;
     return STARK_OK;
@@ -722,6 +738,7 @@ void plan_release(stark_plan_s* p) {
       if (e) cudaEventDestroy(e);
   cudaFree(p->cstage);
   cudaFree(p->m_planes);
+  cudaFree(p->q_planes);
   for (auto e : p->ev)
     if (e) cudaEventDestroy(e);
   p->ev.clear();
@@ -755,15 +772,21 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
   stark_status st = STARK_OK;
-  if (top < 0 && depth == 3 && om == kOutSplitBf16) {
-    // 3xBF16: one pass per operand, every input element read once
-    st = to_status(launch_divide3(da, 0, om, s));
-    if (st == STARK_OK) st = to_status(launch_divide3(db, 1, om, s));
-  } else if (top < 0 && depth == 3) {
-    // breadth first at depth 3: one launch per top-level product, each a
-    // depth-1 subtree read through that product's level-1 sum and written
-    // to its block of 7^(d-1) planes (the outer-prefix form of the deep
-    // kernel keeps too few loads in flight to stream at HBM bandwidth)
+  bool banded = false;
+  if (top < 0 && depth == 3) {
+    // breadth first at depth 3: the seven top-level products' depth-2
+    // subtrees (each read through its level-1 sum), interleaved by row band
+    // in one launch per operand so a band's input comes from HBM once
+    DivideArgs a0 = da, a1 = db;
+    a0.npad = a1.npad = p->npad / 2;
+    banded = launch_divide_banded3(a0, 0, in, om, s) == cudaSuccess &&
+             launch_divide_banded3(a1, 1, in, om, s) == cudaSuccess;
+    cudaGetLastError();
+  }
+  if (top < 0 && depth == 3 && !banded) {
+    // (leaf sides the band does not divide) one launch per top-level
+    // product, each a depth-2 subtree read through that product's level-1
+    // sum and written to its block of 7^(d-1) planes
     const int64_t sub = pow7i(depth - 1);
     // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
     // integers, tf32 in fp32 containers, else the input type
@@ -780,7 +803,7 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
         st = to_status(launch_divide(a, depth - 1, side, in, om, s));
       }
     }
-  } else {
+  } else if (!banded) {
     st = to_status(launch_divide(da, depth, 0, in, om, s));
     if (st == STARK_OK) st = to_status(launch_divide(db, depth, 1, in, om, s));
   }
@@ -801,6 +824,20 @@ static bool plan_deterministic(const stark_plan_s* p, int64_t lb, int64_t le) {
   return p->is_tc && p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P;
 }
 
+// Whether leaves [lb, le) use the sibling-folded combine (combine mode 3): the
+// whole product, breadth first, on the CTA-pair kernel (256-wide tiles).
+static bool plan_sib(const stark_plan_s* p, int64_t lb, int64_t le) {
+  return p->is_tc && p->combine_mode == 3 && p->q_planes && lb == 0 && le == p->P && p->pair_mode == 2 &&
+         p->bn == 256 && p->L % 256 == 0 && !p->dfs && !p->deep_pipeline && p->depth >= 1 &&
+         (p->dt == STARK_F32_SPLIT_BF16 || p->tf32_mn);
+}
+
+// Whether a separate pass writes every element of C (combine modes 2 and 3):
+// then C is not cleared first and no staging copy is used.
+static bool plan_stored(const stark_plan_s* p, int64_t lb, int64_t le) {
+  return plan_deterministic(p, lb, le) || plan_sib(p, lb, le);
+}
+
 // Leaf products of leaves [lb, le) with the combine, operands in workspace
 // planes numbered from plane_base.  With a staging copy of C the products
 // land there; plan_run_accumulate moves them into C.
@@ -818,7 +855,8 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     a.ccount = p->d_ccount;
     a.maxT = p->maxT;
     const bool deterministic = plan_deterministic(p, lb, le);
-    const bool staged = !deterministic && plan_uses_cstage(p, C);
+    const bool sib = plan_sib(p, lb, le);
+    const bool staged = !deterministic && !sib && plan_uses_cstage(p, C);
     a.C = static_cast<float*>(staged ? p->cstage : C);
     a.ldc = staged ? staged_ld(p->n) : p->n;
     a.n = core_side(p);  // C rows/columns the combine covers
@@ -831,6 +869,10 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       a.store_m = 1;
       a.use_tma_c = 0;
       tmC = p->tmM;
+    } else if (sib) {
+      a.sib = 1;
+      a.use_tma_c = 0;
+      tmC = p->tmQ;
     }
     a.pair = p->pair_mode;
     a.band = p->raster_band;
@@ -861,6 +903,11 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
     if (st == STARK_OK && deterministic)
       st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, core_side(p),
                                     static_cast<float*>(C), p->n, s));
+    // sibling fold: the parent planes are the leaf products of the depth-1
+    // recursion; one ordered pass combines them into C
+    if (st == STARK_OK && sib)
+      st = to_status(launch_combine(static_cast<const float*>(p->q_planes), p->depth - 1, 2 * p->L, p->npad,
+                                    core_side(p), static_cast<float*>(C), p->n, s));
   } else if (p->int_tc) {
     LeafTcArgs a{};
     a.P = (int32_t)p->P_ws;
@@ -964,10 +1011,9 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
   // the peeled edge, once per product (with the range that holds leaf 0, so
   // the partial products of a leaf partition still sum to A B), then the
   // staging copy into C
-  const bool staged = p->is_tc && !plan_deterministic(p, lb, le) && plan_uses_cstage(p, C);
+  const bool staged = p->is_tc && !plan_stored(p, lb, le) && plan_uses_cstage(p, C);
   if (st == STARK_OK && p->peel > 0 && lb == 0)
-    st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, plan_deterministic(p, lb, le),
-                     s);
+    st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, plan_stored(p, lb, le), s);
   if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
   if (ev) cudaEventRecord(ev[3], s);
   p->timing_active = false;
@@ -983,8 +1029,8 @@ stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, in
     ++p->timing_used;
     p->timing_active = true;
   }
-  if (p->is_tc && p->combine_mode == 2 && p->m_planes && lb == 0 && le == p->P) {
-    // deterministic combine writes every element of C: nothing to clear
+  if (plan_stored(p, lb, le)) {
+    // a separate combine pass writes every element of C: nothing to clear
   } else if (p->is_tc && plan_uses_cstage(p, C)) {
     if (cudaMemsetAsync(p->cstage, 0, (size_t)p->n * staged_ld(p->n) * 4, s) != cudaSuccess)
       return to_status(cudaGetLastError());

@@ -52,9 +52,12 @@ struct stark_plan_s {
   int* d_err = nullptr;
   uint64_t timeout_ns = stark::kDefaultTimeoutNs;
   int combine_mode = 0;  // 0: TMA bulk reductions where C allows, 1: always vector atomics,
-                         // 2: deterministic (store M planes, ordered combine pass)
+                         // 2: deterministic (store M planes, ordered combine pass),
+                         // 3: sibling fold (parent planes in L2, ordered pass at depth - 1)
   void* m_planes = nullptr;  // [P][L][L] fp32 leaf products (combine mode 2)
   CUtensorMap tmM;
+  void* q_planes = nullptr;  // [P/7][2L][2L] fp32 parent products (combine mode 3, sibling fold)
+  CUtensorMap tmQ;
   int pair_mode = 2;     // leaf schedule where the tiling allows (L % 256 == 0): 2 CTA pairs on one
                          // cta_group::2 MMA, 0 single CTAs
   CUtensorMap tmBp;      // tf32 Y map with 128-row boxes for the pair MMA

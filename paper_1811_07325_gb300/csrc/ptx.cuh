@@ -191,6 +191,26 @@ __device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* m, int32_t 
       : "memory");
 }
 
+// 3-D tiled bulk tensor add-reduction shared -> global (fp32 add at L2).
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap* m, int32_t c0, int32_t c1, int32_t c2,
+                                                  uint32_t src, uint64_t policy) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group.L2::cache_hint"
+      " [%0, {%1, %2, %3}], [%4], %5;" ::"l"(reinterpret_cast<uint64_t>(m)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(src), "l"(policy)
+      : "memory");
+}
+
+// 3-D tiled bulk tensor store shared -> global with an L2 eviction hint.
+__device__ __forceinline__ void tma_store_3d_hint(const CUtensorMap* m, int32_t c0, int32_t c1, int32_t c2,
+                                                  uint32_t src, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], %5;" ::"l"(
+          reinterpret_cast<uint64_t>(m)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(src), "l"(policy)
+      : "memory");
+}
+
 // Non-tensor bulk add-reduction of `bytes` (a multiple of 16) 64-bit
 // integers from shared memory into global memory (at L2; wraps modulo
 // 2^64).  Both addresses 16-byte aligned.

@@ -56,6 +56,7 @@ struct Request {
   void* target = nullptr;      // combine target: C, or the workspace's staging copy
   int64_t ld = 0;              // its row pitch
   stark_status status = STARK_OK;
+  bool deferred = false;       // admission waited at least once for device memory
 };
 
 struct Workspace {
@@ -92,6 +93,10 @@ struct stark_server_s {
   uint64_t next_id = 1;
   int* d_err = nullptr;
   int num_sms = 1;
+  // load counters (stark_server_load)
+  int64_t max_queued = 0;  // most requests waiting at once
+  int64_t deferred = 0;    // requests whose admission waited for device memory
+  int64_t done = 0;        // requests finished
 };
 
 using namespace stark;
@@ -239,6 +244,7 @@ void finish(stark_server_s* s, Request* r, stark_status st) {
   const double lat = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
   s->finished[r->id] = {st, lat};
   s->latency[r->id] = lat;
+  ++s->done;
   s->live.erase(r->id);
   if (r->ws) release_workspace(s, r->ws);
   delete r;
@@ -383,7 +389,13 @@ void worker_loop(stark_server_s* s) {
           if (err == STARK_EBUSY) {
             bool running = false;
             for (Slot& o : s->slots) running = running || !o.running.empty();
-            if (running || !batch.empty()) break;  // memory frees up when those finish
+            if (running || !batch.empty()) {  // memory frees up when those finish
+              if (!r->deferred) {
+                r->deferred = true;
+                ++s->deferred;
+              }
+              break;
+            }
             err = STARK_ENOMEM;                    // cannot ever fit
           }
           s->queue.pop_front();
@@ -514,6 +526,7 @@ stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const voi
     }
     s->live[r->id] = r;
     s->queue.push_back(r);
+    s->max_queued = std::max<int64_t>(s->max_queued, (int64_t)s->queue.size());
   }
   s->cv.notify_one();
   return STARK_OK;
@@ -566,6 +579,15 @@ stark_status stark_server_stats(stark_server_t s, int64_t* cached_workspaces, in
   if (cached_workspaces) *cached_workspaces = w;
   if (owned_bytes) *owned_bytes = (int64_t)s->owned;
   if (queued) *queued = (int64_t)s->queue.size();
+  return STARK_OK;
+}
+
+stark_status stark_server_load(stark_server_t s, int64_t* max_queued, int64_t* deferred, int64_t* finished) {
+  if (!s) return STARK_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (max_queued) *max_queued = s->max_queued;
+  if (deferred) *deferred = s->deferred;
+  if (finished) *finished = s->done;
   return STARK_OK;
 }
 

@@ -76,9 +76,10 @@ struct DivideArgs {
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
-// Breadth-first depth 3 in one pass for fp32 input and 3xBF16 output (every
-// input element read once); other dtypes use launch_divide per top product.
-cudaError_t launch_divide3(const DivideArgs& a, int side, OutMode out, cudaStream_t s);
+// Breadth-first depth 3 as the seven top-level products' depth-2 subtrees in
+// one launch, interleaved by row band so each band's input is read from HBM
+// once (a.npad = the full padded side / 2; every leaf plane written).
+cudaError_t launch_divide_banded3(const DivideArgs& a, int side, InType in, OutMode out, cudaStream_t s);
 // The same for a depth-first subtree (a.top >= 0); launch_divide forwards.
 cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
@@ -146,6 +147,10 @@ struct LeafTcArgs {
                        // swizzle; 0 = Y planes transposed to N x K, read K-major
   int32_t band;        // > 0: a leaf's tiles run in bands of `band` tile columns (row-major inside a
                        // band); 0 or not dividing the tile columns: row-major over the whole leaf
+  int32_t sib;         // 1: sibling-folded combine (CTA-pair kernel): the 7 children of one parent
+                       // run back to back at one tile position and their tiles are stored or added
+                       // into the parent's quadrants (tmC = parent planes [P/7][2L][2L]); leaf
+                       // range of whole parents
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;

@@ -99,6 +99,7 @@ _SIGS = {
     "stark_request_latency": ([_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], _ci),
     "stark_server_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
     "stark_server_destroy": ([_vp], _ci),
+    "stark_server_load": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
     "stark_server_admission": ([ctypes.c_size_t, _i64, _ci, _ci, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                 ctypes.POINTER(_i64)], _ci),
     "stark_error_norms": ([_i64, _ci, _vp, _vp, _vp, _vp, _i64, _vp, _vp, ctypes.POINTER(ErrorReport), _vp], _ci),
@@ -276,7 +277,9 @@ class Plan:
 
     def set_combine(self, mode: int):
         """0: fused, TMA bulk reductions (default); 1: fused, vector atomics;
-        2: deterministic (stored leaf products, ordered combine pass)."""
+        2: deterministic (stored leaf products, ordered combine pass);
+        3: sibling fold (parent products folded in L2, ordered pass one
+        level up)."""
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
 
     def set_pairing(self, mode):
@@ -441,6 +444,14 @@ class Server:
         _check(_lib.stark_server_stats(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(q)),
                "stark_server_stats")
         return {"cached_workspaces": w.value, "owned_bytes": b.value, "queued": q.value}
+
+    def load(self):
+        """Most requests queued at once, requests whose admission waited for
+        device memory, requests finished (``stark_server_load``)."""
+        m, d, f = _i64(), _i64(), _i64()
+        _check(_lib.stark_server_load(self._h, ctypes.byref(m), ctypes.byref(d), ctypes.byref(f)),
+               "stark_server_load")
+        return {"max_queued": m.value, "deferred": d.value, "finished": f.value}
 
 
 def server_admission(hbm_budget_bytes: int, n: int, dtype: DType = DType.F32_SPLIT_BF16, staged: bool = False):

@@ -669,11 +669,72 @@ def test_auto_depth(S):
         assert 0 <= p.depth <= 4
 
 
+# ----------------------------------------------------------------- sibling-folded combine
+@pytest.mark.parametrize("dtype,n,d", [("F32_SPLIT_BF16", 1024, 1), ("F32_SPLIT_BF16", 2048, 2),
+                                       ("F32_SPLIT_BF16", 1001, 1), ("F32_SPLIT_BF16", 2048, 3),
+                                       ("F32_SPLIT_BF16", 4096, 4), ("F32_SPLIT_TF32", 2048, 2),
+                                       ("F32_SPLIT_TF32", 2001, 2)])
+def test_sibling_fold_matches_oracle(S, dtype, n, d):
+    # combine mode 3: the seven children of each parent fold into its
+    # quadrants (store, then add-reductions in sibling order), one ordered
+    # pass one level up writes C.  Every element against the FP64 oracle
+    # (sampled rows above n = 2048), bitwise equal across runs, and within
+    # fp32 reordering of the fused combine
+    A = synth.normal(n, 66 + d, 0)
+    B = synth.normal(n, 66 + d, 1)
+    rows = np.arange(n) if n <= 2048 else synth.sample_rows(n, 128, 66)
+    want = oracle.gemm_rows(A, B, rows)
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    r = torch.from_numpy(rows).cuda()
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        p.set_combine(3)
+        C1 = p.mul(dA, dB)[r].cpu().numpy()
+        C2 = p.mul(dA, dB)[r].cpu().numpy()
+        p.check()
+        check_split(C1, want, an, bn, dtype, L=p.leaf)
+        p.set_combine(0)
+        Cf = p.mul(dA, dB)[r].cpu().numpy()
+        p.check()
+    assert np.array_equal(C1.view(np.uint32), C2.view(np.uint32))
+    assert np.abs(C1 - Cf).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_sibling_fold_conditions_and_fallbacks(S):
+    n = 1024
+    A = synth.normal(n, 67, 0)
+    B = synth.normal(n, 67, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    for d, m in ((0, 1024), (1, 640)):  # depth 0; a leaf side (384) that is not a multiple of 256
+        with S.Plan(m, d, S.DType.F32_SPLIT_BF16) as p:
+            with pytest.raises(S.StarkError) as e:
+                p.set_combine(3)
+            assert e.value.status == S.Status.EUNSUPPORTED
+    with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
+        p.set_combine(3)
+        with pytest.raises(S.StarkError):
+            p.set_traversal(1)  # depth first keeps one subtree: no parent planes
+        # products mode 3 cannot serve run the fused path: single CTAs, and a
+        # partition of the leaves whose partial products sum to A B
+        p.set_pairing(0)
+        check_split(p.mul(dA, dB).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+        p.set_pairing(2)
+        parts = []
+        for lb, le in ((0, 20), (20, 49)):
+            parts.append(p.mul_leaves(dA, dB, lb, le))
+        p.check()
+        check_split((parts[0] + parts[1]).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+
+
 # ----------------------------------------------------------------- full size, sampled rows
 @pytest.mark.slow
 @pytest.mark.parametrize("dtype,d,combine", [("F32_SPLIT_BF16", 2, 0), ("F32_SPLIT_BF16", 3, 0),
                                              ("F32_SPLIT_TF32", 2, 0), ("F32_SPLIT_TF32", 3, 0),
-                                             ("F32_SPLIT_BF16", 2, 2), ("F32_SPLIT_BF16", 3, 2)])
+                                             ("F32_SPLIT_BF16", 2, 2), ("F32_SPLIT_BF16", 3, 2),
+                                             ("F32_SPLIT_BF16", 2, 3), ("F32_SPLIT_BF16", 3, 3),
+                                             ("F32_SPLIT_TF32", 3, 3)])
 def test_full_size_sampled_rows(S, dtype, d, combine):
     # the bench workload in the bench's launch configuration (CTA pairs;
     # fused combine, or the deterministic one of its second leg)
