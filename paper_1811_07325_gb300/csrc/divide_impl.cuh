@@ -168,9 +168,7 @@ struct Tree {
   }
 };
 
-// KEEP: the input is read again soon (by the other top-level products of a
-// band): ordinary cached loads instead of the streaming ones.
-template <typename Tin, int VEC, bool KEEP = false>
+template <typename Tin, int VEC>
 struct Loader {
   using Acc = typename AccOf<Tin>::type;
   const Tin* __restrict__ X;
@@ -178,31 +176,23 @@ struct Loader {
   int64_t ld;   // row stride
   bool vec_ok;  // rows are VEC-aligned: vector loads allowed where in bounds
 
-  template <typename T>
-  __device__ __forceinline__ static T load(const T* p) {
-    if constexpr (KEEP)
-      return __ldg(p);
-    else
-      return __ldcs(p);
-  }
-
   __device__ __forceinline__ Vec<Acc, VEC> operator()(int64_t row, int64_t col) const {
     Vec<Acc, VEC> r;
     if (row < n && col + VEC <= n && vec_ok) {
       const Tin* p = X + row * ld + col;
       if constexpr (sizeof(Tin) * VEC == 16) {
-        const int4 raw = load(reinterpret_cast<const int4*>(p));
+        const int4 raw = __ldcs(reinterpret_cast<const int4*>(p));
         const Tin* t = reinterpret_cast<const Tin*>(&raw);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)t[e];
       } else {
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)load(p + e);
+        for (int e = 0; e < VEC; ++e) r.v[e] = (Acc)__ldcs(p + e);
       }
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; ++e)
-        r.v[e] = (row < n && col + e < n) ? (Acc)load(X + row * ld + col + e) : Acc(0);
+        r.v[e] = (row < n && col + e < n) ? (Acc)__ldcs(X + row * ld + col + e) : Acc(0);
     }
     return r;
   }
@@ -229,10 +219,10 @@ __device__ __forceinline__ TermPair terms_of(int m) {
 // from the full (padded) input, level by level in the same order as the
 // breadth-first divide: S_k = two-term sum of quadrants of S_{k-1} (the
 // outermost evaluation is the deepest level), S_0 = the input.
-template <typename Tin, int VEC, int SIDE, int K, bool KEEP = false>
+template <typename Tin, int VEC, int SIDE, int K>
 struct TopLoader {
   using Acc = typename AccOf<Tin>::type;
-  Loader<Tin, VEC, KEEP> ld;
+  Loader<Tin, VEC> ld;
   int dig[K];
   int64_t npad;  // side of the full problem
 
@@ -352,72 +342,6 @@ cudaError_t launch_one(const DivideArgs& a, cudaStream_t st) {
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
   constexpr int F = D < 2 ? 0 : D - 2;  // outer levels: one grid row per prefix
   divide_kernel<Tin, OUT, D, SIDE, VEC, K><<<dim3((unsigned)blocks, (unsigned)pow7c(F)), 256, 0, st>>>(a, vec_ok);
-  count_launch();
-  return cudaGetLastError();
-}
-
-// Element pointer `elems` elements past `p` in the plane type of OUT.
-template <int OUT, typename Tin>
-__device__ __forceinline__ void* plane_advance(void* p, int64_t elems) {
-  if (!p) return p;
-  if constexpr (OUT == kOutSplitBf16 || OUT == kOutBf16Exact)
-    return reinterpret_cast<__nv_bfloat16*>(p) + elems;
-  else if constexpr (OUT == kOutSplitTf32)
-    return reinterpret_cast<float*>(p) + elems;
-  else
-    return reinterpret_cast<Tin*>(p) + elems;
-}
-
-// Breadth-first depth 3 as seven depth-2 subtrees, one per top-level product
-// M1..M7 (each read through its level-1 operand sum, as the depth-first
-// loader does), interleaved by row band: the blocks run band after band and,
-// within a band, the seven products one after another.  A band's input (the
-// 8 x BAND operand rows whose quadrant vectors its positions read) is read
-// from HBM by the first product and from L2 by the other six, and the blocks
-// in flight write the 2 x 49 planes of one or two products at a time.
-// a.npad is the subproblem side (the full padded side / 2), as for K = 1.
-template <typename Tin, int OUT, int SIDE, int VEC, int BAND>
-__global__ void __launch_bounds__(256, 2) divide_banded_kernel(DivideArgs a, int vec_ok) {
-  using Acc = typename AccOf<Tin>::type;
-  constexpr int R = 2;  // levels below the top one, in registers
-  const int64_t per_row = a.L / VEC;
-  const int64_t per_band = BAND * per_row / blockDim.x;  // blocks per (band, product)
-  const int64_t blk = blockIdx.x;
-  const int64_t band = blk / (7 * per_band);
-  const int m1 = (int)((blk / per_band) % 7);
-  const int64_t pos = (blk % per_band) * blockDim.x + threadIdx.x;
-  const int64_t i = band * BAND + pos / per_row;
-  const int64_t j = (pos % per_row) * VEC;
-  TopLoader<Tin, VEC, SIDE, 1, true> ld;
-  ld.ld = Loader<Tin, VEC, true>{static_cast<const Tin*>(a.X), a.n, a.ld, vec_ok != 0};
-  ld.dig[0] = m1;
-  ld.npad = a.npad << 1;
-  const int64_t plane = a.L * a.L;
-  const int64_t first = (int64_t)m1 * pow7c(R) * plane;  // this product's block of 49 planes
-  const Emitter<OUT, Tin, VEC> emit{plane_advance<OUT, Tin>(a.out_hi, first), plane_advance<OUT, Tin>(a.out_lo, first),
-                                    plane, i * a.L + j, a.range_flag};
-  const int64_t npad = a.npad;
-  Vec<Acc, VEC> in[pow4c(R)];
-#pragma unroll
-  for (int g = 0; g < pow4c(R); ++g) {
-    const int q1 = g >> 2, q2 = g & 3;
-    const int64_t r = i + (int64_t)(q1 >> 1) * (npad >> 1) + (int64_t)(q2 >> 1) * (npad >> 2);
-    const int64_t c = j + (int64_t)(q1 & 1) * (npad >> 1) + (int64_t)(q2 & 1) * (npad >> 2);
-    in[g] = ld(r, c);
-  }
-  Tree<Acc, SIDE, R, VEC>::run(in, 0, emit);
-}
-
-template <typename Tin, int OUT, int SIDE>
-cudaError_t launch_banded3(const DivideArgs& a, cudaStream_t st) {
-  constexpr int VEC = 16 / (int)sizeof(Tin);
-  constexpr int BAND = 256 / (int)sizeof(Tin);  // input rows per band: 8 x BAND x 8L elements (32 MB at L = 2048)
-  if (a.L % VEC != 0 || a.L % BAND != 0 || a.ld < a.n || a.npad != 4 * a.L) return cudaErrorInvalidValue;
-  if ((BAND * (a.L / VEC)) % 256 != 0) return cudaErrorInvalidValue;
-  const int vec_ok = (a.ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
-  const int64_t blocks = (a.L / BAND) * 7 * (BAND * (a.L / VEC) / 256);
-  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  divide_banded_kernel<Tin, OUT, SIDE, VEC, BAND><<<(unsigned)blocks, 256, 0, st>>>(a, vec_ok);
   count_launch();
   return cudaGetLastError();
 }

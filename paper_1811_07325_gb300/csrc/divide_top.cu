@@ -33,21 +33,6 @@ cudaError_t by_depth_top(const DivideArgs& a, int depth, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_divide_banded3(const DivideArgs& a, int side, InType in, OutMode out, cudaStream_t st) {
-  if (in == kInF32 && out == kOutSplitBf16)
-    return side == 0 ? launch_banded3<float, kOutSplitBf16, 0>(a, st) : launch_banded3<float, kOutSplitBf16, 1>(a, st);
-  if (in == kInF32 && out == kOutSplitTf32)
-    return side == 0 ? launch_banded3<float, kOutSplitTf32, 0>(a, st) : launch_banded3<float, kOutSplitTf32, 1>(a, st);
-  if (in == kInF64 && out == kOutPlain)
-    return side == 0 ? launch_banded3<double, kOutPlain, 0>(a, st) : launch_banded3<double, kOutPlain, 1>(a, st);
-  if (in == kInI64 && out == kOutPlain)
-    return side == 0 ? launch_banded3<int64_t, kOutPlain, 0>(a, st) : launch_banded3<int64_t, kOutPlain, 1>(a, st);
-  if (in == kInI64 && out == kOutBf16Exact)
-    return side == 0 ? launch_banded3<int64_t, kOutBf16Exact, 0>(a, st)
-                     : launch_banded3<int64_t, kOutBf16Exact, 1>(a, st);
-  return cudaErrorInvalidValue;
-}
-
 cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t st) {
   if (a.top < 0) return cudaErrorInvalidValue;
   if (in == kInF32 && out == kOutSplitBf16)

@@ -772,21 +772,11 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     db.out_lo = static_cast<char*>(p->Y) + half;
   }
   stark_status st = STARK_OK;
-  bool banded = false;
   if (top < 0 && depth == 3) {
-    // breadth first at depth 3: the seven top-level products' depth-2
-    // subtrees (each read through its level-1 sum), interleaved by row band
-    // in one launch per operand so a band's input comes from HBM once
-    DivideArgs a0 = da, a1 = db;
-    a0.npad = a1.npad = p->npad / 2;
-    banded = launch_divide_banded3(a0, 0, in, om, s) == cudaSuccess &&
-             launch_divide_banded3(a1, 1, in, om, s) == cudaSuccess;
-    cudaGetLastError();
-  }
-  if (top < 0 && depth == 3 && !banded) {
-    // (leaf sides the band does not divide) one launch per top-level
-    // product, each a depth-2 subtree read through that product's level-1
-    // sum and written to its block of 7^(d-1) planes
+    // breadth first at depth 3: one launch per top-level product, each a
+    // depth-2 subtree read through that product's level-1 sum and written
+    // to its block of 7^(d-1) planes (the outer-prefix form of the deep
+    // kernel keeps too few loads in flight to stream at HBM bandwidth)
     const int64_t sub = pow7i(depth - 1);
     // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
     // integers, tf32 in fp32 containers, else the input type
@@ -803,7 +793,7 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
         st = to_status(launch_divide(a, depth - 1, side, in, om, s));
       }
     }
-  } else if (!banded) {
+  } else {
     st = to_status(launch_divide(da, depth, 0, in, om, s));
     if (st == STARK_OK) st = to_status(launch_divide(db, depth, 1, in, om, s));
   }

@@ -76,10 +76,6 @@ struct DivideArgs {
 // Divide phase for one operand: writes the 7^depth leaf operand sums as
 // row-major L x L planes.  side 0 = A (M x K planes), side 1 = B (K x N).
 cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
-// Breadth-first depth 3 as the seven top-level products' depth-2 subtrees in
-// one launch, interleaved by row band so each band's input is read from HBM
-// once (a.npad = the full padded side / 2; every leaf plane written).
-cudaError_t launch_divide_banded3(const DivideArgs& a, int side, InType in, OutMode out, cudaStream_t s);
 // The same for a depth-first subtree (a.top >= 0); launch_divide forwards.
 cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
