@@ -1,9 +1,11 @@
 """Benchmark: Strassen C = A.B at n = 16384, FP32 inputs N(0,1), 3xBF16 split
 leaves on the tcgen05 tensor cores, through libstark.so.
 
-One step = one full product (zero C, divide A and B into every leaf operand,
-one leaf-product launch with the combine fused in its epilogue) on inputs
-already resident in HBM.  Prints one JSON line (rank 0).
+One step = one full product (divide A and B into every leaf operand, one
+leaf-product launch, and the combine of Alg. 5: fused into that launch's
+epilogue, or stored by it and summed by an ordered pass; the plan measures
+which is fastest, stark_plan_set_combine(-1)) on inputs already resident in
+HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--n 16384] [--depth 2] [--dtype bf16|tf32]
@@ -51,9 +53,10 @@ def leaf_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic(n, depth, kernel):
+def measured_traffic(n, depth, kernel, combine=0):
     """DRAM bytes per leaf launch from the committed ncu summary, if it was
-    taken on this exact kernel source, kernel and workload; else None."""
+    taken on this exact kernel source, kernel, combine mode and workload;
+    else None."""
     if kernel != PAIR_KERNEL:
         return None
     try:
@@ -65,7 +68,7 @@ def measured_traffic(n, depth, kernel):
                     kv[k.strip()] = v.strip().strip("`")
         if kv.get("kernel_source_sha256") != leaf_source_hash():
             return None
-        if int(kv.get("n", -1)) != n or int(kv.get("depth", -1)) != depth:
+        if int(kv.get("n", -1)) != n or int(kv.get("depth", -1)) != depth or int(kv.get("combine", 0)) != combine:
             return None
         return float(kv["traffic_bytes_per_launch"])
     except Exception:
@@ -526,7 +529,8 @@ def main():
     ap.add_argument("--no-tf32", action="store_true")
     ap.add_argument("--pairing", type=int, default=-1,
                     help="leaf schedule: 0 single CTAs, 2 cta_group::2 pairs")
-    ap.add_argument("--combine", type=int, default=0)
+    ap.add_argument("--combine", type=int, default=-1,
+                    help="combine mode: 0 fused, 2 deterministic, 3 sibling fold, -1 the fastest, measured")
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
     ap.add_argument("--traversal", type=int, default=0, help="k > 0: depth first over the top k levels")
@@ -660,28 +664,45 @@ def main():
     # ---------------------------------------------------------------- roofline of the leaf kernel
     pk = peaks()
     leaf_flops = 3 * 2.0 * plan.leaves * plan.leaf ** 3  # three bf16 products per leaf
-    achieved = leaf_flops / (phases["leaf_combine"] * 1e-3) / 1e12
+    achieved = leaf_flops / (phases["leaf_kernel"] * 1e-3) / 1e12
     pair_mode = args.pairing if args.pairing >= 0 else 2
     kernel = PAIR_KERNEL if (pair_mode == 2 and plan.leaf % 256 == 0 and args.deep_pipeline != 1) \
         else "leaf_tc_kernel"
     # the leaf launch lasts ~10-20 ms inside a timed region of well under a
     # second at full clocks: the burst peak is its denominator; the sustained
     # (power-capped, seconds-long) figure is kept beside it
-    roofline = {"kernel": f"{kernel} (3xBF16 leaf GEMMs + fused combine)", "bound": "tensor",
+    epilogue = {0: "fused combine", 1: "fused combine (atomics)", 2: "stores each M_l; an ordered pass combines",
+                3: "folds siblings into parent planes; an ordered pass combines one level up"}[plan.combine]
+    roofline = {"kernel": f"{kernel} (3xBF16 leaf GEMMs; epilogue {epilogue})", "bound": "tensor",
                 "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16"], "traffic": measured_traffic(n, plan.depth, kernel),
+                "frac": achieved / pk["bf16"], "traffic": measured_traffic(n, plan.depth, kernel, plan.combine),
                 "peak_source": f"{pk['source']} bf16 burst",
                 "peak_sustained": pk["bf16_sustained"], "frac_of_sustained": achieved / pk["bf16_sustained"],
                 "algorithmic_flops_per_launch": leaf_flops,
-                "launch_ms": phases["leaf_combine"]}
-    divide_bytes = 2 * (n * n * 4) + plan.workspace_bytes  # read A, B; write every leaf operand (hi+lo)
+                "launch_ms": phases["leaf_kernel"]}
+    esz = 4 if args.dtype == "bf16" else 8  # bytes per leaf element per operand (hi + lo)
+    operand_bytes = 2 * plan.leaves * plan.leaf ** 2 * esz
+    divide_bytes = 2 * (n * n * 4) + operand_bytes  # read A, B; write every leaf operand (hi+lo)
+    # the combine's HBM bytes: fused, C cleared and written once (the L2
+    # reductions in between are not algorithmic); stored, the planes written
+    # by the leaf kernel and read by the pass, C written once
+    planes = {2: plan.leaves * plan.leaf ** 2 * 4, 3: plan.leaves // 7 * (2 * plan.leaf) ** 2 * 4}.get(plan.combine, 0)
+    combine_bytes = (2 * planes + n * n * 4) if planes else 2 * n * n * 4
+    combine_pass = None
+    if planes:
+        combine_pass = {"kernel": "combine_kernel (ordered pass)", "bound": "hbm", "ms": phases["after_leaf"],
+                        "algorithmic_bytes": planes + n * n * 4,
+                        "achieved_gbs": (planes + n * n * 4) / (phases["after_leaf"] * 1e-3) / 1e9,
+                        "peak_gbs": pk["hbm_gbs"]}
+        combine_pass["frac"] = combine_pass["achieved_gbs"] / pk["hbm_gbs"]
     # the whole path's roofline (phases serialize): leaf flops at the tensor
-    # peak + divide bytes and the clear and final write of C at HBM bandwidth
-    t_roof = leaf_flops / (pk["bf16"] * 1e12) + (divide_bytes + 2 * n * n * 4) / (pk["hbm_gbs"] * 1e9)
+    # peak + divide and combine bytes at HBM bandwidth
+    t_roof = leaf_flops / (pk["bf16"] * 1e12) + (divide_bytes + combine_bytes) / (pk["hbm_gbs"] * 1e9)
     path_roofline = {"t_roof_ms": t_roof * 1e3, "t_ms": ms, "frac": t_roof * 1e3 / ms,
                      "effective_tflops_at_roof": flops / t_roof / 1e12,
                      "effective_over_bf16_peak": value / world / pk["bf16"],
-                     "model": "leaf 3*2*L^3*7^d flops / bf16 burst + (divide bytes + C clear and write) / HBM"}
+                     "model": "leaf 3*2*L^3*7^d flops / bf16 burst + (divide bytes + combine bytes) / HBM; "
+                              "combine bytes: C cleared and written (fused) or planes written, read and C written"}
 
     comparators = None
     if not args.no_comparators and rank == 0:
@@ -725,28 +746,6 @@ def main():
         except Exception as ex:  # report, do not hide
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
-
-    deterministic = None
-    if rank == 0 and not args.no_tf32 and args.combine == 0:
-        # the same product with the deterministic (unfused, ordered) combine
-        plan.set_combine(2)
-        for _ in range(2):
-            plan.mul(A, B, C)
-        plan.check()
-        plan.set_timing(10)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            plan.mul(A, B, C)
-        e1.record()
-        torch.cuda.synchronize()
-        plan.check()
-        msd = e0.elapsed_time(e1) / 10
-        deterministic = {"value": flops / (msd * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": msd,
-                         "phases_ms": plan.phase_ms(),
-                         "note": "leaf epilogue stores M planes, ordered combine pass; bitwise reproducible"}
-        plan.set_timing(0)
-        plan.set_combine(0)
 
     tf32 = None
     if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
@@ -840,11 +839,12 @@ def main():
                                "fp32 divide sums and combine",
                "data": "synthetic",
                "config": dict(workload_config(args, plan.depth), leaves=plan.leaves, leaf=plan.leaf,
-                              tile=list(plan.tile)),
+                              tile=list(plan.tile), combine=plan.combine,
+                              combine_choice="measured per plan" if args.combine == -1 else "given"),
                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
                "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9, "path_roofline": path_roofline,
-               "error_vs_fp64": error, "comparators": comparators, "deterministic_combine": deterministic, "tf32": tf32, "int64": int64,
+               "error_vs_fp64": error, "comparators": comparators, "combine_pass": combine_pass, "tf32": tf32, "int64": int64,
                "batch": batch, "serve": serve, "peel": peel, "traversal": traversal, "depth_sweep": depth_sweep,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)

@@ -76,7 +76,8 @@ typedef struct {
   int64_t workspace_bytes; /* device bytes the plan owns (leaf operands, tables, ...)    */
   int32_t tile_m, tile_n;  /* leaf GEMM output tile                                      */
   int32_t peel;            /* edge rows/columns done classically (STARK_PLAN_PEEL), else 0 */
-  int32_t reserved[5];
+  int32_t combine;         /* combine mode in effect (stark_plan_set_combine)            */
+  int32_t reserved[4];
 } stark_plan_info;
 
 /* ----------------------------------------------------------------- plans */
@@ -208,8 +209,13 @@ STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, con
  * traversal and (3xTF32) the MN-major layout; a product it cannot serve
  * (stark_mul_leaves, another pairing or pipeline) runs the fused path.
  * All modes agree within fp32 rounding (the order of the additions
- * differs).  Errors: EINVAL, EUNSUPPORTED (mode 2 on an fp64/int64 plan or
- * depth > 3; mode 3 outside its conditions), ENOMEM. */
+ * differs).  mode -1 measures: every mode that applies to the plan runs one
+ * warm-up and three timed products on scratch inputs (allocated for the
+ * call), the fastest stays in effect (stark_plan_info.combine) and the
+ * product buffers of the others are released; F64/I64 plans keep mode 0.
+ * Errors: EINVAL, EUNSUPPORTED (mode 2 on an fp64/int64 plan or depth > 3;
+ * mode 3 outside its conditions), ENOMEM, ETIMEOUT (a trial product's
+ * device wait expired). */
 STARK_API stark_status stark_plan_set_combine(stark_plan_t plan, int mode);
 
 /* Leaf launch schedule of the split-fp32 paths (Alg. 4 leaf products), for leaf
@@ -293,6 +299,14 @@ STARK_API stark_status stark_plan_check(stark_plan_t plan, void *stream);
  * recorded. */
 STARK_API stark_status stark_plan_set_timing(stark_plan_t plan, int records);
 STARK_API stark_status stark_plan_phase_ms(stark_plan_t plan, float out_ms[3]);
+
+/* The same means split one step further, `count` (1..4) of: [0] zeroing C,
+ * [1] divide A and B, [2] the leaf-product kernel (with the fused combine,
+ * when it is fused), [3] what follows it: the separate combine pass of
+ * combine modes 2 and 3, the peeled edge and the staging copy into C (near 0
+ * when there is none).  Errors: EINVAL when nothing was recorded or count is
+ * out of range. */
+STARK_API stark_status stark_plan_phases(stark_plan_t plan, float *out_ms, int count);
 
 /* ----------------------------------------------------------------- batches */
 

@@ -310,6 +310,7 @@ stark_status stark_plan_get_info(stark_plan_t p, stark_plan_info* info) {
   info->workspace_bytes = p->ws_bytes;
   info->tile_m = p->is_tc ? 128 : 64;
   info->tile_n = p->is_tc ? p->bn : 64;
+  info->combine = p->combine_mode;
   return STARK_OK;
 }
 
@@ -438,8 +439,11 @@ stark_status stark_mul_host(stark_plan_t p, const void* A, const void* B, void* 
   return stark_plan_check(p, stream);
 }
 
+static stark_status plan_tune_combine(stark_plan_t p);
+
 stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
-  if (!p || mode < 0 || mode > 3) return STARK_EINVAL;
+  if (!p || mode < -1 || mode > 3) return STARK_EINVAL;
+  if (mode == -1) return plan_tune_combine(p);
   if (mode == 3) {
     // sibling fold on the CTA-pair kernel: 256-wide tiles, breadth first
     if (!p->is_tc || p->depth < 1 || p->dfs || p->L % 256 != 0 || (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn))
@@ -471,6 +475,70 @@ stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   }
   p->combine_mode = mode;
   return STARK_OK;
+}
+
+// Measured choice of the combine mode for a tensor-core plan: every mode that
+// applies (0 fused; 2 deterministic at depth <= 3; 3 sibling fold) runs one
+// warm-up and three timed products on scratch inputs, and the fastest stays;
+// the product buffers of the others are released.  Other plans keep mode 0.
+static stark_status plan_tune_combine(stark_plan_t p) {
+  if (!p->is_tc || p->n == 0 || p->dfs) return stark_plan_set_combine(p, 0);
+  const size_t bytes = (size_t)p->n * p->n * p->esz;
+  void *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  stark_status st = STARK_OK;
+  if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&B, bytes) != cudaSuccess ||
+      cudaMalloc(&C, bytes) != cudaSuccess) {
+    st = STARK_ENOMEM;
+  } else if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = STARK_ECUDA;
+  }
+  int best = 0;
+  if (st == STARK_OK) {
+    cudaMemsetAsync(A, 0x3c, bytes, s);  // bounded, nonzero values
+    cudaMemsetAsync(B, 0x3c, bytes, s);
+    float best_ms = 1e30f;
+    for (int mode : {0, 2, 3}) {
+      if (stark_plan_set_combine(p, mode) != STARK_OK) continue;
+      bool ok = plan_run(p, A, B, C, 0, p->P, s) == STARK_OK;
+      ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+      for (int k = 0; k < 3 && ok; ++k) ok = plan_run(p, A, B, C, 0, p->P, s) == STARK_OK;
+      ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0;
+      if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = mode;
+      }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = STARK_ECUDA;
+    int e = 0;  // a device error during the trials is reported, not kept
+    if (cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && e) {
+      cudaMemset(p->d_err, 0, sizeof(int));
+      st = STARK_ETIMEOUT;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C);
+  cudaGetLastError();
+  // keep the winner's buffers only
+  if (best != 2 && p->m_planes) {
+    cudaFree(p->m_planes);
+    p->m_planes = nullptr;
+    p->ws_bytes -= (int64_t)((size_t)p->P * p->L * p->L * sizeof(float));
+  }
+  if (best != 3 && p->q_planes) {
+    cudaFree(p->q_planes);
+    p->q_planes = nullptr;
+    p->ws_bytes -= (int64_t)((size_t)(p->P / 7) * (2 * p->L) * (2 * p->L) * sizeof(float));
+  }
+  p->combine_mode = best;
+  return st;
 }
 
 // Workspace for `planes_per_half` leaves per operand side, with its maps.
@@ -591,7 +659,7 @@ stark_status stark_plan_set_timing(stark_plan_t p, int records) {
   p->ev.clear();
   p->timing_cap = 0;
   p->timing_used = 0;
-  p->ev.resize((size_t)records * 4, nullptr);
+  p->ev.resize((size_t)records * kTimingEvents, nullptr);
   for (auto& e : p->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return STARK_ECUDA;
   p->timing_cap = records;
@@ -599,17 +667,28 @@ stark_status stark_plan_set_timing(stark_plan_t p, int records) {
 }
 
 stark_status stark_plan_phase_ms(stark_plan_t p, float out_ms[3]) {
-  if (!p || !out_ms || p->timing_used == 0) return STARK_EINVAL;
-  if (cudaEventSynchronize(p->ev[(size_t)(p->timing_used - 1) * 4 + 3]) != cudaSuccess) return STARK_ECUDA;
-  double sum[3] = {0, 0, 0};
+  float four[4];
+  const stark_status st = stark_plan_phases(p, four, 4);
+  if (st != STARK_OK) return st;
+  out_ms[0] = four[0];
+  out_ms[1] = four[1];
+  out_ms[2] = four[2] + four[3];  // leaf products with the combine
+  return STARK_OK;
+}
+
+stark_status stark_plan_phases(stark_plan_t p, float* out_ms, int count) {
+  if (!p || !out_ms || count < 1 || count > 4 || p->timing_used == 0) return STARK_EINVAL;
+  const size_t E = kTimingEvents;
+  if (cudaEventSynchronize(p->ev[(size_t)(p->timing_used - 1) * E + E - 1]) != cudaSuccess) return STARK_ECUDA;
+  double sum[4] = {0, 0, 0, 0};
   for (int r = 0; r < p->timing_used; ++r)
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       float ms = 0;
-      if (cudaEventElapsedTime(&ms, p->ev[(size_t)r * 4 + i], p->ev[(size_t)r * 4 + i + 1]) != cudaSuccess)
+      if (cudaEventElapsedTime(&ms, p->ev[(size_t)r * E + i], p->ev[(size_t)r * E + i + 1]) != cudaSuccess)
         return STARK_ECUDA;
       sum[i] += ms;
     }
-  for (int i = 0; i < 3; ++i) out_ms[i] = (float)(sum[i] / p->timing_used);
+  for (int i = 0; i < count; ++i) out_ms[i] = (float)(sum[i] / p->timing_used);
   return STARK_OK;
 }
 
@@ -808,6 +887,13 @@ stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStre
   return plan_divide_top(p, A, B, s, -1);
 }
 
+// The event set of the product being timed (stark_plan_set_timing), or null.
+static cudaEvent_t* plan_timing_events(stark_plan_s* p) {
+  return (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
+             ? &p->ev[(size_t)(p->timing_used - 1) * kTimingEvents]
+             : nullptr;
+}
+
 // Whether leaves [lb, le) use the deterministic combine (stored M planes and
 // an ordered pass) rather than the fused epilogue.
 static bool plan_deterministic(const stark_plan_s* p, int64_t lb, int64_t le) {
@@ -890,6 +976,12 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       st = to_status(launch_leaf_tc(a, a.row_bytes == 64 ? &p->tmA64 : &p->tmA,
                                     a.row_bytes == 64 ? &p->tmB64 : &p->tmB, &tmC, tf32, p->bn, p->num_sms, s));
     }
+    if (st == STARK_OK && (deterministic || sib)) {
+      if (cudaEvent_t* ev = plan_timing_events(p)) {
+        cudaEventRecord(ev[3], s);  // the leaf products end, the combine pass starts
+        p->timing_leaf_marked = true;
+      }
+    }
     if (st == STARK_OK && deterministic)
       st = to_status(launch_combine(static_cast<const float*>(p->m_planes), p->depth, p->L, p->npad, core_side(p),
                                     static_cast<float*>(C), p->n, s));
@@ -971,9 +1063,7 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
   if (p->n == 0) return STARK_OK;
   if (!A || !B || !C) return STARK_EINVAL;
   if (!p->X || !p->Y) return STARK_ENOMEM;  // a failed workspace reallocation left none
-  cudaEvent_t* ev = (p->timing_used > 0 && p->timing_used <= p->timing_cap && p->timing_active)
-                        ? &p->ev[(size_t)(p->timing_used - 1) * 4]
-                        : nullptr;
+  cudaEvent_t* ev = plan_timing_events(p);
   if (ev) cudaEventRecord(ev[1], s);
   stark_status st = STARK_OK;
   if (!p->dfs) {
@@ -981,6 +1071,10 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
     if (st != STARK_OK) return st;
     if (ev) cudaEventRecord(ev[2], s);
     st = plan_leaves(p, C, lb, le, 0, s);
+    if (ev && !p->timing_leaf_marked) {  // fused: the leaf kernel ends here
+      cudaEventRecord(ev[3], s);
+      p->timing_leaf_marked = true;
+    }
   } else {
     // depth-first over the top p->dfs levels: one subtree's operands at a
     // time (divide and leaves interleave; the phase timer reports them
@@ -1005,8 +1099,10 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
   if (st == STARK_OK && p->peel > 0 && lb == 0)
     st = plan_border(p, A, B, staged ? p->cstage : C, staged ? staged_ld(p->n) : p->n, plan_stored(p, lb, le), s);
   if (st == STARK_OK && staged) st = plan_copy_cstage(p, C, s);
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev && !p->timing_leaf_marked) cudaEventRecord(ev[3], s);  // depth first: one interleaved phase
+  if (ev) cudaEventRecord(ev[4], s);
   p->timing_active = false;
+  p->timing_leaf_marked = false;
   return st;
 }
 
@@ -1015,7 +1111,7 @@ stark_status plan_run(stark_plan_s* p, const void* A, const void* B, void* C, in
   if (p->n == 0) return STARK_OK;
   if (!A || !B || !C) return STARK_EINVAL;
   if (p->timing_used < p->timing_cap) {
-    cudaEventRecord(p->ev[(size_t)p->timing_used * 4], s);
+    cudaEventRecord(p->ev[(size_t)p->timing_used * kTimingEvents], s);
     ++p->timing_used;
     p->timing_active = true;
   }

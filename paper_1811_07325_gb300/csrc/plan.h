@@ -12,6 +12,7 @@
 namespace stark {
 
 constexpr int kMaxDepth = 4;
+constexpr int kTimingEvents = 5;  // per timed product (see stark_plan_s::ev)
 constexpr uint64_t kDefaultTimeoutNs = 4000000000ull;  // 4 s per bounded device wait
 
 int64_t pow7i(int d);
@@ -93,7 +94,9 @@ struct stark_plan_s {
   int timing_cap = 0;
   int timing_used = 0;
   bool timing_active = false;  // the current product records events
-  std::vector<cudaEvent_t> ev;  // 4 per recorded product
+  bool timing_leaf_marked = false;  // the current product recorded the end of its leaf kernel
+  std::vector<cudaEvent_t> ev;  // kTimingEvents per recorded product: start, after zeroing C,
+                                // after the divide, after the leaf kernel, end
 };
 
 namespace stark {

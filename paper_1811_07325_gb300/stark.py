@@ -49,7 +49,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("leaf", ctypes.c_int64),
                 ("depth", ctypes.c_int32), ("dtype", ctypes.c_int32), ("leaves", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("peel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("peel", ctypes.c_int32), ("combine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class ErrorReport(ctypes.Structure):
@@ -81,6 +81,7 @@ _SIGS = {
     "stark_plan_set_traversal": ([_vp, _ci], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
+    "stark_plan_phases": ([_vp, ctypes.POINTER(ctypes.c_float), _ci], _ci),
     "stark_quadrant_table": ([_ci, _ci, _vp, _vp, _vp], _ci),
     "stark_strerror": ([_ci], ctypes.c_char_p),
     "stark_selftest_bounded_wait": ([ctypes.c_uint64], _ci),
@@ -173,6 +174,7 @@ class Plan:
         self.leaves, self.workspace_bytes = info.leaves, info.workspace_bytes
         self.tile = (info.tile_m, info.tile_n)
         self.peel = info.peel
+        self.combine = info.combine
 
     def close(self):
         if getattr(self, "_h", None):
@@ -279,8 +281,11 @@ class Plan:
         """0: fused, TMA bulk reductions (default); 1: fused, vector atomics;
         2: deterministic (stored leaf products, ordered combine pass);
         3: sibling fold (parent products folded in L2, ordered pass one
-        level up)."""
+        level up); -1: the fastest of those that apply, measured."""
         _check(_lib.stark_plan_set_combine(self._h, int(mode)), "stark_plan_set_combine")
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
+        self.combine, self.workspace_bytes = info.combine, info.workspace_bytes
 
     def set_pairing(self, mode):
         """Leaf schedule of the split-fp32 paths: 0 single CTAs; 2 (default)
@@ -324,10 +329,15 @@ class Plan:
         _check(_lib.stark_plan_set_timing(self._h, int(records)), "stark_plan_set_timing")
 
     def phase_ms(self):
-        """Mean per-phase device time (ms) over the recorded products."""
-        out = (ctypes.c_float * 3)()
-        _check(_lib.stark_plan_phase_ms(self._h, out), "stark_plan_phase_ms")
-        return {"zero_c": out[0], "divide": out[1], "leaf_combine": out[2]}
+        """Mean per-phase device time (ms) over the recorded products:
+        zeroing C, the divide, the leaf products with the combine, and that
+        last phase split into the leaf kernel and what follows it (the
+        separate combine pass of combine modes 2 and 3, peeled edge,
+        staging copy)."""
+        out = (ctypes.c_float * 4)()
+        _check(_lib.stark_plan_phases(self._h, out, 4), "stark_plan_phases")
+        return {"zero_c": out[0], "divide": out[1], "leaf_combine": out[2] + out[3], "leaf_kernel": out[2],
+                "after_leaf": out[3]}
 
 
 class Batch:

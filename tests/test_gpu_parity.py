@@ -700,6 +700,33 @@ def test_sibling_fold_matches_oracle(S, dtype, n, d):
     assert np.abs(C1 - Cf).max() <= 1e-5 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("dtype,n,d", [("F32_SPLIT_BF16", 2048, 2), ("F32_SPLIT_BF16", 777, 1), ("F64", 512, 2)])
+def test_measured_combine_choice(S, dtype, n, d):
+    # mode -1 keeps the fastest applicable mode (fp64: the fused one), and
+    # the product stays within its bounds; the phase split is consistent
+    A = synth.normal(n, 68, 0) if dtype != "F64" else synth.uniform(n, 68, 0)
+    B = synth.normal(n, 68, 1) if dtype != "F64" else synth.uniform(n, 68, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        ws0 = p.workspace_bytes
+        p.set_combine(-1)
+        assert p.combine in ((0, 2, 3) if dtype != "F64" else (0,))
+        if p.combine == 0:
+            assert p.workspace_bytes == ws0  # the losers' product planes were released
+        p.set_timing(2)
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        p.check()
+        ph = p.phase_ms()
+        assert ph["leaf_kernel"] > 0 and ph["after_leaf"] >= 0
+        assert abs(ph["leaf_combine"] - ph["leaf_kernel"] - ph["after_leaf"]) < 1e-3
+    if dtype == "F64":
+        assert np.abs(C - want).max() / (an * bn) <= 1e-12
+    else:
+        check_split(C, want, an, bn, dtype, L=p.leaf)
+
+
 def test_sibling_fold_conditions_and_fallbacks(S):
     n = 1024
     A = synth.normal(n, 67, 0)
