@@ -462,6 +462,76 @@ def run_serve(args, stark, synth, torch):
             "cached_workspaces": stats["cached_workspaces"], "workspace_bytes": stats["owned_bytes"]}
 
 
+def run_sharded(args, stark, synth, torch, dist, rank, world, local):
+    """--shard: ONE n x n product split over the ranks (the paper's setting,
+    Sec. III-C / V-F): every rank holds A and B, a plan restricted to its
+    balanced leaf range (its own subtrees' divide and workspace), computes
+    its partial C, and one NCCL sum reduce-scatter leaves it its block of
+    rows of C.  A step is the whole product (local leaves + the exchange);
+    value = 2 n^3 / the slowest rank's time ("scaling": "strong")."""
+    from paper_1811_07325_gb300 import shard
+    n, d = args.n, args.depth
+    dt = stark.DType.F32_SPLIT_BF16 if args.dtype == "bf16" else stark.DType.F32_SPLIT_TF32
+    A = torch.from_numpy(synth.normal(n, args.seed, 0)).cuda()
+    B = torch.from_numpy(synth.normal(n, args.seed, 1)).cuda()
+    plan = shard.shard_plan(n, d, dt, world, rank)
+    b, e = getattr(plan, "shard", None) or (0, plan.leaves)
+
+    def step():
+        if dist is None:
+            return 0, n, plan.mul_leaves(A, B, b, e)
+        return shard.mul_sharded_rows(plan, A, B)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        r0, r1, rows = step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    plan.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    error = None
+    if rank == 0 and not args.no_check and r1 > r0:
+        import oracle
+        idx = np.unique(synth.sample_rows(r1 - r0, min(64, r1 - r0), args.seed + 5))
+        Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+        want = oracle.gemm_rows(Ah, Bh, idx + r0)
+        absprod = oracle.gemm_rows(np.abs(Ah), np.abs(Bh), idx + r0)
+        got = rows[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+        an = float(torch.linalg.vector_norm(A.double()).item())
+        bn = float(torch.linalg.vector_norm(B.double()).item())
+        error = dict(error_vs_fp64(got, want, absprod, an, bn), rows_checked=int(idx.size))
+    flops = 2.0 * n ** 3
+    return {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"strassen n={n} depth={d} fp32 N(0,1) split-{args.dtype}, one product "
+                                   f"sharded over {world} ranks (leaf ranges, NCCL reduce-scatter of C rows)",
+                       "n": n, "depth": d, "leaves": plan.leaves, "rank0_leaves": [b, e],
+                       "rank0_workspace_bytes": plan.workspace_bytes, "collective": "reduce_scatter" if world > 1
+                       else "none (one rank)"},
+            "clocks": clocks, "error_vs_fp64": error, "e2e": None,
+            "note": "strong scaling of one product; the default bench line runs independent products per rank"}
+
+
 def workload_config(args, depth):
     n = args.n
     return {"workload": f"strassen n={n} depth={depth} fp32 N(0,1) split-{args.dtype}", "n": n, "depth": depth,
@@ -535,6 +605,8 @@ def main():
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
     ap.add_argument("--traversal", type=int, default=0, help="k > 0: depth first over the top k levels")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="one product sharded over the ranks: leaf ranges + NCCL reduce-scatter (strong scaling)")
     ap.add_argument("--no-oracle-timings", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=600)
@@ -560,6 +632,13 @@ def main():
 
     n, d = args.n, args.depth
     dt = stark.DType.F32_SPLIT_BF16 if args.dtype == "bf16" else stark.DType.F32_SPLIT_TF32
+    if args.shard:
+        out = run_sharded(args, stark, synth, torch, dist, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     seed = args.seed + 7919 * rank  # independent product per rank
     A_h = torch.from_numpy(synth.normal(n, seed, 0)).pin_memory()
     B_h = torch.from_numpy(synth.normal(n, seed, 1)).pin_memory()

@@ -77,7 +77,11 @@ typedef struct {
   int32_t tile_m, tile_n;  /* leaf GEMM output tile                                      */
   int32_t peel;            /* edge rows/columns done classically (STARK_PLAN_PEEL), else 0 */
   int32_t combine;         /* combine mode in effect (stark_plan_set_combine)            */
-  int32_t reserved[4];
+  int32_t shard_levels;    /* stark_plan_set_shard: top levels above the shard's subtrees (0: none) */
+  int32_t shard_first;     /* first leaf whose operands the shard's workspace holds     */
+  int32_t workspace_leaves;/* leaves whose operands the workspace holds (all of them, one  */
+                           /* depth-first subtree's, or a shard's subtrees')               */
+  int32_t reserved[1];
 } stark_plan_info;
 
 /* ----------------------------------------------------------------- plans */
@@ -184,7 +188,10 @@ STARK_API stark_status stark_mul_leaves(stark_plan_t plan, const void *A, const 
  * (hi planes, then lo planes; bf16 values, or TF32 values in fp32
  * containers); F64/I64 hold [leaves][L][L].  Every plane is row-major: A
  * planes are the leaf's M x K operand, B planes its K x N operand, except
- * for F32_SPLIT_TF32 whose B planes are stored transposed (N x K).  The
+ * for F32_SPLIT_TF32 with the K-major layout (stark_plan_set_tf32_layout 0),
+ * whose B planes are stored transposed (N x K).  A plan restricted by
+ * stark_plan_set_shard holds the operands of its subtrees' leaves only
+ * (stark_plan_info.workspace_leaves of them, from leaf shard_first on).  The
  * pointers stay valid until the plan is destroyed and are overwritten by the
  * next product. */
 STARK_API stark_status stark_plan_operands(stark_plan_t plan, const void *A, const void *B, void *stream, const void **X,
@@ -268,6 +275,23 @@ STARK_API stark_status stark_plan_set_pipeline(stark_plan_t plan, int deep);
  * 2 on an F64/I64 plan, or the deterministic combine mode), ENOMEM, ECUDA.
  * stark_plan_operands is not available in depth-first mode. */
 STARK_API stark_status stark_plan_set_traversal(stark_plan_t plan, int levels);
+
+/* Restrict the plan to the leaves [leaf_begin, leaf_end) of its recursion
+ * tree, for sharding one product across devices (Stark runs the leaf
+ * products as independent tasks spread over the cluster, Sec. III-C, Alg. 4;
+ * its strong scaling over executors is Sec. V-F).  The workspace is
+ * reallocated to hold only the operands of the subtrees below the top 2
+ * recursion levels (1 for F64/I64) that contain those leaves, and
+ * stark_mul_leaves on any sub-range of [leaf_begin, leaf_end) divides only
+ * those subtrees (A and B read through the operand sums of the levels
+ * above, formed on the fly as in the depth-first traversal) before its leaf
+ * launch: a rank's divide work and workspace shrink with its share.
+ * stark_mul on a restricted plan returns EINVAL (it is not the whole
+ * product); [0, leaves) lifts the restriction.  Summing the partial C of
+ * shards that partition [0, leaves) gives A*B.  Errors: EINVAL (empty or
+ * out-of-range leaves), EUNSUPPORTED (depth > 3, depth 0, a depth-first
+ * traversal, the K-major 3xTF32 layout), ENOMEM. */
+STARK_API stark_status stark_plan_set_shard(stark_plan_t plan, int64_t leaf_begin, int64_t leaf_end);
 
 /* Exact integer leaves on the tensor cores for an I64 plan whose inputs
  * satisfy |A_ij|, |B_ij| <= max_abs (the exact integer path;

@@ -12,6 +12,10 @@ Functions (each cites what it follows; see ``stark_oracle.c``):
                                    (int64 wraps modulo 2^64).
 * ``gemm_rows(A, B, rows)``     -- selected rows of the same product, in float64.
 * ``strassen(A, B, depth)``     -- Alg. 1 recursion, C22 with +M3.
+* ``strassen_abs(A, B, depth)``  -- the error majorant: Alg. 1 on |A|, |B|
+                                   with every sign +, so |dC| <= e * S for
+                                   a relative error e per leaf product and
+                                   addition.
 * ``strassen_operands(X, npad, depth, side)`` -- the divide phase: every leaf's
                                    fp32 operand sum (Alg. 1 / Alg. 3).
 * ``split_bf16(x)``, ``split_tf32(x)`` -- hi = RN(x), lo = RN(x - hi) in the
@@ -61,6 +65,8 @@ def _load():
             lib.oracle_strassen_f64.restype = ci
             lib.oracle_strassen_i64.argtypes = [i64, ci, vp, vp, vp]
             lib.oracle_strassen_i64.restype = ci
+            lib.oracle_strassen_abs_f64.argtypes = [i64, ci, vp, vp, vp]
+            lib.oracle_strassen_abs_f64.restype = ci
             lib.oracle_strassen_operands_f32.argtypes = [i64, i64, ci, vp, ci, vp]
             lib.oracle_strassen_operands_f32.restype = ci
             lib.oracle_split_bf16.argtypes = [i64, vp, vp, vp]
@@ -128,6 +134,17 @@ def strassen(A: np.ndarray, B: np.ndarray, depth: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle strassen rejected its arguments")
     return C
+
+
+def strassen_abs(A: np.ndarray, B: np.ndarray, depth: int) -> np.ndarray:
+    """Error majorant S of Alg. 1 with ``depth`` levels: the recursion on
+    |A| and |B| with every coefficient +1 (float64)."""
+    lib = _load()
+    A, B = _square(A, np.float64), _square(B, np.float64)
+    S = np.empty_like(A)
+    if lib.oracle_strassen_abs_f64(A.shape[0], depth, _p(A), _p(B), _p(S)) != 0:
+        raise ValueError("oracle strassen_abs rejected its arguments")
+    return S
 
 
 def strassen_operands(X: np.ndarray, npad: int, depth: int, side: str) -> np.ndarray:

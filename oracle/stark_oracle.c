@@ -21,6 +21,14 @@
  *                                     at the leaves.  C22 uses +M3 (the printed
  *                                     -M3 is a sign typo: only +M3 makes the
  *                                     identity equal A*B).
+ *   oracle_strassen_abs_f64           Alg. 1 with every input entry and every
+ *                                     +-1 coefficient of its sums and of its
+ *                                     combine replaced by its absolute value:
+ *                                     the majorant S of the recursion's
+ *                                     rounding errors (each leaf term
+ *                                     a_ik b_kj enters S_ij with weight 1), so
+ *                                     a relative error e per leaf product or
+ *                                     addition bounds |dC_ij| by about e S_ij.
  *   oracle_strassen_operands_f32      the divide phase of Alg. 1 / Alg. 3
  *                                     (Sec. III-C): the leaf operand sums of
  *                                     all 7^depth leaves, each level forming
@@ -155,8 +163,11 @@ static void uadd(int64_t m, uview x, uview y, int s, uview out)
         }
 }
 
+/* Leaf products, rows spread over OpenMP threads (each row of C is one
+ * thread's, k ascending: the same arithmetic as one thread). */
 static void dclassical(int64_t m, dview A, dview B, dview C)
 {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         for (int64_t j = 0; j < m; ++j) C.p[i * C.ld + j] = 0.0;
         for (int64_t k = 0; k < m; ++k) {
@@ -167,6 +178,7 @@ static void dclassical(int64_t m, dview A, dview B, dview C)
 }
 static void uclassical(int64_t m, uview A, uview B, uview C)
 {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         for (int64_t j = 0; j < m; ++j) C.p[i * C.ld + j] = 0;
         for (int64_t k = 0; k < m; ++k) {
@@ -237,6 +249,42 @@ static void ustrassen(int64_t m, int level, uview A, uview B, uview C)
     free(S.p); free(T.p);
 }
 
+/* The error majorant: Alg. 1's recursion on |A| and |B| with all signs +
+ * (the operand sums of M1..M7 and the four combines add absolute values).
+ * A and B are already nonnegative here. */
+static void dstrassen_abs(int64_t m, int level, dview A, dview B, dview C)
+{
+    if (level == 0) { dclassical(m, A, B, C); return; }
+    const int64_t h = m / 2;
+    dview A11 = dsub(A, h, 0, 0), A12 = dsub(A, h, 0, 1), A21 = dsub(A, h, 1, 0), A22 = dsub(A, h, 1, 1);
+    dview B11 = dsub(B, h, 0, 0), B12 = dsub(B, h, 0, 1), B21 = dsub(B, h, 1, 0), B22 = dsub(B, h, 1, 1);
+    dview S = dalloc(h), T = dalloc(h);
+    dview M[7];
+    for (int i = 0; i < 7; ++i) M[i] = dalloc(h);
+    /* |M1| <= (|A11| + |A22|)(|B11| + |B22|) */
+    dadd(h, A11, A22, +1, S); dadd(h, B11, B22, +1, T); dstrassen_abs(h, level - 1, S, T, M[0]);
+    /* |M2| <= (|A21| + |A22|) |B11| */
+    dadd(h, A21, A22, +1, S); dstrassen_abs(h, level - 1, S, B11, M[1]);
+    /* |M3| <= |A11| (|B12| + |B22|) */
+    dadd(h, B12, B22, +1, T); dstrassen_abs(h, level - 1, A11, T, M[2]);
+    /* |M4| <= |A22| (|B21| + |B11|) */
+    dadd(h, B21, B11, +1, T); dstrassen_abs(h, level - 1, A22, T, M[3]);
+    /* |M5| <= (|A11| + |A12|) |B22| */
+    dadd(h, A11, A12, +1, S); dstrassen_abs(h, level - 1, S, B22, M[4]);
+    /* |M6| <= (|A21| + |A11|)(|B11| + |B12|) */
+    dadd(h, A21, A11, +1, S); dadd(h, B11, B12, +1, T); dstrassen_abs(h, level - 1, S, T, M[5]);
+    /* |M7| <= (|A12| + |A22|)(|B21| + |B22|) */
+    dadd(h, A12, A22, +1, S); dadd(h, B21, B22, +1, T); dstrassen_abs(h, level - 1, S, T, M[6]);
+    /* C11: M1 M4 M5 M7, C12: M3 M5, C21: M2 M4, C22: M1 M2 M3 M6, all added */
+    dview C11 = dsub(C, h, 0, 0), C12 = dsub(C, h, 0, 1), C21 = dsub(C, h, 1, 0), C22 = dsub(C, h, 1, 1);
+    dadd(h, M[0], M[3], +1, C11); dadd(h, C11, M[4], +1, C11); dadd(h, C11, M[6], +1, C11);
+    dadd(h, M[2], M[4], +1, C12);
+    dadd(h, M[1], M[3], +1, C21);
+    dadd(h, M[0], M[1], +1, C22); dadd(h, C22, M[2], +1, C22); dadd(h, C22, M[5], +1, C22);
+    for (int i = 0; i < 7; ++i) free(M[i].p);
+    free(S.p); free(T.p);
+}
+
 /* Pad an n x n matrix with zeros to m x m (m >= n).  Alg. 1 is stated for
  * n = 2^p; other sizes are embedded in a zero-padded square whose side is a
  * multiple of 2^depth, and the top-left n x n block of the product is kept. */
@@ -269,6 +317,25 @@ int oracle_strassen_f64(int64_t n, int depth, const double *A, const double *B, 
     dstrassen(m, depth, a, b, c);
     for (int64_t i = 0; i < n; ++i) memcpy(C + i * n, Cp + i * m, (size_t)n * sizeof(double));
     free(Ap); free(Bp); free(Cp);
+    return 0;
+}
+
+/* S = the error majorant of Alg. 1 with `depth` levels on |A|, |B| (zero
+ * padding as oracle_strassen_f64).  Returns 0, or -1 on bad arguments. */
+int oracle_strassen_abs_f64(int64_t n, int depth, const double *A, const double *B, double *S)
+{
+    if (n < 0 || depth < 0 || depth > 12) return -1;
+    if (n == 0) return 0;
+    const int64_t m = padded_side(n, depth);
+    double *Ap = (double *)pad_copy(n, m, A, sizeof(double));
+    double *Bp = (double *)pad_copy(n, m, B, sizeof(double));
+    double *Sp = (double *)calloc((size_t)(m * m), sizeof(double));
+    if (!Ap || !Bp || !Sp) { free(Ap); free(Bp); free(Sp); return -1; }
+    for (int64_t i = 0; i < m * m; ++i) { Ap[i] = fabs(Ap[i]); Bp[i] = fabs(Bp[i]); }
+    dview a = { Ap, m }, b = { Bp, m }, c = { Sp, m };
+    dstrassen_abs(m, depth, a, b, c);
+    for (int64_t i = 0; i < n; ++i) memcpy(S + i * n, Sp + i * m, (size_t)n * sizeof(double));
+    free(Ap); free(Bp); free(Sp);
     return 0;
 }
 

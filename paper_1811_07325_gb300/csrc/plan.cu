@@ -311,6 +311,9 @@ stark_status stark_plan_get_info(stark_plan_t p, stark_plan_info* info) {
   info->tile_m = p->is_tc ? 128 : 64;
   info->tile_n = p->is_tc ? p->bn : 64;
   info->combine = p->combine_mode;
+  info->shard_levels = p->shard_levels;
+  info->shard_first = (int32_t)p->shard_first;
+  info->workspace_leaves = (int32_t)p->P_ws;
   return STARK_OK;
 }
 
@@ -587,6 +590,7 @@ static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
 
 stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
   if (!p || levels < 0 || levels > 2) return STARK_EINVAL;
+  if (levels && p->shard_levels) return STARK_EUNSUPPORTED;  // a shard keeps its own workspace
   if (!traversal_supported(p->depth, p->dt, levels) || (levels && p->combine_mode >= 2)) return STARK_EUNSUPPORTED;
   if (levels == p->dfs || p->n == 0) {
     p->dfs = levels;
@@ -598,6 +602,35 @@ stark_status stark_plan_set_traversal(stark_plan_t p, int levels) {
   // plan keeps its previous one)
   p->dfs = p->P_ws == p->P / pow7i(levels) ? levels : prev;
   return st;
+}
+
+stark_status stark_plan_set_shard(stark_plan_t p, int64_t lb, int64_t le) {
+  if (!p || lb < 0 || le > p->P || lb >= le) return STARK_EINVAL;
+  if (p->dfs) return STARK_EUNSUPPORTED;
+  if (lb == 0 && le == p->P) {  // the whole product: breadth first, full workspace
+    const stark_status st = p->shard_levels && p->n > 0 ? plan_alloc_operands(p, p->P) : STARK_OK;
+    if (st == STARK_OK) {
+      p->shard_levels = 0;
+      p->shard_lb = 0;
+      p->shard_le = p->P;
+      p->shard_first = 0;
+    }
+    return st;
+  }
+  // subtrees below two top levels where the loaders have them, else one
+  const int k = traversal_supported(p->depth, p->dt, 2) ? 2 : traversal_supported(p->depth, p->dt, 1) ? 1 : 0;
+  if (k == 0 || (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn)) return STARK_EUNSUPPORTED;
+  const int64_t gs = pow7i(p->depth - k);
+  const int64_t g0 = lb / gs, g1 = (le + gs - 1) / gs;
+  if (p->n > 0) {
+    const stark_status st = plan_alloc_operands(p, (g1 - g0) * gs);
+    if (st != STARK_OK) return st;
+  }
+  p->shard_levels = k;
+  p->shard_lb = lb;
+  p->shard_le = le;
+  p->shard_first = g0 * gs;
+  return STARK_OK;
 }
 
 stark_status stark_plan_set_input_bound(stark_plan_t p, int64_t max_abs) {
@@ -833,22 +866,28 @@ static stark_status to_status(cudaError_t e) {
 // Divide phase into the workspace.  top < 0: every leaf operand (breadth
 // first); top = i1: only the subtree below top-level product M_{i1+1}
 // (depth-first traversal), its leaves in planes 0..7^(d-1)-1.
-stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top) {
+stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int top, int levels,
+                             int64_t plane_off) {
   if (!p->X || !p->Y) return STARK_ENOMEM;  // no workspace (failed reallocation)
-  // depth first: the subtree below p->dfs levels along the M-index path `top`
-  const int64_t npad = top >= 0 ? p->npad >> p->dfs : p->npad;
-  const int depth = top >= 0 ? p->depth - p->dfs : p->depth;
+  // depth first: the subtree below `levels` top levels along the M-index path `top`
+  const int lv = top >= 0 ? levels : 0;
+  const int64_t npad = p->npad >> lv;
+  const int depth = p->depth - lv;
+  // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
+  // integers, tf32 in fp32 containers, else the input type
+  const size_t ehi = (p->dt == STARK_F32_SPLIT_BF16 || p->int_tc) ? 2 : p->dt == STARK_F32_SPLIT_TF32 ? 4 : 8;
+  const size_t off = (size_t)plane_off * (size_t)p->L * p->L * ehi;  // first output plane
   // the core of A and B (all of them unless an edge is peeled), row stride n
-  DivideArgs da{A, core_side(p), npad, p->L, p->X, nullptr, p->d_err, top, p->n};
-  DivideArgs db{B, core_side(p), npad, p->L, p->Y, nullptr, p->d_err, top, p->n};
-  da.top_levels = db.top_levels = top >= 0 ? p->dfs : 0;
+  DivideArgs da{A, core_side(p), npad, p->L, static_cast<char*>(p->X) + off, nullptr, p->d_err, top, p->n};
+  DivideArgs db{B, core_side(p), npad, p->L, static_cast<char*>(p->Y) + off, nullptr, p->d_err, top, p->n};
+  da.top_levels = db.top_levels = lv;
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
   OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
   if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
   if (p->is_tc) {
     const int64_t half = p->P_ws * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
-    da.out_lo = static_cast<char*>(p->X) + half;
-    db.out_lo = static_cast<char*>(p->Y) + half;
+    da.out_lo = static_cast<char*>(p->X) + half + off;
+    db.out_lo = static_cast<char*>(p->Y) + half + off;
   }
   stark_status st = STARK_OK;
   if (top < 0 && depth == 3) {
@@ -857,9 +896,6 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     // to its block of 7^(d-1) planes (the outer-prefix form of the deep
     // kernel keeps too few loads in flight to stream at HBM bandwidth)
     const int64_t sub = pow7i(depth - 1);
-    // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
-    // integers, tf32 in fp32 containers, else the input type
-    const size_t ehi = (p->dt == STARK_F32_SPLIT_BF16 || p->int_tc) ? 2 : p->dt == STARK_F32_SPLIT_TF32 ? 4 : 8;
     const size_t plane = (size_t)p->L * p->L * ehi;
     for (int t = 0; t < 7 && st == STARK_OK; ++t) {
       for (int side = 0; side < 2 && st == STARK_OK; ++side) {
@@ -882,9 +918,21 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
   return st;
 }
 
+// Divide of a shard's subtrees that hold leaves [lb, le) (stark_plan_set_shard).
+static stark_status plan_divide_shard(stark_plan_s* p, const void* A, const void* B, cudaStream_t s, int64_t lb,
+                                      int64_t le) {
+  const int k = p->shard_levels;
+  const int64_t gs = pow7i(p->depth - k);
+  stark_status st = STARK_OK;
+  for (int64_t g = lb / gs; g * gs < le && st == STARK_OK; ++g)
+    st = plan_divide_top(p, A, B, s, (int)g, k, g * gs - p->shard_first);
+  return st;
+}
+
 stark_status plan_divide(stark_plan_s* p, const void* A, const void* B, cudaStream_t s) {
   if (p->dfs) return STARK_EUNSUPPORTED;  // the workspace holds one subtree only
-  return plan_divide_top(p, A, B, s, -1);
+  if (p->shard_levels) return plan_divide_shard(p, A, B, s, p->shard_lb, p->shard_le);
+  return plan_divide_top(p, A, B, s, -1, 0, 0);
 }
 
 // The event set of the product being timed (stark_plan_set_timing), or null.
@@ -1066,8 +1114,24 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
   cudaEvent_t* ev = plan_timing_events(p);
   if (ev) cudaEventRecord(ev[1], s);
   stark_status st = STARK_OK;
-  if (!p->dfs) {
-    st = plan_divide_top(p, A, B, s, -1);
+  if (lb == le) {
+    // no leaves: C keeps what the caller put there (the peeled edge below
+    // still belongs to the range that starts at leaf 0)
+    if (ev) cudaEventRecord(ev[2], s);
+  } else if (p->shard_levels) {
+    // a shard: divide only the subtrees holding leaves [lb, le), whose
+    // operands fill the workspace from leaf shard_first on
+    if (lb < p->shard_lb || le > p->shard_le) return STARK_EINVAL;
+    st = plan_divide_shard(p, A, B, s, lb, le);
+    if (st != STARK_OK) return st;
+    if (ev) cudaEventRecord(ev[2], s);
+    st = plan_leaves(p, C, lb, le, p->shard_first, s);
+    if (ev && !p->timing_leaf_marked) {
+      cudaEventRecord(ev[3], s);
+      p->timing_leaf_marked = true;
+    }
+  } else if (!p->dfs) {
+    st = plan_divide_top(p, A, B, s, -1, 0, 0);
     if (st != STARK_OK) return st;
     if (ev) cudaEventRecord(ev[2], s);
     st = plan_leaves(p, C, lb, le, 0, s);
@@ -1088,7 +1152,7 @@ stark_status plan_run_accumulate(stark_plan_s* p, const void* A, const void* B, 
       const int64_t b0 = top * p->P_ws, b1 = b0 + p->P_ws;
       const int64_t lo = lb > b0 ? lb : b0, hi = le < b1 ? le : b1;
       if (lo >= hi) continue;
-      st = plan_divide_top(p, A, B, s, top);
+      st = plan_divide_top(p, A, B, s, top, p->dfs, 0);
       if (st == STARK_OK) st = plan_leaves(p, C, lo, hi, b0, s);
     }
   }
@@ -1153,6 +1217,7 @@ stark_status plan_copy_cstage(const stark_plan_s* p, void* C, cudaStream_t s) {
 extern "C" stark_status stark_plan_set_tf32_layout(stark_plan_t p, int mn) {
   if (!p || mn < 0 || mn > 1) return STARK_EINVAL;
   if (p->dt != STARK_F32_SPLIT_TF32) return mn ? STARK_EUNSUPPORTED : STARK_OK;
+  if (!mn && p->shard_levels) return STARK_EUNSUPPORTED;  // a shard's planes are transposed by group
   if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
   p->tf32_mn = mn;
   return plan_operand_maps(p, p->P_ws);

@@ -85,6 +85,11 @@ struct stark_plan_s {
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   int host_calls = 0;
   int64_t peel = 0;           // edge rows/columns done classically (n = core + peel)
+  // leaf-range shard (stark_plan_set_shard): the workspace holds the operands
+  // of the subtrees below shard_levels top levels that cover leaves
+  // [shard_lb, shard_le); workspace plane 0 is leaf shard_first
+  int shard_levels = 0;  // 0: no shard (every leaf's operands, or depth first)
+  int64_t shard_lb = 0, shard_le = 0, shard_first = 0;
   int pend_set = -1;          // staging set whose copy out is not yet enqueued
   void* pend_C = nullptr;     // its host destination
   // staging copy of C (row pitch staged_ld(n)) for the tensor-core combine

@@ -1,12 +1,15 @@
 """Sharding one product across devices by leaves.
 
 The 7^d leaf products of one recursion tree are independent (the paper runs
-them as parallel tasks, Sec. III-C and Alg. 4); each rank computes the leaves
-of its share with ``stark_mul_leaves`` (its partial C is the sum of those
-leaves' signed combine contributions), and one sum all-reduce over the ranks
-gives every rank C = A.B (``mul_sharded``), or one sum reduce-scatter gives
-each rank its block of rows of C (``mul_sharded_rows``).  That reduction is
-the only exchange the path has.
+them as parallel tasks, Sec. III-C and Alg. 4, and measures strong scaling
+over executors, Sec. V-F).  Each rank takes a balanced contiguous range of
+leaves (``leaf_range``) and a plan restricted to it (``shard_plan``: the
+workspace and the divide cover only the subtrees holding those leaves), and
+computes its partial C (the sum of its leaves' signed combine
+contributions) with ``stark_mul_leaves``.  One sum reduce-scatter gives each
+rank its block of rows of C = A.B (``mul_sharded_rows``, the default), or
+one sum all-reduce gives every rank all of C (``mul_sharded``).  That
+reduction is the only exchange the path has.
 
 Argument marshalling only: the products run in libstark.so; the reduction
 is torch.distributed's (NCCL on GPUs).
@@ -24,6 +27,23 @@ def leaf_range(leaves: int, world: int, rank: int) -> tuple[int, int]:
     return begin, begin + base + (1 if rank < extra else 0)
 
 
+def shard_plan(n: int, depth: int, dtype, world: int, rank: int):
+    """A plan for this rank's leaves of an n x n product at ``depth``
+    (``stark_plan_set_shard`` on ``leaf_range``), or a whole plan when the
+    rank's range is everything (one rank) or empty."""
+    from . import stark
+    p = stark.Plan(n, depth, dtype)
+    begin, end = leaf_range(p.leaves, world, rank)
+    if begin < end and (begin, end) != (0, p.leaves):
+        p.set_shard(begin, end)
+    return p
+
+
+def _rank_leaves(plan, world, rank):
+    shard = getattr(plan, "shard", None)
+    return shard if shard is not None else leaf_range(plan.leaves, world, rank)
+
+
 def mul_sharded(plan, A, B, C, group=None, stream=None):
     """C = A @ B on every rank of ``group``: local leaves, then one sum all-reduce.
 
@@ -32,7 +52,7 @@ def mul_sharded(plan, A, B, C, group=None, stream=None):
     import torch.distributed as dist
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
-    begin, end = leaf_range(plan.leaves, world, rank)
+    begin, end = _rank_leaves(plan, world, rank)
     plan.mul_leaves(A, B, begin, end, C=C, stream=stream)
     dist.all_reduce(C, op=dist.ReduceOp.SUM, group=group)
     return C
@@ -59,8 +79,9 @@ def mul_sharded_rows(plan, A, B, group=None, stream=None):
     rank = dist.get_rank(group)
     n = plan.n
     rb = -(-n // world)
-    partial = torch.zeros((world * rb, n), dtype=A.dtype, device=A.device)
-    begin, end = leaf_range(plan.leaves, world, rank)
+    partial = torch.empty((world * rb, n), dtype=A.dtype, device=A.device)
+    partial[n:].zero_()  # padding rows of the last block (the product overwrites the first n)
+    begin, end = _rank_leaves(plan, world, rank)
     plan.mul_leaves(A, B, begin, end, C=partial[:n], stream=stream)
     out = torch.empty((rb, n), dtype=A.dtype, device=A.device)
     dist.reduce_scatter_tensor(out, partial, op=dist.ReduceOp.SUM, group=group)

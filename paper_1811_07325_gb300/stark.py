@@ -49,7 +49,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("leaf", ctypes.c_int64),
                 ("depth", ctypes.c_int32), ("dtype", ctypes.c_int32), ("leaves", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("peel", ctypes.c_int32), ("combine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("peel", ctypes.c_int32), ("combine", ctypes.c_int32), ("shard_levels", ctypes.c_int32),
+                ("shard_first", ctypes.c_int32), ("workspace_leaves", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class ErrorReport(ctypes.Structure):
@@ -79,6 +81,7 @@ _SIGS = {
     "stark_plan_set_tf32_layout": ([_vp, _ci], _ci),
     "stark_plan_set_input_bound": ([_vp, _i64], _ci),
     "stark_plan_set_traversal": ([_vp, _ci], _ci),
+    "stark_plan_set_shard": ([_vp, _i64, _i64], _ci),
     "stark_plan_set_timing": ([_vp, _ci], _ci),
     "stark_plan_phase_ms": ([_vp, ctypes.POINTER(ctypes.c_float)], _ci),
     "stark_plan_phases": ([_vp, ctypes.POINTER(ctypes.c_float), _ci], _ci),
@@ -262,7 +265,9 @@ class Plan:
         x, y = _vp(), _vp()
         _check(_lib.stark_plan_operands(self._h, a, b, _stream_handle(stream), ctypes.byref(x), ctypes.byref(y)),
                "stark_plan_operands")
-        P, L = self.leaves, self.leaf
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
+        P, L = info.workspace_leaves, self.leaf  # a shard's workspace holds its subtrees' leaves only
         if self.dtype == DType.F32_SPLIT_BF16:
             shape, ts, view = (2 * P, L, L), "<i2", torch.bfloat16
         elif self.dtype == DType.F32_SPLIT_TF32:
@@ -292,6 +297,16 @@ class Plan:
         CTA pairs on one cta_group::2 MMA of 256 x 256 (mode 1 is refused
         with EUNSUPPORTED)."""
         _check(_lib.stark_plan_set_pairing(self._h, int(mode)), "stark_plan_set_pairing")
+
+    def set_shard(self, begin: int, end: int):
+        """Restrict the plan to leaves [begin, end) (``stark_plan_set_shard``):
+        a rank-local workspace and divide for sharding one product."""
+        _check(_lib.stark_plan_set_shard(self._h, int(begin), int(end)), "stark_plan_set_shard")
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
+        self.workspace_bytes = info.workspace_bytes
+        self.shard = (int(begin), int(end))
+        self.shard_levels, self.shard_first = info.shard_levels, info.shard_first
 
     def set_tf32_layout(self, mn: bool):
         """3xTF32 B operand: MN-major planes (no transpose pass) or K-major."""

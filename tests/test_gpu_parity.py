@@ -22,6 +22,7 @@ Bars (written here, derived in the comments):
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_1811_07325_gb300 import synth
 
@@ -219,33 +220,29 @@ def test_f64_within_bound(S, n, depths):
 
 
 # ----------------------------------------------------------------- split fp32
-SPLIT_BOUND = {"F32_SPLIT_BF16": 2.0 ** -12, "F32_SPLIT_TF32": 2.0 ** -16}
-# Per-product relative error of the split: |x - hi - lo| <= u^2 |x| with
-# u = 2^-8 (bf16) or 2^-11 (tf32), and the dropped lo*lo term <= u^2 |xy|,
-# so each product is off by at most ~3 u^2 relative.
-SPLIT_U2 = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22}
-
-
-MMA_K = {"F32_SPLIT_BF16": 16, "F32_SPLIT_TF32": 8}
-
-
-def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=0, L=None):
-    """Normwise bound 1e-6 (the configs' sizes, n >= 64) and the RMS bug
-    signal; tiny n, where averaging cannot bring the 16/22-bit split below
-    1e-6 of ||A|| ||B||, gets the componentwise bound instead:
-    |dC_ij| <= (3 u^2 + n 2^-23) 3^d (|A| |B|)_ij."""
+def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None):
+    """The split-precision bars (tests/bounds.py): with the inputs given and
+    every row of C compared, the componentwise bound |dC_ij| <= c S_ij
+    against the oracle's error majorant, at every n; for n >= 64 the
+    normwise ratio <= 1e-6 (the configs' bound) and the relative RMS model
+    bound.  (Below n = 64 the 16/22-bit split cannot average down to 1e-6 of
+    ||A|| ||B||; the componentwise bound is the bar there.)"""
     diff = C.astype(np.float64) - want
     ratio = np.abs(diff).max() / (A64norm * B64norm)
-    rel_rms = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
+    rel_rms = np.sqrt(np.mean(diff ** 2)) / max(np.sqrt(np.mean(want ** 2)), 1e-300)
     n = want.shape[1]
-    if n >= 64:
-        L = n if L is None else L
-        assert ratio <= 1e-6, ratio
-        assert rel_rms <= SPLIT_BOUND[dtype] + 3 * (L / MMA_K[dtype]) * 2.0 ** -24, rel_rms
+    L = n if L is None else L
+    d = bounds.infer_depth(n, L) if d is None else d
+    if A is not None and want.shape[0] == n and n <= 2048:
+        S = bounds.majorant(oracle, A.astype(np.float64), B.astype(np.float64), d, L)
+        c = bounds.componentwise_c(dtype, L, d)
+        excess = np.abs(diff) / np.maximum(c * S, 1e-300)
+        assert np.all(np.abs(diff) <= c * S), excess.max()
     else:
-        absAB = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
-        tol = (3 * SPLIT_U2[dtype] + n * 2.0 ** -23) * 3 ** d * absAB
-        assert np.all(np.abs(diff) <= tol), np.max(np.abs(diff) / tol)
+        assert n >= 64, "small products need the inputs for the componentwise bound"
+    if n >= 64:
+        assert ratio <= 1e-6, ratio
+        assert rel_rms <= bounds.rms_bound(dtype, L, d), rel_rms
     return ratio, rel_rms
 
 
@@ -280,8 +277,8 @@ def test_split_repeatable_and_stream_ordered(S):
         s.synchronize()
         want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
         an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
-        check_split(C1.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
-        check_split(C2.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16")
+        check_split(C1.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
+        check_split(C2.cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
 
 
 @pytest.mark.parametrize("n,d", [(1024, 2), (1000, 3), (1004, 1), (1001, 2), (777, 1)])
@@ -298,7 +295,7 @@ def test_split_combine_modes_agree(S, n, d):
             C = p.mul(dev(A), dev(B))
             p.check()
             out.append(C.cpu().numpy())
-            check_split(out[-1], want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+            check_split(out[-1], want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
     # same products, different addition order into C: fp32-level agreement
     assert np.abs(out[0] - out[1]).max() <= 1e-5 * np.abs(want).max()
 
@@ -320,7 +317,7 @@ def test_deterministic_combine_is_bitwise_reproducible(S, n, d, dtype):
         p.set_combine(0)
         Cf = p.mul(dA, dB).cpu().numpy()
     assert np.array_equal(C1.view(np.uint32), C2.view(np.uint32))  # bit for bit
-    check_split(C1, want, an, bn, dtype, L=L)
+    check_split(C1, want, an, bn, dtype, A, B, L=L)
     assert np.abs(C1 - Cf).max() <= 1e-5 * np.abs(want).max()  # same products, other order
 
 
@@ -346,7 +343,7 @@ def test_leaf_schedules_agree(S, n, d):
             diff = got.astype(np.float64) - want
             assert np.abs(diff).max() / (an * bn) <= 1e-6
             rel = np.sqrt(np.mean(diff ** 2)) / np.sqrt(np.mean(want ** 2))
-            assert rel <= SPLIT_BOUND["F32_SPLIT_BF16"] + 3 * (p.leaf / 16) * 2.0 ** -24
+            assert rel <= bounds.rms_bound("F32_SPLIT_BF16", p.leaf, d)
     for k in (1, 2, 3, 4):
         assert np.abs(out[k] - out[0]).max() <= 1e-5 * np.abs(want).max()
 
@@ -391,7 +388,7 @@ def test_pair_mma_matches_oracle(S, dtype, n, d, combine, dfs):
         C1 = p.mul(dA, dB).cpu().numpy()
         C2 = p.mul(dA, dB).cpu().numpy()
         p.check()
-        check_split(C1, want, an, bn, dtype, L=p.leaf)
+        check_split(C1, want, an, bn, dtype, A, B, L=p.leaf)
         p.set_pairing(0)
         C0 = p.mul(dA, dB).cpu().numpy()
     assert np.abs(C1 - C0).max() <= 1e-5 * np.abs(want).max()
@@ -423,7 +420,7 @@ def test_depth_first_traversal_matches(S, n, d, dtype, levels):
         assert ws_bfs - p.workspace_bytes == operands - operands // 7 ** levels
         Cd = p.mul(dA, dB).cpu().numpy()
         p.check()
-        check_split(Cd, want, an, bn, dtype, L=p.leaf)
+        check_split(Cd, want, an, bn, dtype, A, B, L=p.leaf)
         p.set_traversal(0)
         assert p.workspace_bytes == ws_bfs
     assert np.abs(Cd - Cb).max() <= 1e-5 * np.abs(want).max()
@@ -494,11 +491,11 @@ def test_tf32_mn_major_layout_matches(S, n, d, dfs, combine):
         Cm = p.mul(dA, dB).cpu().numpy()  # default: MN-major
         p.set_tf32_layout(False)
         Ck = p.mul(dA, dB).cpu().numpy()
-        check_split(Ck, want, an, bn, "F32_SPLIT_TF32", L=p.leaf)
+        check_split(Ck, want, an, bn, "F32_SPLIT_TF32", A, B, L=p.leaf)
         p.set_tf32_layout(True)
         assert np.array_equal(p.mul(dA, dB).cpu().numpy(), Cm) or combine != 2
         p.check()
-        check_split(Cm, want, an, bn, "F32_SPLIT_TF32", L=p.leaf)
+        check_split(Cm, want, an, bn, "F32_SPLIT_TF32", A, B, L=p.leaf)
     assert np.abs(Cm - Ck).max() <= 1e-5 * np.abs(want).max()
     with S.Plan(64, 0, S.DType.F32_SPLIT_BF16) as q:
         with pytest.raises(S.StarkError):
@@ -590,10 +587,11 @@ def test_mul_host_matches_device(S):
     with S.Plan(n, 2, S.DType.F32_SPLIT_BF16) as p:
         Ch = p.mul_host(A, B)
         Cd = p.mul(dev(A), dev(B)).cpu().numpy()
+        L = p.leaf
     want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
     an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
-    check_split(Ch, want, an, bn, "F32_SPLIT_BF16")
-    check_split(Cd, want, an, bn, "F32_SPLIT_BF16")
+    check_split(Ch, want, an, bn, "F32_SPLIT_BF16", A, B, L=L)
+    check_split(Cd, want, an, bn, "F32_SPLIT_BF16", A, B, L=L)
 
 
 def test_mul_host_async_pipeline(S):
@@ -612,7 +610,7 @@ def test_mul_host_async_pipeline(S):
     for k, (a, b) in enumerate(pairs):
         want = oracle.gemm_classical(a.astype(np.float64), b.astype(np.float64))
         an, bn = np.linalg.norm(a.astype(np.float64)), np.linalg.norm(b.astype(np.float64))
-        check_split(Cs[k].numpy(), want, an, bn, "F32_SPLIT_BF16")
+        check_split(Cs[k].numpy(), want, an, bn, "F32_SPLIT_BF16", a, b, L=p.leaf)
 
 
 def test_mul_host_enqueue_and_wait(S):
@@ -638,7 +636,7 @@ def test_mul_host_enqueue_and_wait(S):
     for k, (a, b) in enumerate(pairs):
         want = oracle.gemm_classical(a.astype(np.float64), b.astype(np.float64))
         an, bn = np.linalg.norm(a.astype(np.float64)), np.linalg.norm(b.astype(np.float64))
-        check_split(first[k].numpy(), want, an, bn, "F32_SPLIT_BF16")
+        check_split(first[k].numpy(), want, an, bn, "F32_SPLIT_BF16", a, b, L=p.leaf)
     for k in range(2):
         assert np.abs(Cs[k].numpy() - first[4 - k].numpy()).max() <= 1e-5 * np.abs(first[4 - k].numpy()).max()
 
@@ -692,7 +690,7 @@ def test_sibling_fold_matches_oracle(S, dtype, n, d):
         C1 = p.mul(dA, dB)[r].cpu().numpy()
         C2 = p.mul(dA, dB)[r].cpu().numpy()
         p.check()
-        check_split(C1, want, an, bn, dtype, L=p.leaf)
+        check_split(C1, want, an, bn, dtype, A, B, L=p.leaf)
         p.set_combine(0)
         Cf = p.mul(dA, dB)[r].cpu().numpy()
         p.check()
@@ -724,7 +722,7 @@ def test_measured_combine_choice(S, dtype, n, d):
     if dtype == "F64":
         assert np.abs(C - want).max() / (an * bn) <= 1e-12
     else:
-        check_split(C, want, an, bn, dtype, L=p.leaf)
+        check_split(C, want, an, bn, dtype, A, B, L=p.leaf)
 
 
 def test_sibling_fold_conditions_and_fallbacks(S):
@@ -746,13 +744,13 @@ def test_sibling_fold_conditions_and_fallbacks(S):
         # products mode 3 cannot serve run the fused path: single CTAs, and a
         # partition of the leaves whose partial products sum to A B
         p.set_pairing(0)
-        check_split(p.mul(dA, dB).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+        check_split(p.mul(dA, dB).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
         p.set_pairing(2)
         parts = []
         for lb, le in ((0, 20), (20, 49)):
             parts.append(p.mul_leaves(dA, dB, lb, le))
         p.check()
-        check_split((parts[0] + parts[1]).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", L=p.leaf)
+        check_split((parts[0] + parts[1]).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
 
 
 # ----------------------------------------------------------------- full size, sampled rows
@@ -830,3 +828,72 @@ def test_mul_sharded_single_rank_nccl(S, tmp_path):
         assert (r0, r1) == (0, n) and np.array_equal(rows[:n].cpu().numpy(), want)
     finally:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- sharding one product (rank-local shards)
+@pytest.mark.parametrize("dtype,n,d,world", [("F32_SPLIT_BF16", 1024, 2, 3), ("F32_SPLIT_BF16", 2048, 3, 8),
+                                             ("F32_SPLIT_TF32", 1001, 2, 2), ("I64", 512, 3, 4),
+                                             ("F64", 640, 2, 3)])
+def test_shards_partition_the_product(S, dtype, n, d, world):
+    # each "rank" (run one after another on this GPU) holds a plan restricted
+    # to its leaf range: a smaller workspace, a divide of its own subtrees
+    # only; the partial products sum to A.B (int64 bit-exact)
+    from paper_1811_07325_gb300 import shard
+    if dtype == "I64":
+        A, B = synth.integers(n, 69, 0, -16, 16), synth.integers(n, 69, 1, -16, 16)
+        want = oracle.gemm_classical(A, B)
+    else:
+        A, B = synth.normal(n, 69, 0), synth.normal(n, 69, 1)
+        if dtype == "F64":
+            A, B = A.astype(np.float64), B.astype(np.float64)
+        want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype]) as full:
+        full_ws, leaves = full.workspace_bytes, full.leaves
+    total = None
+    for r in range(world):
+        with shard.shard_plan(n, d, S.DType[dtype], world, r) as p:
+            b, e = shard.leaf_range(leaves, world, r)
+            assert p.shard == (b, e) and p.workspace_bytes < full_ws
+            with pytest.raises(S.StarkError) as ex:
+                p.mul(dA, dB)  # not the whole product
+            assert ex.value.status == S.Status.EINVAL
+            part = p.mul_leaves(dA, dB, b, e)
+            p.check()
+            total = part if total is None else total + part
+    got = total.cpu().numpy()
+    if dtype == "I64":
+        assert np.array_equal(got, want)
+    elif dtype == "F64":
+        an, bn = np.linalg.norm(A), np.linalg.norm(B)
+        assert np.abs(got - want).max() / (an * bn) <= 1e-12
+    else:
+        an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+        L = (n + (128 << d) - 1) // (128 << d) * 128
+        check_split(got, want, an, bn, dtype, L=L)
+
+
+def test_shard_divides_only_its_subtrees(S):
+    # the shard's workspace holds exactly the operands of the subtrees that
+    # contain its leaves (bit-identical to the oracle's divide for them)
+    n, d = 1024, 3
+    A = synth.normal(n, 70, 0)
+    B = synth.normal(n, 70, 1)
+    with S.Plan(n, d, S.DType.F32_SPLIT_BF16) as p:
+        p.set_shard(100, 150)
+        assert p.shard_levels == 2 and p.shard_first == 98  # groups of 7 leaves: 98 .. 153
+        planes = 154 - 98
+        L = p.leaf
+        X, Y = p.operands(dev(A), dev(B))
+        torch.cuda.synchronize()
+        for side, got, M in (("A", X, A), ("B", Y, B)):
+            ops = oracle.strassen_operands(M, p.n_pad, d, side)[98:154]
+            hi, lo = oracle.split_bf16(ops)
+            g = got.view(2, planes, L, L).float().cpu().numpy()
+            assert np.array_equal(g[0], hi) and np.array_equal(g[1], lo), side
+        p.set_shard(0, p.leaves)  # the whole product again
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        p.check()
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    check_split(C, want, an, bn, "F32_SPLIT_BF16", A, B, L=L)

@@ -413,3 +413,113 @@ def test_split_reconstruction_error(split, bits):
     # hi carries `bits` bits, lo the next `bits`: the remainder is below 2^-(2 bits) relative
     assert rel.max() <= 2.0 ** (-2 * bits)
     assert rel.max() > 2.0 ** (-2 * bits - 8)  # and lo is really truncated
+
+
+# ---------------------------------------------------------------------------
+# The error majorant (oracle.strassen_abs): Alg. 1 on |A|, |B| with every
+# sign +.  Pinned by the classical product at depth 0, by its closed form on
+# the all-ones matrix, by the literal 2x2 formulas and by dominance over
+# |A||B|; then used to show what the split-precision bounds catch.
+T_ABS = (12, 4, 4, 12)  # quadrant products (all signs +) in C11, C12, C21, C22 of one level
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_strassen_abs_depth0_and_dominance(d):
+    # exact small integers (every sum exact in fp64); at depth 0 the
+    # majorant is the classical |A||B|, at every depth it dominates it
+    n = 24
+    A = synth.integers(n, 40 + d, 0, -9, 9)
+    B = synth.integers(n, 40 + d, 1, -9, 9)
+    S = oracle.strassen_abs(A.astype(np.float64), B.astype(np.float64), d)
+    absAB = (np.abs(A) @ np.abs(B)).astype(np.float64)
+    if d == 0:
+        assert np.array_equal(S, absAB)
+    else:
+        assert np.all(S >= absAB) and np.any(S > absAB)
+    assert np.array_equal(oracle.strassen_abs(-A.astype(np.float64), B.astype(np.float64), d), S)  # |.| of the inputs
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_strassen_abs_closed_form_on_ones(d):
+    # all-ones n x n: every quadrant product of side h is h, so
+    # S_ij = L * prod over levels of the count of quadrant products in the
+    # C quadrant that (i, j) falls in: 12 (C11, C22) or 4 (C12, C21)
+    n = 8 << d
+    S = oracle.strassen_abs(np.ones((n, n)), np.ones((n, n)), d)
+    L = n >> d
+    want = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            v = L
+            for k in range(1, d + 1):
+                q = 2 * ((i >> (int(math.log2(n)) - k)) & 1) + ((j >> (int(math.log2(n)) - k)) & 1)
+                v *= T_ABS[q]
+            want[i, j] = v
+    assert np.array_equal(S, want)
+
+
+def test_strassen_abs_2x2_literal():
+    # depth 1 on 2x2 scalars, the seven products with absolute values written out
+    a11, a12, a21, a22 = 3.0, -1.0, 2.0, -5.0
+    b11, b12, b21, b22 = -2.0, 4.0, 1.0, 6.0
+    A = np.array([[a11, a12], [a21, a22]])
+    B = np.array([[b11, b12], [b21, b22]])
+    x = lambda v: abs(v)  # noqa: E731
+    m1 = (x(a11) + x(a22)) * (x(b11) + x(b22))
+    m2 = (x(a21) + x(a22)) * x(b11)
+    m3 = x(a11) * (x(b12) + x(b22))
+    m4 = x(a22) * (x(b21) + x(b11))
+    m5 = (x(a11) + x(a12)) * x(b22)
+    m6 = (x(a21) + x(a11)) * (x(b11) + x(b12))
+    m7 = (x(a12) + x(a22)) * (x(b21) + x(b22))
+    want = np.array([[m1 + m4 + m5 + m7, m3 + m5], [m2 + m4, m1 + m2 + m3 + m6]])
+    assert np.array_equal(oracle.strassen_abs(A, B, 1), want)
+
+
+def emulated_split_product(A, B, d, drop=None):
+    """The 3xBF16 Strassen product emulated on the CPU from the oracle's
+    pieces: fp32 leaf operands (the divide), their bf16 hi/lo split, the
+    three kept products per leaf in fp64, combined by W_d.  drop = (leaf,
+    row0, col0, size): that tile of that leaf's product is left out, the
+    way a lost output tile of the leaf kernel would be."""
+    n = A.shape[0]
+    L = n >> d
+    X = oracle.strassen_operands(A, n, d, "A")
+    Y = oracle.strassen_operands(B, n, d, "B")
+    xh, xl = oracle.split_bf16(X)
+    yh, yl = oracle.split_bf16(Y)
+    Wd = kron_table(W, d)
+    C = np.zeros((n, n))
+    Cq = quadrant_blocks(C, d)
+    for l in range(7 ** d):
+        M = xh[l].astype(np.float64) @ yh[l] + xh[l].astype(np.float64) @ yl[l] + xl[l].astype(np.float64) @ yh[l]
+        if drop is not None and drop[0] == l:
+            _, r0, c0, s = drop
+            M[r0:r0 + s, c0:c0 + s] = 0.0
+        for q in range(4 ** d):
+            if Wd[q, l]:
+                Cq[q] += Wd[q, l] * M
+    return C, L
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_split_bounds_pass_correct_and_catch_a_dropped_tile(d):
+    # the bars of the GPU parity tests (tests/bounds.py): the emulated split
+    # product meets them, and the same product with one 128 x 128 output
+    # tile of one leaf left out fails both the componentwise bound and the
+    # relative RMS bound
+    import bounds
+    n = 512
+    A = synth.normal(n, 50 + d, 0)
+    B = synth.normal(n, 50 + d, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    S = oracle.strassen_abs(A.astype(np.float64), B.astype(np.float64), d)
+    C, L = emulated_split_product(A, B, d)
+    c = bounds.componentwise_c("F32_SPLIT_BF16", L, d)
+    rel = lambda X: np.sqrt(np.mean((X - want) ** 2)) / np.sqrt(np.mean(want ** 2))  # noqa: E731
+    assert np.all(np.abs(C - want) <= c * S)
+    assert rel(C) <= bounds.rms_bound("F32_SPLIT_BF16", L, d)
+    leaf = 7 ** d - 3  # a leaf with targets in several quadrants
+    Cbad, _ = emulated_split_product(A, B, d, drop=(leaf, L - 128, 0, 128))
+    assert not np.all(np.abs(Cbad - want) <= c * S)
+    assert rel(Cbad) > bounds.rms_bound("F32_SPLIT_BF16", L, d)

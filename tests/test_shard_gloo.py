@@ -32,13 +32,24 @@ def test_leaf_range_partitions():
 
 
 class CpuLeafPlan:
-    """CPU stand-in: partial product of a leaf range (oracle operands + table)."""
+    """CPU stand-in: partial product of a leaf range (oracle operands + table).
+
+    ``set_shard`` restricts it like ``stark_plan_set_shard``: it then keeps
+    the operands of the subtrees (below min(2, depth) top levels) that hold
+    its leaves and refuses ranges outside its shard."""
 
     def __init__(self, n, depth, npad):
         from paper_1811_07325_gb300 import stark
         self.n, self.depth, self.npad = n, depth, npad
         self.leaves = 7 ** depth
         self.count, self.quad, self.sign = stark.quadrant_table(depth, 2)
+        self.first, self.kept = 0, self.leaves
+
+    def set_shard(self, begin, end):
+        gs = 7 ** (self.depth - min(2, self.depth))
+        self.first = begin // gs * gs
+        self.kept = -(-end // gs) * gs - self.first
+        self.shard = (begin, end)
 
     def offsets(self, q):
         r = c = 0
@@ -50,12 +61,15 @@ class CpuLeafPlan:
 
     def mul_leaves(self, A, B, begin, end, C=None, stream=None):
         import oracle
+        if not (self.first <= begin <= end <= self.first + self.kept):
+            raise ValueError("leaves outside the shard")
         L = self.npad >> self.depth
-        X = oracle.strassen_operands(A.numpy().astype(np.float32), self.npad, self.depth, "A").astype(np.int64)
-        Y = oracle.strassen_operands(B.numpy().astype(np.float32), self.npad, self.depth, "B").astype(np.int64)
+        keep = slice(self.first, self.first + self.kept)  # this rank's subtrees only
+        X = oracle.strassen_operands(A.numpy().astype(np.float32), self.npad, self.depth, "A")[keep].astype(np.int64)
+        Y = oracle.strassen_operands(B.numpy().astype(np.float32), self.npad, self.depth, "B")[keep].astype(np.int64)
         Cp = np.zeros((self.npad, self.npad), np.int64)
         for leaf in range(begin, end):
-            M = X[leaf] @ Y[leaf]
+            M = X[leaf - self.first] @ Y[leaf - self.first]
             for t in range(self.count[leaf]):
                 r, c = self.offsets(int(self.quad[leaf, t]))
                 Cp[r:r + L, c:c + L] += int(self.sign[leaf, t]) * M
@@ -85,12 +99,14 @@ def _worker(rank, world, port, n, depth, npad, out_path, fail_rank, rows=False):
         if rank == fail_rank:
             raise SystemExit(3)  # this rank dies before the collective
         try:
+            plan = CpuLeafPlan(n, depth, npad)
+            plan.set_shard(*shard.leaf_range(plan.leaves, world, rank))  # as shard.shard_plan does
             if rows:
-                r0, r1, blk = shard.mul_sharded_rows(CpuLeafPlan(n, depth, npad), A, B)
+                r0, r1, blk = shard.mul_sharded_rows(plan, A, B)
                 np.save(f"{out_path}.{rank}.npy", blk[:r1 - r0].numpy())
                 np.save(f"{out_path}.{rank}.span.npy", np.array([r0, r1]))
             else:
-                shard.mul_sharded(CpuLeafPlan(n, depth, npad), A, B, C)
+                shard.mul_sharded(plan, A, B, C)
                 np.save(f"{out_path}.{rank}.npy", C.numpy())
         except Exception as e:  # the collective must fail, not hang
             with open(f"{out_path}.{rank}.err", "w") as f:
