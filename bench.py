@@ -36,6 +36,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "effective TFLOP/s (2n³/t) at n=16384, stated error vs FP64; p50/p99 serve latency"
+_T0 = time.perf_counter()
+
+
+def progress(what):
+    """One line on stderr per finished leg (the JSON line stays on stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {what}", file=sys.stderr, flush=True)
 
 
 LEAF_SOURCES = ["paper_1811_07325_gb300/csrc/leaf_tc2.cu", "paper_1811_07325_gb300/csrc/leaf_common.cuh",
@@ -297,6 +303,7 @@ def run_batch(args, stark, synth, torch):
     t_create = time.perf_counter()
     bt = stark.Batch(sizes, -1, stark.DType.F32_SPLIT_BF16)
     t_create = time.perf_counter() - t_create
+    progress(f"batch created and tuned in {t_create:.1f} s")
     for _ in range(3):
         bt.mul(As, Bs, Cs)
     bt.check()
@@ -441,10 +448,12 @@ def run_serve(args, stark, synth, torch):
         return np.array(lat), wall
 
     one_pass(synth.exponential_gaps(count, args.seed + 23, 200.0))  # warm the workspace cache
+    progress("serve warm-up pass done")
     sweep = []
     for k, rate in enumerate((200.0, 2000.0, 8000.0)):
         before = srv.load()
         lat, wall = one_pass(synth.exponential_gaps(count, args.seed + 24 + k, rate))
+        progress(f"serve pass at {rate:.0f} req/s done")
         after = srv.load()
         sweep.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                       "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
@@ -666,6 +675,7 @@ def main():
         plan.mul(A, B, C)
     plan.check()
 
+    progress(f"plan ready (combine mode {plan.combine}), warm-up done")
     # ---------------------------------------------------------------- timed region
     plan.set_timing(args.steps)
     sampler = ClockSampler(local)
@@ -694,6 +704,7 @@ def main():
     flops = 2.0 * n ** 3
     value = world * flops / (ms * 1e-3) / 1e12
 
+    progress("timed region done")
     # ---------------------------------------------------------------- error vs FP64
     error = None
     abs_prod = None  # the oracle's sampled rows of |A||B|, shared by the error checks
@@ -702,20 +713,26 @@ def main():
         rows = synth.sample_rows(n, 256, args.seed + 5)
         want = oracle.gemm_rows(A_h.numpy(), B_h.numpy(), rows)
         abs_prod = oracle.gemm_rows(np.abs(A_h.numpy()), np.abs(B_h.numpy()), rows)
-        got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
-        an = float(torch.linalg.vector_norm(A.double()).item())
-        bn = float(torch.linalg.vector_norm(B.double()).item())
-        error = dict(error_vs_fp64(got, want, abs_prod, an, bn), rows_checked=int(rows.size),
-                     reference="oracle classical FP64 rows", bound=1e-6)
-        # anchor for "FP32-level": the same rows from one classical FP32
-        # product (cuBLAS SGEMM, TF32 off) against the same FP64 rows
+        # the FP64 reductions on the GPU (stark_error_norms): norms of A, B
+        # and the error of the sampled rows against the oracle's
+        rep = stark.error_norms(A, B, C, rows, want, abs_prod)
+        error = {"max_abs_over_normA_normB": rep["max_abs_over_normA_normB"], "rel_rms": rep["rel_rms"],
+                 "componentwise_max": rep["max_componentwise"], "rows_checked": int(rows.size),
+                 "reference": "oracle classical FP64 rows", "bound": 1e-6,
+                 "reduced_by": "stark_error_norms (FP64 on the GPU)"}
+        # anchor for "FP32-level": one classical FP32 product (cuBLAS SGEMM,
+        # TF32 off) judged the same way on the same rows
         prev = torch.backends.cuda.matmul.allow_tf32
         torch.backends.cuda.matmul.allow_tf32 = False
-        c32 = torch.matmul(A[torch.from_numpy(rows).cuda()], B).double().cpu().numpy()
+        c32 = torch.matmul(A, B)
         torch.backends.cuda.matmul.allow_tf32 = prev
-        error["fp32_classical"] = error_vs_fp64(c32, want, abs_prod, an, bn)
+        r32 = stark.error_norms(A, B, c32, rows, want, abs_prod)
+        error["fp32_classical"] = {"max_abs_over_normA_normB": r32["max_abs_over_normA_normB"],
+                                   "rel_rms": r32["rel_rms"], "componentwise_max": r32["max_componentwise"]}
         del c32
+        torch.cuda.empty_cache()
 
+    progress("error vs FP64 done")
     # ---------------------------------------------------------------- end to end (host buffers)
     # every step copies its inputs host->device and its result device->host
     # (pinned buffers); the asynchronous entry point overlaps one step's
@@ -740,6 +757,7 @@ def main():
            "api": "stark_mul_host_enqueue + stark_plan_host_wait (pinned host buffers, copies overlapped with the neighbouring products)"}
     e2e.update(link_bandwidth(torch, A_h, B_h, A, B, C, C_hs[0], e2e_s))
 
+    progress("end to end done")
     # ---------------------------------------------------------------- roofline of the leaf kernel
     pk = peaks()
     leaf_flops = 3 * 2.0 * plan.leaves * plan.leaf ** 3  # three bf16 products per leaf
@@ -826,6 +844,7 @@ def main():
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
 
+    progress("comparators done")
     tf32 = None
     if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
         # the same product with 3xTF32 leaves, for comparison
@@ -852,14 +871,14 @@ def main():
             want = oracle.gemm_rows(A_h.numpy(), B_h.numpy(), rows)
             if abs_prod is None:
                 abs_prod = oracle.gemm_rows(np.abs(A_h.numpy()), np.abs(B_h.numpy()), rows)
-            got = C32[torch.from_numpy(rows).cuda()].double().cpu().numpy()
-            an = float(torch.linalg.vector_norm(A.double()).item())
-            bn = float(torch.linalg.vector_norm(B.double()).item())
-            tf32["error_vs_fp64"] = error_vs_fp64(got, want, abs_prod, an, bn)
+            r = stark.error_norms(A, B, C32, rows, want, abs_prod)
+            tf32["error_vs_fp64"] = {"max_abs_over_normA_normB": r["max_abs_over_normA_normB"],
+                                     "rel_rms": r["rel_rms"], "componentwise_max": r["max_componentwise"]}
         p32.close()
         del C32
         torch.cuda.empty_cache()
 
+    progress("tf32 leg done")
     int64 = None
     if rank == 0 and not args.no_batch:
         # integer form (n = 4096, entries in [-16, 16]): exact int64 Strassen on
@@ -891,24 +910,32 @@ def main():
 
     batch = serve = None
     if rank == 0 and not args.no_batch:
+        progress("int64 leg done")
         batch = run_batch(args, stark, synth, torch)
+        progress("batch leg done")
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, stark, synth, torch)
+        progress("serve leg done")
     peel = None
     traversal = None
     depth_sweep = None
     if rank == 0 and not args.no_batch:
         peel = run_peel(args, stark, synth, torch)
+        progress("peel leg done")
         if args.dtype == "bf16" and args.depth <= 3:
             traversal = run_traversal(args, stark, synth, torch, A, B)
+            progress("traversal leg done")
         if args.dtype == "bf16":
             depth_sweep = run_depth_sweep(args, stark, synth, torch, A, B)
+            progress("depth sweep done")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, args.seed)
+        progress("cpu baseline done")
         if not args.no_oracle_timings:
             cpu["oracle_timings"] = oracle_timings(args.seed)
+            progress("oracle timings done")
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,

@@ -342,11 +342,12 @@ typedef struct stark_batch_s *stark_batch_t;
  * leaf launch, whose epilogue combines (Alg. 5) into each member's own C;
  * the member divides (Alg. 3) precede it.  The launch sequence is recorded
  * in a CUDA graph on first use and replayed while the pointers stay the
- * same.  depth = -1: each member's depth is chosen by the autotuner, which
- * times the candidate depths on the device (cached per (n, dtype) for the
- * process); members whose leaf side allows 256-wide tiles share one grouped
- * launch, the others a second one with 128-wide tiles.  Allocates every
- * member's workspace.
+ * same.  depth = -1: each member's depth and leaf tile are chosen by the
+ * autotuner, which times the candidate (depth, tile) pairs on the device
+ * (cached per size class and dtype for the process); otherwise members
+ * whose leaf side allows it use 256-wide tiles.  Members on 256-wide tiles
+ * share one grouped launch of CTA pairs, the others a second one with
+ * 128-wide tiles on single CTAs.  Allocates every member's workspace.
  * Errors: EINVAL (count <= 0 or > 4096, n[i] <= 0, depth out of range),
  * EUNSUPPORTED (other dtypes, not a GB300), ENOMEM, ECUDA. */
 STARK_API stark_status stark_batch_create(int32_t count, const int64_t *n, int depth, stark_dtype dtype,
@@ -361,6 +362,12 @@ STARK_API stark_status stark_batch_destroy(stark_batch_t batch);
  * call the graph is re-recorded first, which waits for the device. */
 STARK_API stark_status stark_batch_mul(stark_batch_t batch, const void *const *A, const void *const *B,
                                        void *const *C, void *stream);
+
+/* Leaf tile width of member `index` (caller's order): 256 (CTA pairs on
+ * 256 x 256 tiles) or 128 (single CTAs on 128 x 128 tiles); with depth -1
+ * the autotuner times both where the leaf side allows 256 and keeps the
+ * faster (with its depth). */
+STARK_API stark_status stark_batch_tile(stark_batch_t batch, int32_t index, int32_t *tile_n);
 
 /* Depth chosen for member `index`. */
 STARK_API stark_status stark_batch_depth(stark_batch_t batch, int32_t index, int32_t *depth);

@@ -10,11 +10,12 @@
 // unchanged.
 //
 // Depth per member: given, or chosen by the autotuner, which times the
-// candidate depths on the device (one warm-up and three timed products per
-// candidate on scratch inputs) and caches the winner per (n, dtype) for the
-// process.  Members whose leaf side allows 256-wide tiles share one grouped
-// launch of CTA pairs (256 x 256 tiles, cta_group::2), the others a second
-// one with 128 x 128 tiles on single CTAs.
+// candidate (depth, leaf tile) pairs on the device (one warm-up and three
+// timed products per candidate on scratch inputs) and caches the winner per
+// size class and dtype for the process.  The tile candidates are CTA pairs
+// on 256 x 256 tiles (cta_group::2; leaf sides that are multiples of 256)
+// and single CTAs on 128 x 128 tiles.  Members whose tile is 256 share one
+// grouped launch of CTA pairs, the others a second one of single CTAs.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -29,12 +30,20 @@ namespace stark {
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::pair<int64_t, int>, int> g_tuned;  // (n, dtype) -> depth
+std::map<std::pair<int64_t, int>, std::pair<int, int>> g_tuned;  // (n class, dtype) -> (depth, tile)
 
-// Device time (ms) of one product of side n at `depth`, averaged over 3.
-float time_depth(int64_t n, int depth, stark_dtype dt, void* A, void* B, void* C, cudaStream_t s) {
+// Device time (ms) of one product of side n at `depth` with leaf tiles of
+// width `tile` (256: CTA pairs; 128: single CTAs), averaged over 3.
+float time_depth(int64_t n, int depth, stark_dtype dt, int tile, void* A, void* B, void* C, cudaStream_t s) {
   stark_plan_s p;
   if (plan_init(&p, n, depth, dt) != STARK_OK) {
+    plan_release(&p);
+    return -1.f;
+  }
+  if (tile == 128 && p.bn == 256) {  // single CTAs on 128-wide tiles (operand maps do not depend on it)
+    p.bn = 128;
+    p.pair_mode = 0;
+  } else if (tile != p.bn) {
     plan_release(&p);
     return -1.f;
   }
@@ -60,16 +69,21 @@ float time_depth(int64_t n, int depth, stark_dtype dt, void* A, void* B, void* C
 }  // namespace
 
 // Measured depth choice for n x n products (cached per process).
-int autotune_depth(int64_t n_req, stark_dtype dt) {
+void autotune(int64_t n_req, stark_dtype dt, int* depth_out, int* tile_out) {
   // size class: n rounded up to 64 (n <= 1024), 128 (n <= 2048), else 256
   const int64_t q = n_req <= 1024 ? 64 : n_req <= 2048 ? 128 : 256;
   const int64_t n = (n_req + q - 1) / q * q;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find({n, (int)dt});
-    if (it != g_tuned.end()) return it->second;
+    if (it != g_tuned.end()) {
+      *depth_out = it->second.first;
+      *tile_out = it->second.second;
+      return;
+    }
   }
   int best = choose_depth(n, dt);
+  int best_tile = (padded_side(n, best, dt) >> best) % 256 == 0 ? 256 : 128;
   const size_t bytes = (size_t)n * n * element_size(dt);
   void *A = nullptr, *B = nullptr, *C = nullptr;
   cudaStream_t s = nullptr;
@@ -81,10 +95,15 @@ int autotune_depth(int64_t n_req, stark_dtype dt) {
     for (int d = 0; d <= 3; ++d) {
       if ((padded_side(n, d, dt) >> d) < tile_granularity(dt)) continue;
       if (d > 0 && (n >> d) < 128) break;
-      const float ms = time_depth(n, d, dt, A, B, C, s);
-      if (ms > 0 && ms < best_ms) {
-        best_ms = ms;
-        best = d;
+      const bool wide = (padded_side(n, d, dt) >> d) % 256 == 0;
+      for (int tile : {256, 128}) {
+        if (tile == 256 && !wide) continue;
+        const float ms = time_depth(n, d, dt, tile, A, B, C, s);
+        if (ms > 0 && ms < best_ms) {
+          best_ms = ms;
+          best = d;
+          best_tile = tile;
+        }
       }
     }
   }
@@ -94,8 +113,15 @@ int autotune_depth(int64_t n_req, stark_dtype dt) {
   cudaFree(C);
   cudaGetLastError();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[{n, (int)dt}] = best;
-  return best;
+  g_tuned[{n, (int)dt}] = {best, best_tile};
+  *depth_out = best;
+  *tile_out = best_tile;
+}
+
+int autotune_depth(int64_t n, stark_dtype dt) {
+  int d = 0, tile = 128;
+  autotune(n, dt, &d, &tile);
+  return d;
 }
 
 }  // namespace stark
@@ -120,6 +146,7 @@ struct stark_batch_s {
   cudaEvent_t join_ev[kForks] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<int> caller_index;  // caller's index of each (size-sorted) member
+  std::vector<int> tiles;         // leaf tile width of each member (caller's order)
   std::vector<const void*> last;  // pointers the graph was captured with
   int64_t replays = 0;
 };
@@ -161,8 +188,10 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   b->plans.assign(count, nullptr);
+  b->tiles.assign(count, 128);
   for (int i = 0; i < count && st == STARK_OK; ++i) {
-    const int d = depth >= 0 ? depth : autotune_depth(n[i], dt);
+    int d = depth, tile = 0;
+    if (depth < 0) autotune(n[i], dt, &d, &tile);
     auto* p = new (std::nothrow) stark_plan_s();
     if (!p) {
       st = STARK_ENOMEM;
@@ -170,14 +199,17 @@ stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, star
     }
     b->plans[i] = p;
     st = plan_init(p, n[i], d, dt);
+    // the tuned tile, or 256-wide wherever the leaf side allows it
+    if (st == STARK_OK) b->tiles[i] = (p->L % 256 == 0 && tile != 128) ? 256 : 128;
   }
   if (st != STARK_OK) {
     batch_free(b);
     return st;
   }
-  // two grouped launches: members whose leaf side allows 256-wide tiles
-  // first, then the rest with 128-wide tiles; largest products first in each
-  auto wide = [&](int i) { return b->plans[i]->L % 256 == 0; };
+  // two grouped launches: members on 256-wide tiles (CTA pairs) first, then
+  // the rest on 128-wide tiles; largest products first in each
+  const std::vector<int> tiles = b->tiles;
+  auto wide = [&](int i) { return tiles[i] == 256; };
   std::sort(order.begin(), order.end(), [&](int x, int y) {
     if (wide(x) != wide(y)) return wide(x);
     return b->plans[x]->n > b->plans[y]->n;
@@ -250,6 +282,12 @@ stark_status stark_batch_destroy(stark_batch_t b) {
   if (!b) return STARK_OK;
   cudaDeviceSynchronize();
   batch_free(b);
+  return STARK_OK;
+}
+
+stark_status stark_batch_tile(stark_batch_t b, int32_t index, int32_t* tile_n) {
+  if (!b || !tile_n || index < 0 || index >= (int32_t)b->tiles.size()) return STARK_EINVAL;
+  *tile_n = b->tiles[index];
   return STARK_OK;
 }
 

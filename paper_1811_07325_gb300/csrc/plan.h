@@ -27,6 +27,9 @@ int choose_depth(int64_t n, stark_dtype dt);
 // 2048 / beyond) and caches the winner per (class, dtype) for the process.
 // Tensor-core dtypes.
 int autotune_depth(int64_t n, stark_dtype dt);
+// The same search over (depth, leaf tile): tile 256 = CTA pairs on 256 x 256
+// tiles (leaf sides that are multiples of 256), 128 = single CTAs on 128 x 128.
+void autotune(int64_t n, stark_dtype dt, int* depth, int* tile);
 
 }  // namespace stark
 

@@ -93,6 +93,7 @@ _SIGS = {
     "stark_batch_destroy": ([_vp], _ci),
     "stark_batch_mul": ([_vp, _vp, _vp, _vp, _vp], _ci),
     "stark_batch_depth": ([_vp, _i32, ctypes.POINTER(_i32)], _ci),
+    "stark_batch_tile": ([_vp, _i32, ctypes.POINTER(_i32)], _ci),
     "stark_batch_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                           ctypes.POINTER(_i64)], _ci),
     "stark_batch_check": ([_vp, _vp], _ci),
@@ -387,6 +388,15 @@ class Batch:
             d = _i32()
             _check(_lib.stark_batch_depth(self._h, i, ctypes.byref(d)), "stark_batch_depth")
             out.append(d.value)
+        return out
+
+    def tiles(self):
+        """Leaf tile width of every member (256: CTA pairs, 128: single CTAs)."""
+        out = []
+        for i in range(len(self.sizes)):
+            t = _i32()
+            _check(_lib.stark_batch_tile(self._h, i, ctypes.byref(t)), "stark_batch_tile")
+            out.append(t.value)
         return out
 
     def info(self):
