@@ -41,7 +41,33 @@ _T0 = time.perf_counter()
 
 def progress(what):
     """One line on stderr per finished leg (the JSON line stays on stdout)."""
+    _LINE["last"] = what
     print(f"[bench {time.perf_counter() - _T0:7.1f} s] {what}", file=sys.stderr, flush=True)
+
+
+# The JSON line: assembled as soon as the timed product's figures exist and
+# completed leg by leg; printed once, at the end, or by the watchdog when the
+# run overstays its deadline (then with "incomplete" naming where it was).
+_LINE = {"out": None, "printed": False, "last": "start", "lock": threading.Lock()}
+
+
+def print_line(extra=None):
+    with _LINE["lock"]:
+        if _LINE["printed"] or _LINE["out"] is None:
+            return False
+        out = dict(_LINE["out"], **(extra or {}))
+        print(json.dumps(out), flush=True)
+        _LINE["printed"] = True
+        return True
+
+
+def start_watchdog(deadline_s):
+    def run():
+        time.sleep(max(1.0, deadline_s - (time.perf_counter() - _T0)))
+        if print_line({"incomplete": f"deadline of {deadline_s:.0f} s passed after: {_LINE['last']}"}):
+            progress("deadline passed: printed the line gathered so far")
+            os._exit(0)
+    threading.Thread(target=run, daemon=True).start()
 
 
 LEAF_SOURCES = ["paper_1811_07325_gb300/csrc/leaf_tc2.cu", "paper_1811_07325_gb300/csrc/leaf_common.cuh",
@@ -614,6 +640,8 @@ def main():
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
     ap.add_argument("--traversal", type=int, default=0, help="k > 0: depth first over the top k levels")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--deadline", type=float, default=900.0,
+                    help="seconds after which the line gathered so far is printed and the run ends")
     ap.add_argument("--shard", action="store_true",
                     help="one product sharded over the ranks: leaf ranges + NCCL reduce-scatter (strong scaling)")
     ap.add_argument("--no-oracle-timings", action="store_true")
@@ -631,6 +659,8 @@ def main():
             print(json.dumps(out), flush=True)
         return
 
+    if rank == 0:
+        start_watchdog(args.deadline)
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -801,6 +831,23 @@ def main():
                      "model": "leaf 3*2*L^3*7^d flops / bf16 burst + (divide bytes + combine bytes) / HBM; "
                               "combine bytes: C cleared and written (fused) or planes written, read and C written"}
 
+    if rank == 0:
+        _LINE["out"] = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype,
+            "dtype_detail": f"fp32 in/out; 3x{args.dtype} split tensor-core leaf products, fp32 accumulate; "
+                            "fp32 divide sums and combine",
+            "data": "synthetic",
+            "config": dict(workload_config(args, plan.depth), leaves=plan.leaves, leaf=plan.leaf,
+                           tile=list(plan.tile), combine=plan.combine,
+                           combine_choice="measured per plan" if args.combine == -1 else "given"),
+            "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+            "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
+            "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9, "path_roofline": path_roofline,
+            "error_vs_fp64": error, "combine_pass": combine_pass}
+    line = _LINE["out"] if rank == 0 else {}
+
     comparators = None
     if not args.no_comparators and rank == 0:
         comparators = {}
@@ -844,6 +891,7 @@ def main():
             comparators["fp64_error"] = str(ex)
         comparators["unit"] = "effective TFLOP/s (2n^3/t), same GPU"
 
+    line["comparators"] = comparators
     progress("comparators done")
     tf32 = None
     if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
@@ -878,6 +926,7 @@ def main():
         del C32
         torch.cuda.empty_cache()
 
+    line["tf32"] = tf32
     progress("tf32 leg done")
     int64 = None
     if rank == 0 and not args.no_batch:
@@ -910,50 +959,36 @@ def main():
 
     batch = serve = None
     if rank == 0 and not args.no_batch:
+        line["int64"] = int64
         progress("int64 leg done")
-        batch = run_batch(args, stark, synth, torch)
+        batch = line["batch"] = run_batch(args, stark, synth, torch)
         progress("batch leg done")
     if rank == 0 and not args.no_serve:
-        serve = run_serve(args, stark, synth, torch)
+        serve = line["serve"] = run_serve(args, stark, synth, torch)
         progress("serve leg done")
     peel = None
     traversal = None
     depth_sweep = None
     if rank == 0 and not args.no_batch:
-        peel = run_peel(args, stark, synth, torch)
+        peel = line["peel"] = run_peel(args, stark, synth, torch)
         progress("peel leg done")
         if args.dtype == "bf16" and args.depth <= 3:
-            traversal = run_traversal(args, stark, synth, torch, A, B)
+            traversal = line["traversal"] = run_traversal(args, stark, synth, torch, A, B)
             progress("traversal leg done")
         if args.dtype == "bf16":
-            depth_sweep = run_depth_sweep(args, stark, synth, torch, A, B)
+            depth_sweep = line["depth_sweep"] = run_depth_sweep(args, stark, synth, torch, A, B)
             progress("depth sweep done")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, args.seed)
+        cpu = line["cpu_baseline"] = cpu_baseline(n, args.seed)
         progress("cpu baseline done")
         if not args.no_oracle_timings:
             cpu["oracle_timings"] = oracle_timings(args.seed)
             progress("oracle timings done")
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": args.dtype,
-               "dtype_detail": f"fp32 in/out; 3x{args.dtype} split tensor-core leaf products, fp32 accumulate; "
-                               "fp32 divide sums and combine",
-               "data": "synthetic",
-               "config": dict(workload_config(args, plan.depth), leaves=plan.leaves, leaf=plan.leaf,
-                              tile=list(plan.tile), combine=plan.combine,
-                              combine_choice="measured per plan" if args.combine == -1 else "given"),
-               "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
-               "phases_ms": phases, "divide_algorithmic_bytes": divide_bytes,
-               "divide_gbs": divide_bytes / (phases["divide"] * 1e-3) / 1e9, "path_roofline": path_roofline,
-               "error_vs_fp64": error, "comparators": comparators, "combine_pass": combine_pass, "tf32": tf32, "int64": int64,
-               "batch": batch, "serve": serve, "peel": peel, "traversal": traversal, "depth_sweep": depth_sweep,
-               "cpu_baseline": cpu}
-        print(json.dumps(out), flush=True)
+        print_line()
     plan.close()
     if dist is not None:
         dist.destroy_process_group()

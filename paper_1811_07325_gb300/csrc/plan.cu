@@ -187,35 +187,62 @@ int64_t operand_bytes(int64_t n, int depth, stark_dtype dt) {
   return 2 * P * L * L * per;
 }
 
-// Roofline-style cost model for the depth choice: leaf tensor/CUDA-core
-// time plus divide and C traffic at HBM bandwidth (Sec. IV's idea of a
-// per-stage cost, with GB300 rates in place of Spark's).
+// Cost model for the depth choice (Sec. IV's per-stage cost with GB300
+// rates in place of Spark's): the leaf launch's work at the kernel's
+// measured rate, stretched by the quantisation of its tiles over the SMs,
+// plus the divide's and C's bytes at HBM bandwidth and a fixed cost per
+// launch.  Constants measured on GB300 (152 SMs): fp64 CUDA-core leaves
+// 1.25 TFLOP/s, int64 6.85 TOP/s (64 x 64 tiles, one tile per SM at a time
+// reaches the per-SM rate), 3xBF16 pair leaves 1.76 PFLOP/s and 3xTF32 0.93
+// (three products per leaf term), HBM 6.7 TB/s, 22 us per divide launch
+// (the depth-3 divide is one launch per top-level product and side, 14, and
+// reads its input three times over).  The SM count is the device's (152
+// when the host has no device).
 double model_seconds(int64_t n, int depth, stark_dtype dt) {
   const int64_t npad = padded_side(n, depth, dt);
   const double L = (double)(npad >> depth);
   const double P = (double)pow7i(depth);
-  double flops = 2.0 * P * L * L * L;
-  double rate;
+  // the device's SM count; host-only callers without a device get GB300's
+  int dev = 0, v = 0;
+  const bool have = cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0;
+  cudaGetLastError();
+  const double sms = have ? (double)v : 152.0;
+  double flops = 2.0 * P * L * L * L, rate, items, slots;
   switch (dt) {
-    case STARK_F32_SPLIT_BF16: flops *= 3; rate = 1.7e15; break;
-    case STARK_F32_SPLIT_TF32: flops *= 3; rate = 0.85e15; break;
-    case STARK_F64: rate = 1.2e12; break;
-    default: rate = 4.0e12; break;
+    case STARK_F32_SPLIT_BF16:
+    case STARK_F32_SPLIT_TF32: {
+      flops *= 3;
+      rate = dt == STARK_F32_SPLIT_BF16 ? 1.76e15 : 0.93e15;
+      const bool pair = (npad >> depth) % 256 == 0;  // 256 x 256 tiles on CTA pairs, else 128 x 128 on one CTA
+      const double t = pair ? 256.0 : 128.0;
+      items = P * (L / t) * (L / t);
+      slots = pair ? sms / 2 : sms;
+      if (!pair) rate *= 0.85;
+      break;
+    }
+    default:
+      rate = dt == STARK_F64 ? 1.25e12 : 6.85e12;
+      items = P * (L / 64.0) * (L / 64.0);
+      slots = sms;
+      break;
   }
-  const double in_bytes = 2.0 * (double)n * n * element_size(dt);
+  const double waves = std::ceil(items / slots) / std::max(items / slots, 1e-9);
+  const double esz = (double)element_size(dt);
+  const double in_bytes = 2.0 * (double)n * n * esz * (depth == 3 ? 3.0 : 1.0);
   const double ws = (double)operand_bytes(n, depth, dt);
-  const double c_bytes = (double)n * n * element_size(dt) * (1.0 + std::pow(3.0, depth) * 2.0 / 8.0);
-  const double items = P * (L / 128.0) * (L / 128.0);
-  const double waves = std::ceil(items / 148.0) / std::max(1.0, items / 148.0);
-  return flops / rate * waves + (in_bytes + ws + c_bytes) / 6.5e12 + 8e-6 * 3;
+  const double c_bytes = (double)n * n * esz;  // clearing C; the combine's adds stay in L2 / under the leaf work
+  const double launches = (depth == 3 ? 14.0 : 2.0);
+  return flops / rate * waves + (in_bytes + ws + c_bytes) / 6.7e12 + launches * 22e-6 + 5e-6;
 }
 
 int choose_depth(int64_t n, stark_dtype dt) {
   int best = 0;
   double best_t = 1e300;
-  for (int d = 0; d <= kMaxDepth; ++d) {
+  // depths 0..3: the range the constants were measured over (depth 4 stays
+  // available when asked for)
+  for (int d = 0; d <= 3; ++d) {
     if ((padded_side(n, d, dt) >> d) < tile_granularity(dt)) continue;
-    if (d > 0 && (n >> d) < 256) break;  // leaves below 256 are launch/latency bound
     const double t = model_seconds(n, d, dt);
     if (t < best_t) {
       best_t = t;

@@ -1,0 +1,49 @@
+"""The closed-form depth choice (depth = -1 for F64 and I64; the cost model
+of the paper's Sec. IV restated with GB300 rates) against the depths timed
+on the device: the model's pick must be within 10 % of the fastest measured
+depth, at several sizes (the U-shaped optimum over the partition count of
+Sec. V-C, found by the model)."""
+import numpy as np
+import pytest
+
+from paper_1811_07325_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def timed(p, A, B, C, reps):
+    p.mul(A, B, C)
+    p.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(3):  # best of three rounds: the device is shared with nothing else here
+        e0.record()
+        for _ in range(reps):
+            p.mul(A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    p.check()
+    return best
+
+
+@pytest.mark.parametrize("dtype", ["F64", "I64"])
+def test_model_depth_within_ten_percent_of_best(stark_lib, dtype):
+    S = stark_lib
+    dt = S.DType[dtype]
+    for n in (768, 1536, 3072):
+        if dtype == "F64":
+            A, B = synth.uniform(n, 11, 0), synth.uniform(n, 11, 1)
+        else:
+            A, B = synth.integers(n, 11, 0, -16, 16), synth.integers(n, 11, 1, -16, 16)
+        dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        C = torch.empty_like(dA)
+        times = {}
+        for d in range(4):
+            with S.Plan(n, d, dt) as p:
+                times[d] = timed(p, dA, dB, C, 3 if n >= 3072 else 5)
+        with S.Plan(n, -1, dt) as p:
+            chosen = p.depth
+        best = min(times.values())
+        assert times[chosen] <= 1.10 * best, (dtype, n, chosen, times)
