@@ -160,9 +160,13 @@ STARK_API stark_status stark_mul_host_async(stark_plan_t plan, const void *A, co
  * enqueued so far.  CUDA multiplexes streams onto a few hardware queues; an
  * operation that waits on a later event holds back everything queued behind
  * it in a shared queue, so this form enqueues operations in the order they
- * become ready and puts no wait on any stream it does not own: copies in of
- * one call then overlap the product of the previous one whatever the
- * queue assignment.  (stark_mul_host_async's wait on `stream` can hold back
+ * become ready and puts no wait on any stream it does not own.  Copies in
+ * one direction still wait behind copies in the other when the plan's copy
+ * streams share a queue (then each product costs the two copies one after
+ * the other, about 17.6 ms at n = 16384 instead of the product's 13.9): a
+ * process with many streams should raise CUDA_DEVICE_MAX_CONNECTIONS (read
+ * when CUDA starts; 8 by default) to 32 so the plan's streams get queues
+ * of their own.  (stark_mul_host_async's wait on `stream` can hold back
  * the next call's copies when `stream` shares a queue with the plan's.)
  * Buffer rules as stark_mul_host_async, with "until stark_plan_host_wait
  * returned" for "until `stream` has passed that point".  Errors as
