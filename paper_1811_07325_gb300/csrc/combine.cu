@@ -59,6 +59,9 @@ __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ 
         if constexpr (VEC == 4) {
           const float4 x = __ldcs(reinterpret_cast<const float4*>(src));
           v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else if constexpr (VEC == 2) {
+          const float2 x = __ldcs(reinterpret_cast<const float2*>(src));
+          v[0] = x.x; v[1] = x.y;
         } else {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) v[e] = __ldcs(src + e);
@@ -128,7 +131,7 @@ cudaError_t launch_combine(const float* M, int depth, int64_t L, int64_t npad, i
   switch (depth) {
     case 0: return launch_d<0, 4>(M, L, npad, n, C, ldc, s);
     case 1: return launch_d<1, 4>(M, L, npad, n, C, ldc, s);
-    case 2: return launch_d<2, 4>(M, L, npad, n, C, ldc, s);
+    case 2: return launch_d<2, 2>(M, L, npad, n, C, ldc, s);  // 16 partial sums of 2: 64 registers, 4 blocks per SM
     case 3: return launch_d<3, 1>(M, L, npad, n, C, ldc, s);
     default: return cudaErrorInvalidValue;
   }
