@@ -105,9 +105,10 @@ def measured_traffic(n, depth, kernel, combine=0):
                     kv[k.strip()] = v.strip().strip("`")
         if kv.get("kernel_source_sha256") != leaf_source_hash():
             return None
-        if int(kv.get("n", -1)) != n or int(kv.get("depth", -1)) != depth or int(kv.get("combine", 0)) != combine:
+        if int(kv.get("n", -1)) != n or int(kv.get("depth", -1)) != depth:
             return None
-        return float(kv["traffic_bytes_per_launch"])
+        key = f"traffic_bytes_per_launch.combine{combine}"
+        return float(kv[key]) if key in kv else None
     except Exception:
         return None
 

@@ -20,7 +20,9 @@ def _profile(tmp_path, sha, kernel="leaf_tc2_kernel", n=16384, depth=2, traffic=
     p = tmp_path / "traffic.md"
     p.write_text("# summary\n\n"
                  f"- kernel: {kernel}\n- n: {n}\n- depth: {depth}\n"
-                 f"- traffic_bytes_per_launch: {traffic}\n- kernel_source_sha256: `{sha}`\n")
+                 f"- traffic_bytes_per_launch.combine0: {traffic}\n"
+                 f"- traffic_bytes_per_launch.combine2: {traffic // 2}\n"
+                 f"- kernel_source_sha256: `{sha}`\n")
     return str(p)
 
 
@@ -29,6 +31,8 @@ def test_traffic_attached_only_for_the_captured_source(tmp_path, monkeypatch):
     # an absolute profile path (os.path.join keeps it; the sources stay under ROOT)
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", _profile(tmp_path, sha))
     assert bench.measured_traffic(16384, 2, bench.PAIR_KERNEL) == 123e9
+    assert bench.measured_traffic(16384, 2, bench.PAIR_KERNEL, combine=2) == 61.5e9
+    assert bench.measured_traffic(16384, 2, bench.PAIR_KERNEL, combine=3) is None  # not captured
     # another workload, another kernel, or a changed source: no figure
     assert bench.measured_traffic(8192, 2, bench.PAIR_KERNEL) is None
     assert bench.measured_traffic(16384, 3, bench.PAIR_KERNEL) is None
