@@ -909,30 +909,44 @@ def main():
         # the same product with 3xTF32 leaves, for comparison
         del C
         torch.cuda.empty_cache()
+        # (and again with accumulator promotion every 256 of K: the tensor
+        # core's own accumulation then spans 256 instead of the leaf side)
         p32 = stark.Plan(n, d, stark.DType.F32_SPLIT_TF32)
         C32 = torch.empty_like(A)
-        for _ in range(2):
-            p32.mul(A, B, C32)
-        p32.check()
-        p32.set_timing(5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(5):
-            p32.mul(A, B, C32)
-        e1.record()
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / 5
-        ph32 = p32.phase_ms()
-        tf32 = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32, "phases_ms": ph32}
         if not args.no_check:
             import oracle
             rows = synth.sample_rows(n, 256, args.seed + 5)
             want = oracle.gemm_rows(A_h.numpy(), B_h.numpy(), rows)
             if abs_prod is None:
                 abs_prod = oracle.gemm_rows(np.abs(A_h.numpy()), np.abs(B_h.numpy()), rows)
-            r = stark.error_norms(A, B, C32, rows, want, abs_prod)
-            tf32["error_vs_fp64"] = {"max_abs_over_normA_normB": r["max_abs_over_normA_normB"],
-                                     "rel_rms": r["rel_rms"], "componentwise_max": r["max_componentwise"]}
+
+        def tf32_leg(promotion):
+            p32.set_promotion(promotion)
+            for _ in range(2):
+                p32.mul(A, B, C32)
+            p32.check()
+            p32.set_timing(5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                p32.mul(A, B, C32)
+            e1.record()
+            torch.cuda.synchronize()
+            ms32 = e0.elapsed_time(e1) / 5
+            leg = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32,
+                   "phases_ms": p32.phase_ms()}
+            p32.set_timing(0)
+            if not args.no_check:
+                r = stark.error_norms(A, B, C32, rows, want, abs_prod)
+                leg["error_vs_fp64"] = {"max_abs_over_normA_normB": r["max_abs_over_normA_normB"],
+                                        "rel_rms": r["rel_rms"], "componentwise_max": r["max_componentwise"]}
+            return leg
+
+        tf32 = tf32_leg(0)
+        try:
+            tf32["promoted_k256"] = tf32_leg(256)
+        except stark.StarkError as ex:  # report, do not hide
+            tf32["promoted_k256"] = str(ex)
         p32.close()
         del C32
         torch.cuda.empty_cache()

@@ -81,7 +81,7 @@ typedef struct {
   int32_t shard_first;     /* first leaf whose operands the shard's workspace holds     */
   int32_t workspace_leaves;/* leaves whose operands the workspace holds (all of them, one  */
                            /* depth-first subtree's, or a shard's subtrees')               */
-  int32_t reserved[1];
+  int32_t promotion_k;     /* stark_plan_set_promotion: K per tensor-core accumulation, 0: off */
 } stark_plan_info;
 
 /* ----------------------------------------------------------------- plans */
@@ -256,6 +256,24 @@ STARK_API stark_status stark_plan_set_raster(stark_plan_t plan, int band);
  * EINVAL (null plan, mn outside 0..1), EUNSUPPORTED (mn = 1 on a plan of
  * another dtype). */
 STARK_API stark_status stark_plan_set_tf32_layout(stark_plan_t plan, int mn);
+
+/* Accumulator promotion for the split-fp32 leaf products (the leaf GEMMs of
+ * Alg. 4; the paper's leaves are FP64 and need none).  The tensor core sums
+ * a leaf tile's products over K in its fp32 accumulator; its additions do
+ * not round to nearest, so their error grows with the number of K steps.
+ * k_chunk > 0 limits one tensor-core accumulation to k_chunk of K: after
+ * each chunk the partial tile is added to a running fp32 sum on the CUDA
+ * cores (round to nearest), and the running sum is what the combine sees.
+ * k_chunk = 0 (default) accumulates over the whole leaf side.  Costs the
+ * MMAs the time of each drain and of each tile's epilogue (the two
+ * accumulators of a CTA hold the running sum and the chunk, instead of
+ * alternating between tiles).  Applies to the CTA-pair leaf kernel:
+ * leaf side a multiple of 256, 256-wide tiles, 3xBF16 or 3xTF32 with the
+ * MN-major layout, combine modes 0-2.  Errors: EINVAL (null plan, k_chunk
+ * < 0 or not a multiple of 256), EUNSUPPORTED (another dtype, leaf side or
+ * layout, or combine mode 3; a later product whose leaves would run on
+ * another kernel also returns EUNSUPPORTED). */
+STARK_API stark_status stark_plan_set_promotion(stark_plan_t plan, int k_chunk);
 
 /* Operand pipeline of the 3xBF16 leaf launch with 256-wide tiles: deep = 1
  * runs single CTAs that stage K = 32 per step in four 48 KB buffers

@@ -62,10 +62,36 @@ struct Tc2Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
+// Accumulator promotion (LeafTcArgs::promo_kb): the two TMEM accumulators
+// of a CTA become the running sum R0 (K chunk 0 accumulates there directly)
+// and the chunk accumulator R1 (K chunks 1, 2, ...).  After each chunk the
+// epilogue warps add R1 into R0 on the CUDA cores in fp32 with round to
+// nearest, and write R0 back; the last chunk's R1 is added as the tile is
+// read out.  The tensor core's own accumulation so spans promo_kb K blocks
+// instead of the whole leaf side.  The two accumulators no longer alternate
+// between tiles, so the MMAs wait for each drain and for each tile's
+// epilogue.
+template <int BN>
+__device__ __forceinline__ void promote_drain(uint32_t tmem_base, int quarter) {
+  const uint32_t row = tmem_base + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t a[32], b[32];
+    tmem_ld_32x32b_x32(row + (uint32_t)(c * 32), a);
+    tmem_ld_32x32b_x32(row + (uint32_t)(BN + c * 32), b);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__fadd_rn(__uint_as_float(a[j]), __uint_as_float(b[j])));
+    tmem_st_32x32b_x32(row + (uint32_t)(c * 32), a);
+  }
+  tmem_st_wait();
+}
+
 // GROUPED: items of several problems (GroupDesc array, tensor maps in global
 // memory), as in the single-CTA kernel's grouped mode.  SIB: sibling-major
-// item order with the sibling-folded combine (LeafTcArgs::sib).
-template <bool TF32, bool GROUPED, bool TMN, bool SIB>
+// item order with the sibling-folded combine (LeafTcArgs::sib).  PROMO:
+// accumulator promotion (above; one problem, not with SIB).
+template <bool TF32, bool GROUPED, bool TMN, bool SIB, bool PROMO = false>
 __global__ void __launch_bounds__(kThreads2, 1)
     leaf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
@@ -199,21 +225,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
       uint32_t acc_phase = 0;
       bool ok = true;
       bool issued = false;
-      for (int item = unit; ok && item < num_items; item += units) {
-        if (SIB && !decode(item).valid) continue;
-        const int kblocks = GROUPED ? decode(item).kblocks : p.L / Cfg::BK;
-        // both CTAs' epilogues have drained this accumulator
-        if (!mbar_wait_bounded_cluster(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * Cfg::BN);
-        for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait_bounded(full_bar(s), phase, p.err, kDevTimeoutFull, p.timeout_ns)) {
-            ok = false;
-            break;
-          }
+      // K blocks [kb0, kb1) of the current item into the accumulator at
+      // d_tmem (the first one overwrites it); false when a wait expired
+      auto run_kblocks = [&](uint32_t d_tmem, int kb0, int kb1) -> bool {
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait_bounded(full_bar(s), phase, p.err, kDevTimeoutFull, p.timeout_ns)) return false;
           tc_fence_after();
           const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
 #pragma unroll
@@ -229,7 +245,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
               b_hi = smem_desc_k<Cfg::RB>(st + 2 * Cfg::A_BYTES + boff);
               b_lo = smem_desc_k<Cfg::RB>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + boff);
             }
-            const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+            const uint32_t first = (kb == kb0 && k == 0) ? 0u : 1u;
             if constexpr (TF32) {
               mma2_tf32(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
               mma2_tf32(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
@@ -247,17 +263,61 @@ __global__ void __launch_bounds__(kThreads2, 1)
             phase ^= 1;
           }
         }
-        if (!ok) break;
-        mma2_commit_mc(accf_bar(acc), 0x3);  // both halves of the accumulator complete
-        if (++acc == 2) {
-          acc = 0;
-          acc_phase ^= 1;
+        return true;
+      };
+      if constexpr (PROMO) {
+        // accumulator r is filled fills[r] times; fill f waits for the
+        // drain of fill f - 1 (barrier phase parity (f & 1) ^ 1)
+        uint32_t fills0 = 0u, fills1 = 0u;
+        int cur = 0;
+        const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
+        for (int item = unit; ok && item < num_items; item += units) {
+          for (int kc = 0; kc < kblocks; kc += ck) {
+            const int r = kc == 0 ? 0 : 1;
+            const uint32_t f = r ? fills1 : fills0;
+            if (!mbar_wait_bounded_cluster(acce_bar(r), (f & 1u) ^ 1u, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
+              ok = false;
+              break;
+            }
+            cur = r;
+            tc_fence_after();
+            if (!run_kblocks(tmem_base + (uint32_t)(r * Cfg::BN), kc, kc + ck < kblocks ? kc + ck : kblocks)) {
+              ok = false;
+              break;
+            }
+            mma2_commit_mc(accf_bar(r), 0x3);  // this chunk is complete in both CTAs
+            if (r) ++fills1; else ++fills0;
+          }
         }
-      }
-      if (!ok && issued) {
-        // MMAs in flight finish before TMEM is released (own barrier only)
-        mma2_commit_mc(accf_bar(acc), 0x1);
-        mbar_wait_bounded(accf_bar(acc), acc_phase, nullptr, 0, 200000000ull);
+        if (!ok && issued) {
+          mma2_commit_mc(accf_bar(cur), 0x1);
+          mbar_wait_bounded(accf_bar(cur), (cur ? fills1 : fills0) & 1u, nullptr, 0, 200000000ull);
+        }
+      } else {
+        for (int item = unit; ok && item < num_items; item += units) {
+          if (SIB && !decode(item).valid) continue;
+          const int kblocks = GROUPED ? decode(item).kblocks : p.L / Cfg::BK;
+          // both CTAs' epilogues have drained this accumulator
+          if (!mbar_wait_bounded_cluster(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (!run_kblocks(tmem_base + (uint32_t)(acc * Cfg::BN), 0, kblocks)) {
+            ok = false;
+            break;
+          }
+          mma2_commit_mc(accf_bar(acc), 0x3);  // both halves of the accumulator complete
+          if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1;
+          }
+        }
+        if (!ok && issued) {
+          // MMAs in flight finish before TMEM is released (own barrier only)
+          mma2_commit_mc(accf_bar(acc), 0x1);
+          mbar_wait_bounded(accf_bar(acc), acc_phase, nullptr, 0, 200000000ull);
+        }
       }
     }
   } else {
@@ -265,20 +325,55 @@ __global__ void __launch_bounds__(kThreads2, 1)
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     const uint32_t ebuf = epi_base + (uint32_t)(warp - 2) * 8192u;
     const uint64_t pol_c = policy_evict_first();
-    int acc = 0;
-    uint32_t acc_phase = 0;
-    for (int item = unit; item < num_items; item += units) {
-      const ItemInfo it = decode(item);
-      if (!it.valid) continue;
-      if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
-      tc_fence_after();
-      epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(acc * Cfg::BN), quarter, lane, ebuf, pol_c);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(acc), 0));
-      if (++acc == 2) {
-        acc = 0;
-        acc_phase ^= 1;
+    if constexpr (PROMO) {
+      uint32_t got0 = 0u, got1 = 0u;  // completed fills of each accumulator seen
+      const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
+      const int nch = (kblocks + ck - 1) / ck;
+      bool ok = true;
+      for (int item = unit; ok && item < num_items; item += units) {
+        const ItemInfo it = decode(item);
+        if (!mbar_wait_bounded(accf_bar(0), got0 & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
+        ++got0;
+        for (int c = 1; c < nch; ++c) {
+          if (!mbar_wait_bounded(accf_bar(1), got1 & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          ++got1;
+          if (c + 1 < nch) {
+            tc_fence_after();
+            promote_drain<Cfg::BN>(tmem_base, quarter);  // R0 += R1
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(1), 0));
+          }
+        }
+        if (!ok) break;
+        tc_fence_after();
+        epilogue_item<Cfg::BN, false>(it, p, tmem_base, 0u, quarter, lane, ebuf, pol_c, nch > 1 ? Cfg::BN : -1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_cluster(mapa_shared(acce_bar(0), 0));
+          if (nch > 1) mbar_arrive_cluster(mapa_shared(acce_bar(1), 0));
+        }
+      }
+    } else {
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      for (int item = unit; item < num_items; item += units) {
+        const ItemInfo it = decode(item);
+        if (!it.valid) continue;
+        if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
+        tc_fence_after();
+        epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(acc * Cfg::BN), quarter, lane, ebuf, pol_c);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(acc), 0));
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
       }
     }
     bulk_wait_group<0>();  // each lane's own bulk reductions
@@ -291,11 +386,12 @@ __global__ void __launch_bounds__(kThreads2, 1)
   cluster_sync();
 }
 
-template <bool TF32, bool GROUPED, bool TMN = false, bool SIB = false>
+template <bool TF32, bool GROUPED, bool TMN = false, bool SIB = false, bool PROMO = false>
 cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmC,
                     int num_sms, cudaStream_t st) {
   using Cfg = Tc2Cfg<TF32, TMN>;
-  auto kern = leaf_tc2_kernel<TF32, GROUPED, TMN, SIB>;
+  auto kern = leaf_tc2_kernel<TF32, GROUPED, TMN, SIB, PROMO>;
+  if (PROMO && a.promo_kb <= 0) return cudaErrorInvalidValue;
   int64_t items;
   if constexpr (GROUPED) {
     if (!a.groups || a.ngroups <= 0) return cudaErrorInvalidValue;
@@ -322,6 +418,12 @@ bool leaf_tc2_fits(const LeafTcArgs& a) { return a.L % 256 == 0; }
 cudaError_t launch_leaf_tc2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorMap* tmB,
                             const CUtensorMap* tmC, bool tf32, int num_sms, cudaStream_t st) {
   if (!leaf_tc2_fits(a)) return cudaErrorInvalidValue;
+  if (a.promo_kb > 0) {
+    // accumulator promotion: bf16 and MN-major tf32, not with the sibling fold
+    if (a.sib || (tf32 && !a.b_mn)) return cudaErrorInvalidValue;
+    return tf32 ? launch2<true, false, true, false, true>(a, tmA, tmB, tmC, num_sms, st)
+                : launch2<false, false, false, false, true>(a, tmA, tmB, tmC, num_sms, st);
+  }
   if (a.sib) {
     if (tf32 && !a.b_mn) return cudaErrorInvalidValue;  // sibling fold: bf16 and MN-major tf32 only
     return tf32 ? launch2<true, false, true, true>(a, tmA, tmB, tmC, num_sms, st)

@@ -341,6 +341,7 @@ stark_status stark_plan_get_info(stark_plan_t p, stark_plan_info* info) {
   info->shard_levels = p->shard_levels;
   info->shard_first = (int32_t)p->shard_first;
   info->workspace_leaves = (int32_t)p->P_ws;
+  info->promotion_k = p->promo_k;
   return STARK_OK;
 }
 
@@ -475,8 +476,10 @@ stark_status stark_plan_set_combine(stark_plan_t p, int mode) {
   if (!p || mode < -1 || mode > 3) return STARK_EINVAL;
   if (mode == -1) return plan_tune_combine(p);
   if (mode == 3) {
-    // sibling fold on the CTA-pair kernel: 256-wide tiles, breadth first
-    if (!p->is_tc || p->depth < 1 || p->dfs || p->L % 256 != 0 || (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn))
+    // sibling fold on the CTA-pair kernel: 256-wide tiles, breadth first;
+    // not with accumulator promotion
+    if (!p->is_tc || p->depth < 1 || p->dfs || p->L % 256 != 0 || (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn) ||
+        p->promo_k)
       return STARK_EUNSUPPORTED;
     if (!p->q_planes && p->n > 0) {
       const int64_t parents = p->P / 7, side = 2 * p->L;
@@ -685,6 +688,21 @@ stark_status stark_plan_set_pairing(stark_plan_t p, int enable) {
   if (!p || enable < 0 || enable > 2) return STARK_EINVAL;
   if (enable == 1) return STARK_EUNSUPPORTED;  // no schedule shares tiles between CTAs by multicast
   p->pair_mode = enable;
+  return STARK_OK;
+}
+
+stark_status stark_plan_set_promotion(stark_plan_t p, int k_chunk) {
+  if (!p || k_chunk < 0 || k_chunk % 256 != 0) return STARK_EINVAL;
+  if (k_chunk == 0) {
+    p->promo_k = 0;
+    return STARK_OK;
+  }
+  // CTA-pair leaves (256-wide tiles, L % 256 == 0), bf16 or MN-major tf32,
+  // not with the sibling fold
+  if (!p->is_tc || p->L % 256 != 0 || p->bn != 256 || p->combine_mode == 3 ||
+      (p->dt == STARK_F32_SPLIT_TF32 && !p->tf32_mn))
+    return STARK_EUNSUPPORTED;
+  p->promo_k = k_chunk;
   return STARK_OK;
 }
 
@@ -1040,6 +1058,12 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       }
     }
     const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
+    if (p->promo_k) {
+      // accumulator promotion runs on the CTA-pair kernel only
+      if (a.pair != 2 || p->bn != 256 || !leaf_tc2_fits(a) || sib || (tf32 && !p->tf32_mn))
+        return STARK_EUNSUPPORTED;
+      a.promo_kb = p->promo_k / (tf32 ? 32 : 64);
+    }
     if (a.pair == 2 && p->bn == 256 && leaf_tc2_fits(a)) {
       // CTA pairs on one 256 x 256 MMA; K-major tf32 needs Y boxes of 128 rows
       if (tf32 && !p->tf32_mn && !p->has_mapbp) {

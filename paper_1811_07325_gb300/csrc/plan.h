@@ -69,6 +69,7 @@ struct stark_plan_s {
   bool has_mapbp = false;
   int deep_pipeline = 0; // 1: 3xBF16 with 64-byte rows, 4 stages of 48 KB (256-wide tiles)
   int raster_band = 0;   // tile columns per raster band of a leaf (0: row-major)
+  int promo_k = 0;       // accumulator promotion every promo_k of K (CTA-pair leaves), 0: off
   CUtensorMap tmA64, tmB64;  // operand maps for the 64-byte-row schedule
   bool has_maps64 = false;
   // I64 with a declared input bound: exact bf16 tensor-core leaves

@@ -147,6 +147,9 @@ struct LeafTcArgs {
                        // run back to back at one tile position and their tiles are stored or added
                        // into the parent's quadrants (tmC = parent planes [P/7][2L][2L]); leaf
                        // range of whole parents
+  int32_t promo_kb;    // > 0 (CTA-pair kernel): accumulator promotion -- every promo_kb K blocks
+                       // the tensor-core partial sum is added into a running fp32 sum on the
+                       // CUDA cores (round to nearest); 0: one tensor-core accumulation over K
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;

@@ -51,7 +51,7 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("peel", ctypes.c_int32), ("combine", ctypes.c_int32), ("shard_levels", ctypes.c_int32),
                 ("shard_first", ctypes.c_int32), ("workspace_leaves", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("promotion_k", ctypes.c_int32)]
 
 
 class ErrorReport(ctypes.Structure):
@@ -78,6 +78,7 @@ _SIGS = {
     "stark_plan_set_pairing": ([_vp, _ci], _ci),
     "stark_plan_set_pipeline": ([_vp, _ci], _ci),
     "stark_plan_set_raster": ([_vp, _ci], _ci),
+    "stark_plan_set_promotion": ([_vp, _ci], _ci),
     "stark_plan_set_tf32_layout": ([_vp, _ci], _ci),
     "stark_plan_set_input_bound": ([_vp, _i64], _ci),
     "stark_plan_set_traversal": ([_vp, _ci], _ci),
@@ -179,6 +180,7 @@ class Plan:
         self.tile = (info.tile_m, info.tile_n)
         self.peel = info.peel
         self.combine = info.combine
+        self.promotion_k = info.promotion_k
 
     def close(self):
         if getattr(self, "_h", None):
@@ -283,6 +285,12 @@ class Plan:
             X, Y = X.view(view), Y.view(view)
         return X, Y
 
+    def info(self) -> PlanInfo:
+        """What the plan decided (``stark_plan_get_info``)."""
+        info = PlanInfo()
+        _check(_lib.stark_plan_get_info(self._h, ctypes.byref(info)), "stark_plan_get_info")
+        return info
+
     def set_combine(self, mode: int):
         """0: fused, TMA bulk reductions (default); 1: fused, vector atomics;
         2: deterministic (stored leaf products, ordered combine pass);
@@ -312,6 +320,13 @@ class Plan:
     def set_tf32_layout(self, mn: bool):
         """3xTF32 B operand: MN-major planes (no transpose pass) or K-major."""
         _check(_lib.stark_plan_set_tf32_layout(self._h, 1 if mn else 0), "stark_plan_set_tf32_layout")
+
+    def set_promotion(self, k_chunk: int):
+        """Accumulator promotion of the split-fp32 leaf products: every
+        ``k_chunk`` of K (a multiple of 256) the tensor-core partial sum joins
+        a running fp32 sum on the CUDA cores; 0 turns it off."""
+        _check(_lib.stark_plan_set_promotion(self._h, int(k_chunk)), "stark_plan_set_promotion")
+        self.promotion_k = int(k_chunk)
 
     def set_raster(self, band: int):
         """Leaf tile order: bands of ``band`` tile columns (0: row-major)."""

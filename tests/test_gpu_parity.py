@@ -17,7 +17,9 @@ Bars (written here, derived in the comments):
       3 (L / k) 2^-24: the tensor-core accumulation, up to one fp32 ulp per
       accumulating MMA (k = 16 bf16 / 8 tf32 per MMA, 3 MMAs per K step,
       L = leaf side): at L = 4096 this term, not the split, dominates, which
-      is why 3xTF32 is measured no more accurate than 3xBF16 there.
+      is why 3xTF32 is measured no more accurate than 3xBF16 there.  With
+      accumulator promotion every kc of K the term covers kc instead of L
+      (plus the fp32 additions of the chunks; tests/bounds.py).
 """
 import numpy as np
 import pytest
@@ -220,13 +222,14 @@ def test_f64_within_bound(S, n, depths):
 
 
 # ----------------------------------------------------------------- split fp32
-def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None):
+def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None, kc=None):
     """The split-precision bars (tests/bounds.py): with the inputs given and
     every row of C compared, the componentwise bound |dC_ij| <= c S_ij
     against the oracle's error majorant, at every n; for n >= 64 the
     normwise ratio <= 1e-6 (the configs' bound) and the relative RMS model
     bound.  (Below n = 64 the 16/22-bit split cannot average down to 1e-6 of
-    ||A|| ||B||; the componentwise bound is the bar there.)"""
+    ||A|| ||B||; the componentwise bound is the bar there.)  kc: the K of
+    one tensor-core accumulation under accumulator promotion."""
     diff = C.astype(np.float64) - want
     ratio = np.abs(diff).max() / (A64norm * B64norm)
     rel_rms = np.sqrt(np.mean(diff ** 2)) / max(np.sqrt(np.mean(want ** 2)), 1e-300)
@@ -235,14 +238,14 @@ def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None
     d = bounds.infer_depth(n, L) if d is None else d
     if A is not None and want.shape[0] == n and n <= 2048:
         S = bounds.majorant(oracle, A.astype(np.float64), B.astype(np.float64), d, L)
-        c = bounds.componentwise_c(dtype, L, d)
+        c = bounds.componentwise_c(dtype, L, d, kc)
         excess = np.abs(diff) / np.maximum(c * S, 1e-300)
         assert np.all(np.abs(diff) <= c * S), excess.max()
     else:
         assert n >= 64, "small products need the inputs for the componentwise bound"
     if n >= 64:
         assert ratio <= 1e-6, ratio
-        assert rel_rms <= bounds.rms_bound(dtype, L, d), rel_rms
+        assert rel_rms <= bounds.rms_bound(dtype, L, d, kc), rel_rms
     return ratio, rel_rms
 
 
@@ -751,6 +754,115 @@ def test_sibling_fold_conditions_and_fallbacks(S):
             parts.append(p.mul_leaves(dA, dB, lb, le))
         p.check()
         check_split((parts[0] + parts[1]).cpu().numpy(), want, an, bn, "F32_SPLIT_BF16", A, B, L=p.leaf)
+
+
+# ----------------------------------------------------------------- accumulator promotion
+@pytest.mark.parametrize("dtype,n,d,k,combine", [
+    ("F32_SPLIT_BF16", 512, 1, 256, 2),    # L = 256: one chunk, promotion changes nothing
+    ("F32_SPLIT_BF16", 1024, 1, 256, 0),   # L = 512: two chunks, the second added at read-out
+    ("F32_SPLIT_BF16", 2048, 1, 256, 2),   # L = 1024: four chunks, two drains in TMEM
+    ("F32_SPLIT_BF16", 1536, 1, 512, 1),   # L = 768: chunks of 512 and 256; vector atomics
+    ("F32_SPLIT_BF16", 1001, 2, 256, 0),   # ragged n: the staging copy of C
+    ("F32_SPLIT_BF16", 2048, 2, 256, 2),
+    ("F32_SPLIT_TF32", 1024, 1, 256, 0),
+    ("F32_SPLIT_TF32", 2048, 1, 256, 2),
+    ("F32_SPLIT_TF32", 1536, 1, 512, 0),
+])
+def test_promotion_matches_oracle(S, dtype, n, d, k, combine):
+    # every K chunk's tensor-core partial sum joins an fp32 running sum; the
+    # product stays within the split bounds against the FP64 oracle, a second
+    # product on the same plan agrees (the barrier phases carry over), and it
+    # differs from the unpromoted product only by rounding
+    A = synth.normal(n, 71 + d, 0)
+    B = synth.normal(n, 71 + d, 1)
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, d, S.DType[dtype]) as p:
+        p.set_combine(combine)
+        p.set_promotion(k)
+        assert p.info().promotion_k == k
+        C1 = p.mul(dA, dB).cpu().numpy()
+        C2 = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        check_split(C1, want, an, bn, dtype, A, B, L=p.leaf, kc=k)
+        p.set_promotion(0)
+        Cn = p.mul(dA, dB).cpu().numpy()
+        p.check()
+        single_chunk = k >= p.leaf
+    if combine == 2:
+        assert np.array_equal(C1.view(np.uint32), C2.view(np.uint32))
+        if single_chunk:
+            assert np.array_equal(C1.view(np.uint32), Cn.view(np.uint32))
+    else:
+        assert np.abs(C1 - C2).max() <= 1e-5 * np.abs(want).max()
+    assert np.abs(C1 - Cn).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("dtype,gain", [("F32_SPLIT_TF32", 4.0), ("F32_SPLIT_BF16", 1.0)])
+def test_promotion_cuts_accumulation_error(S, dtype, gain):
+    # one leaf of side 4096 (depth 0): the tensor core's accumulation over K
+    # = 4096 dominates the 3xTF32 error, and it grows in proportion to the K
+    # it spans, so promotion every 512 should cut it ~8x (required: 4x);
+    # 3xBF16's 16-bit split dominates its own error, so there promotion
+    # must only not hurt.  Both within the promoted bounds.
+    n = 4096
+    A = synth.normal(n, 75, 0)
+    B = synth.normal(n, 75, 1)
+    rows = synth.sample_rows(n, 64, 75)
+    want = oracle.gemm_rows(A, B, rows)
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    dA, dB = dev(A), dev(B)
+    r = torch.from_numpy(rows).cuda()
+    rms = {}
+    with S.Plan(n, 0, S.DType[dtype]) as p:
+        for k in (0, 512):
+            p.set_promotion(k)
+            C = p.mul(dA, dB)[r].cpu().numpy()
+            p.check()
+            _, rms[k] = check_split(C, want, an, bn, dtype, L=p.leaf, kc=k)
+    assert rms[512] * gain <= rms[0], rms
+
+
+def test_promotion_conditions(S):
+    n = 1024
+    A = synth.normal(n, 73, 0)
+    B = synth.normal(n, 73, 1)
+    dA, dB = dev(A), dev(B)
+    with S.Plan(n, 1, S.DType.F32_SPLIT_BF16) as p:
+        for bad in (-256, 300):
+            with pytest.raises(S.StarkError) as e:
+                p.set_promotion(bad)
+            assert e.value.status == S.Status.EINVAL
+        p.set_promotion(512)
+        with pytest.raises(S.StarkError) as e:
+            p.set_combine(3)  # the sibling fold keeps its own accumulators
+        assert e.value.status == S.Status.EUNSUPPORTED
+        p.set_pairing(0)  # single CTAs: promotion has no kernel there
+        with pytest.raises(S.StarkError) as e:
+            p.mul(dA, dB)
+        assert e.value.status == S.Status.EUNSUPPORTED
+        p.set_pairing(2)
+        p.mul(dA, dB)
+        p.check()
+    with S.Plan(n, 1, S.DType.F32_SPLIT_BF16) as p:
+        p.set_combine(3)
+        with pytest.raises(S.StarkError) as e:
+            p.set_promotion(256)
+        assert e.value.status == S.Status.EUNSUPPORTED
+    with S.Plan(640, 1, S.DType.F32_SPLIT_BF16) as p:  # leaf side 384
+        with pytest.raises(S.StarkError) as e:
+            p.set_promotion(256)
+        assert e.value.status == S.Status.EUNSUPPORTED
+    with S.Plan(512, 1, S.DType.F64) as p:
+        with pytest.raises(S.StarkError) as e:
+            p.set_promotion(256)
+        assert e.value.status == S.Status.EUNSUPPORTED
+    with S.Plan(n, 1, S.DType.F32_SPLIT_TF32) as p:
+        p.set_tf32_layout(False)
+        with pytest.raises(S.StarkError) as e:
+            p.set_promotion(256)
+        assert e.value.status == S.Status.EUNSUPPORTED
 
 
 # ----------------------------------------------------------------- full size, sampled rows
