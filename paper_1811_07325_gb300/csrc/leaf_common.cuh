@@ -176,13 +176,11 @@ __device__ __forceinline__ ItemInfo decode_item(int item, const LeafTcArgs& p, c
 // with the 128-byte swizzle and issues one TMA bulk add-reduction per target
 // (the add happens at L2).  Fallback (C not 16-byte addressable by TMA):
 // signed vector atomics from registers.  With p.store_m the tile is stored
-// to the leaf's M plane instead (deterministic, unfused combine).  With
-// add_col >= 0 (accumulator promotion) the tile is the fp32 sum of the
-// running accumulator at acc_col and the last K chunk's at add_col.
+// to the leaf's M plane instead (deterministic, unfused combine).
 template <int BN, bool INT1>
 __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcArgs& p, uint32_t tmem_base,
                                               uint32_t acc_col, int quarter, int lane, uint32_t ebuf,
-                                              uint64_t pol_c, int32_t add_col = -1) {
+                                              uint64_t pol_c) {
   const int row_in_tile = quarter * 32 + lane;
   const int m0 = it.m0, n0 = it.n0, nt = it.nt;
   const CTarget* tg = it.tg;
@@ -196,16 +194,6 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
   for (int chunk = 0; chunk < BN / 32; ++chunk) {
     uint32_t r[32];
     tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc_col + (uint32_t)(chunk * 32), r);
-    if (add_col >= 0) {
-      // accumulator promotion: the last K chunk's partial sum (columns from
-      // add_col) joins the running sum in fp32, round to nearest
-      uint32_t r2[32];
-      tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)add_col + (uint32_t)(chunk * 32),
-                         r2);
-      tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r2[j])));
-    }
     tmem_ld_wait();
     if constexpr (INT1) {
       // exact integers held in fp32: signed 64-bit adds into C (wrap mod

@@ -62,27 +62,34 @@ struct Tc2Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
-// Accumulator promotion (LeafTcArgs::promo_kb): the two TMEM accumulators
-// of a CTA become the running sum R0 (K chunk 0 accumulates there directly)
-// and the chunk accumulator R1 (K chunks 1, 2, ...).  After each chunk the
-// epilogue warps add R1 into R0 on the CUDA cores in fp32 with round to
-// nearest, and write R0 back; the last chunk's R1 is added as the tile is
-// read out.  The tensor core's own accumulation so spans promo_kb K blocks
-// instead of the whole leaf side.  The two accumulators no longer alternate
-// between tiles, so the MMAs wait for each drain and for each tile's
-// epilogue.
+// Accumulator promotion (LeafTcArgs::promo_kb): a tile's K range is cut
+// into chunks of promo_kb K blocks.  Of the CTA's two TMEM accumulators one
+// holds the tile's running sum (chunk 0 accumulates there directly) and the
+// other takes chunks 1, 2, ...; after each of those the epilogue warps fold
+// it into the running sum on the CUDA cores (fp32, round to nearest) and
+// release it.  The tensor core's own accumulation so spans promo_kb K
+// blocks instead of the whole leaf side.  The two accumulators swap roles
+// from one tile to the next: once the last chunk is folded, the next tile's
+// chunk 0 starts in the released accumulator while the epilogue stores the
+// finished running sum from the other.  The MMAs wait for each fold.
 template <int BN>
-__device__ __forceinline__ void promote_drain(uint32_t tmem_base, int quarter) {
+__device__ __forceinline__ void promote_fold(uint32_t tmem_base, uint32_t run_col, uint32_t chunk_col, int quarter) {
   const uint32_t row = tmem_base + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
-    uint32_t a[32], b[32];
-    tmem_ld_32x32b_x32(row + (uint32_t)(c * 32), a);
-    tmem_ld_32x32b_x32(row + (uint32_t)(BN + c * 32), b);
+  for (int c = 0; c < BN / 64; ++c) {
+    uint32_t a0[32], a1[32], b0[32], b1[32];
+    tmem_ld_32x32b_x32(row + run_col + (uint32_t)(c * 64), a0);
+    tmem_ld_32x32b_x32(row + run_col + (uint32_t)(c * 64 + 32), a1);
+    tmem_ld_32x32b_x32(row + chunk_col + (uint32_t)(c * 64), b0);
+    tmem_ld_32x32b_x32(row + chunk_col + (uint32_t)(c * 64 + 32), b1);
     tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__fadd_rn(__uint_as_float(a[j]), __uint_as_float(b[j])));
-    tmem_st_32x32b_x32(row + (uint32_t)(c * 32), a);
+    for (int j = 0; j < 32; ++j) {
+      a0[j] = __float_as_uint(__fadd_rn(__uint_as_float(a0[j]), __uint_as_float(b0[j])));
+      a1[j] = __float_as_uint(__fadd_rn(__uint_as_float(a1[j]), __uint_as_float(b1[j])));
+    }
+    tmem_st_32x32b_x32(row + run_col + (uint32_t)(c * 64), a0);
+    tmem_st_32x32b_x32(row + run_col + (uint32_t)(c * 64 + 32), a1);
   }
   tmem_st_wait();
 }
@@ -266,14 +273,15 @@ __global__ void __launch_bounds__(kThreads2, 1)
         return true;
       };
       if constexpr (PROMO) {
-        // accumulator r is filled fills[r] times; fill f waits for the
-        // drain of fill f - 1 (barrier phase parity (f & 1) ^ 1)
+        // accumulator r is filled f_r times; every fill waits for the
+        // release of the one before (barrier phase parity (f_r & 1) ^ 1).
+        // Tile j keeps its running sum in accumulator j & 1.
         uint32_t fills0 = 0u, fills1 = 0u;
-        int cur = 0;
+        int cur = 0, run = 0;
         const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
-        for (int item = unit; ok && item < num_items; item += units) {
+        for (int item = unit; ok && item < num_items; item += units, run ^= 1) {
           for (int kc = 0; kc < kblocks; kc += ck) {
-            const int r = kc == 0 ? 0 : 1;
+            const int r = kc == 0 ? run : run ^ 1;
             const uint32_t f = r ? fills1 : fills0;
             if (!mbar_wait_bounded_cluster(acce_bar(r), (f & 1u) ^ 1u, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
               ok = false;
@@ -330,33 +338,33 @@ __global__ void __launch_bounds__(kThreads2, 1)
       const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
       const int nch = (kblocks + ck - 1) / ck;
       bool ok = true;
-      for (int item = unit; ok && item < num_items; item += units) {
+      int run = 0;
+      for (int item = unit; ok && item < num_items; item += units, run ^= 1) {
         const ItemInfo it = decode(item);
-        if (!mbar_wait_bounded(accf_bar(0), got0 & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns)) break;
-        ++got0;
+        const int other = run ^ 1;
+        // chunk 0 in the running accumulator
+        if (!mbar_wait_bounded(accf_bar(run), (run ? got1 : got0) & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns))
+          break;
+        if (run) ++got1; else ++got0;
         for (int c = 1; c < nch; ++c) {
-          if (!mbar_wait_bounded(accf_bar(1), got1 & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns)) {
+          if (!mbar_wait_bounded(accf_bar(other), (other ? got1 : got0) & 1u, p.err, kDevTimeoutAccFull,
+                                 p.timeout_ns)) {
             ok = false;
             break;
           }
-          ++got1;
-          if (c + 1 < nch) {
-            tc_fence_after();
-            promote_drain<Cfg::BN>(tmem_base, quarter);  // R0 += R1
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(1), 0));
-          }
+          if (other) ++got1; else ++got0;
+          tc_fence_after();
+          promote_fold<Cfg::BN>(tmem_base, (uint32_t)(run * Cfg::BN), (uint32_t)(other * Cfg::BN), quarter);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(other), 0));  // the chunk is folded
         }
         if (!ok) break;
         tc_fence_after();
-        epilogue_item<Cfg::BN, false>(it, p, tmem_base, 0u, quarter, lane, ebuf, pol_c, nch > 1 ? Cfg::BN : -1);
+        epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(run * Cfg::BN), quarter, lane, ebuf, pol_c);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive_cluster(mapa_shared(acce_bar(0), 0));
-          if (nch > 1) mbar_arrive_cluster(mapa_shared(acce_bar(1), 0));
-        }
+        if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(run), 0));
       }
     } else {
       int acc = 0;
