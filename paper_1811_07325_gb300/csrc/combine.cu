@@ -114,6 +114,90 @@ __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ 
   }
 }
 
+// Depth 3 with the planes streamed through shared memory.  At depth 3 a
+// thread holds 64 partial sums, which leaves too few registers for enough
+// plane loads in flight to stream at HBM bandwidth; here a block of 128
+// threads owns 128 consecutive positions of one row and cp.async copies
+// the planes' row segments into a ring of kRing stages, one sibling group
+// (the 7 leaves below one depth-2 product, 3.5 KB) per stage, kRing - 1
+// groups in flight.  Each thread adds its position's values in ascending
+// leaf order, exactly as combine_kernel<3, 1> does.
+constexpr int kRing = 12;
+constexpr int kTW3 = 128;
+
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__global__ void __launch_bounds__(kTW3, 4) combine3_staged_kernel(const float* __restrict__ M, int64_t L, int64_t npad,
+                                                                int64_t n, float* __restrict__ C, int64_t ldc) {
+  __shared__ __align__(16) float ring[kRing][7][kTW3];
+  const int64_t tiles = L / kTW3;
+  const int64_t r = (int64_t)blockIdx.x / tiles;
+  const int64_t j0 = ((int64_t)blockIdx.x % tiles) * kTW3;
+  const int t = threadIdx.x;
+  const int64_t plane = L * L;
+  // group g (leaves 7g .. 7g + 6) into stage g % kRing: 7 x 32 copies of 16 bytes
+  auto issue = [&](int g) {
+    float* st = &ring[g % kRing][0][0];
+    for (int k = t; k < 7 * (kTW3 / 4); k += kTW3) {
+      const int leaf = k / (kTW3 / 4), c4 = (k % (kTW3 / 4)) * 4;
+      cp_async_16(static_cast<uint32_t>(__cvta_generic_to_shared(st + leaf * kTW3 + c4)),
+                  M + (int64_t)(7 * g + leaf) * plane + r * L + j0 + c4);
+    }
+  };
+#pragma unroll 1
+  for (int g = 0; g < kRing - 1; ++g) {
+    issue(g);
+    cp_async_commit();
+  }
+  float out[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) out[q] = 0.f;
+#pragma unroll
+  for (int g = 0; g < 49; ++g) {
+    cp_async_wait<kRing - 2>();  // group g has landed (this thread's copies)
+    __syncthreads();             // ... and every thread's
+    const int i1 = g / 7, i2 = g % 7;
+#pragma unroll
+    for (int i3 = 0; i3 < 7; ++i3) {
+      const float v = ring[g % kRing][i3][t];
+#pragma unroll
+      for (int a1 = 0; a1 < 2; ++a1)
+#pragma unroll
+        for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+          for (int a3 = 0; a3 < 2; ++a3) {
+            if (a1 >= tgt_n(i1) || a2 >= tgt_n(i2) || a3 >= tgt_n(i3)) continue;
+            const int q = (tgt_q(i1, a1) * 4 + tgt_q(i2, a2)) * 4 + tgt_q(i3, a3);
+            const int sign = tgt_s(i1, a1) * tgt_s(i2, a2) * tgt_s(i3, a3);
+            out[q] = sign > 0 ? out[q] + v : out[q] - v;
+          }
+    }
+    __syncthreads();  // stage g % kRing is free again
+    if (g + kRing - 1 < 49) issue(g + kRing - 1);
+    cp_async_commit();  // (an empty group past the end keeps the count uniform)
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int q = 0; q < 64; ++q) {
+    int64_t ro = 0, co = 0;
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+      const int digit = (q >> (2 * (3 - k))) & 3;
+      ro += (int64_t)(digit >> 1) * (npad >> k);
+      co += (int64_t)(digit & 1) * (npad >> k);
+    }
+    const int64_t row = ro + r, col = co + j0 + t;
+    if (row < n && col < n) C[row * ldc + col] = out[q];
+  }
+}
+
 template <int D, int VEC>
 cudaError_t launch_d(const float* M, int64_t L, int64_t npad, int64_t n, float* C, int64_t ldc, cudaStream_t s) {
   if (L % VEC != 0) return cudaErrorInvalidValue;
@@ -132,7 +216,14 @@ cudaError_t launch_combine(const float* M, int depth, int64_t L, int64_t npad, i
     case 0: return launch_d<0, 4>(M, L, npad, n, C, ldc, s);
     case 1: return launch_d<1, 4>(M, L, npad, n, C, ldc, s);
     case 2: return launch_d<2, 2>(M, L, npad, n, C, ldc, s);  // 16 partial sums of 2: 64 registers, 4 blocks per SM
-    case 3: return launch_d<3, 1>(M, L, npad, n, C, ldc, s);
+    case 3:
+      if (L % kTW3 == 0) {
+        const int64_t blocks = L * (L / kTW3);
+        combine3_staged_kernel<<<(unsigned)blocks, kTW3, 0, s>>>(M, L, npad, n, C, ldc);
+        count_launch();
+        return cudaGetLastError();
+      }
+      return launch_d<3, 1>(M, L, npad, n, C, ldc, s);
     default: return cudaErrorInvalidValue;
   }
 }

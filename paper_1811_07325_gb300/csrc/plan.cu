@@ -935,7 +935,12 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
     db.out_lo = static_cast<char*>(p->Y) + half + off;
   }
   stark_status st = STARK_OK;
-  if (top < 0 && depth == 3) {
+  if (top < 0 && depth == 3 && (om == kOutSplitBf16 || om == kOutSplitTf32) && divide_staged_fits(p->L)) {
+    // breadth first at depth 3, split fp32: one pass per operand, the
+    // input tile staged in shared memory
+    st = to_status(launch_divide_staged(da, 0, om, s));
+    if (st == STARK_OK) st = to_status(launch_divide_staged(db, 1, om, s));
+  } else if (top < 0 && depth == 3) {
     // breadth first at depth 3: one launch per top-level product, each a
     // depth-2 subtree read through that product's level-1 sum and written
     // to its block of 7^(d-1) planes (the outer-prefix form of the deep

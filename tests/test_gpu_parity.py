@@ -135,7 +135,10 @@ def test_int64_equals_oracle_strassen(S):
 
 # ----------------------------------------------------------------- divide phase
 @pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
-@pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3), (1001, 4)])
+@pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3), (1001, 4),
+                                 # depth 3 with L a multiple of 256: the staged one-pass divide
+                                 # (aligned rows; ragged rows and columns; unaligned row stride)
+                                 (2048, 3), (2044, 3), (2001, 3)])
 def test_divide_split_bit_exact(S, dtype, n, d):
     dt = S.DType[dtype]
     A = synth.normal(n, 7 + d, 0)
