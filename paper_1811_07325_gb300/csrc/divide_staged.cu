@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(TW / kStagedVec) divide_staged_kernel(DivideAr
 
 template <int OUT, int SIDE>
 cudaError_t launch_staged(const DivideArgs& a, cudaStream_t st) {
-  constexpr int TW = 256;
+  constexpr int TW = 128;
   constexpr int SMEM = 64 * TW * 4;
   if (a.L % TW != 0 || a.ld < a.n || a.top >= 0) return cudaErrorInvalidValue;
   const int vec_ok = (a.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
@@ -115,7 +115,7 @@ cudaError_t launch_staged(const DivideArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-bool divide_staged_fits(int64_t L) { return L > 0 && L % 256 == 0; }
+bool divide_staged_fits(int64_t L) { return L > 0 && L % 128 == 0; }
 
 cudaError_t launch_divide_staged(const DivideArgs& a, int side, OutMode out, cudaStream_t st) {
   if (out == kOutSplitBf16) return side == 0 ? launch_staged<kOutSplitBf16, 0>(a, st) : launch_staged<kOutSplitBf16, 1>(a, st);

@@ -229,10 +229,16 @@ double model_seconds(int64_t n, int depth, stark_dtype dt) {
   }
   const double waves = std::ceil(items / slots) / std::max(items / slots, 1e-9);
   const double esz = (double)element_size(dt);
-  const double in_bytes = 2.0 * (double)n * n * esz * (depth == 3 ? 3.0 : 1.0);
+  // depth 3: the split dtypes divide in one staged pass per operand (leaf
+  // side a multiple of 128); otherwise one launch per top-level product,
+  // reading the input three times
+  const bool staged = depth == 3 && (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) &&
+                      divide_staged_fits(npad >> depth);
+  const bool per_top = depth == 3 && !staged;
+  const double in_bytes = 2.0 * (double)n * n * esz * (per_top ? 3.0 : 1.0);
   const double ws = (double)operand_bytes(n, depth, dt);
   const double c_bytes = (double)n * n * esz;  // clearing C; the combine's adds stay in L2 / under the leaf work
-  const double launches = (depth == 3 ? 14.0 : 2.0);
+  const double launches = (per_top ? 14.0 : 2.0);
   return flops / rate * waves + (in_bytes + ws + c_bytes) / 6.7e12 + launches * 22e-6 + 5e-6;
 }
 

@@ -80,7 +80,7 @@ cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, O
 cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType in, OutMode out, cudaStream_t s);
 // Depth 3, split-fp32 outputs, breadth first (a.top < 0): one pass per
 // operand with the input tile staged in shared memory (divide_staged.cu);
-// needs L % 256 == 0 (divide_staged_fits).  Same planes as launch_divide.
+// needs L % 128 == 0 (divide_staged_fits).  Same planes as launch_divide.
 bool divide_staged_fits(int64_t L);
 cudaError_t launch_divide_staged(const DivideArgs& a, int side, OutMode out, cudaStream_t s);
 // C (+)= A B on sub-blocks (M x K times K x N, row strides lda, ldb, ldc in
