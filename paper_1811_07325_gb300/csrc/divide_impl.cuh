@@ -104,6 +104,17 @@ struct Emitter {
       }
       if (bad) record_error(range_flag, kDevIntRange);
       store_vec(reinterpret_cast<__nv_bfloat16*>(hi) + at, h);
+    } else if constexpr (OUT == kOutSplitBf16 && VEC % 2 == 0) {
+      // two values per conversion (round to nearest even each, as below)
+      __nv_bfloat162 h[VEC / 2], l[VEC / 2];
+#pragma unroll
+      for (int e = 0; e < VEC / 2; ++e) {
+        h[e] = __floats2bfloat162_rn(x.v[2 * e], x.v[2 * e + 1]);
+        const float2 hf = __bfloat1622float2(h[e]);
+        l[e] = __floats2bfloat162_rn(x.v[2 * e] - hf.x, x.v[2 * e + 1] - hf.y);
+      }
+      store_vec(reinterpret_cast<__nv_bfloat162*>(hi) + at / 2, h);
+      store_vec(reinterpret_cast<__nv_bfloat162*>(lo) + at / 2, l);
     } else if constexpr (OUT == kOutSplitBf16) {
       __nv_bfloat16 h[VEC], l[VEC];
 #pragma unroll
@@ -130,9 +141,9 @@ struct Emitter {
     }
   }
 
-  template <typename E>
-  __device__ __forceinline__ static void store_vec(E* p, const E (&x)[VEC]) {
-    constexpr int bytes = (int)sizeof(E) * VEC;
+  template <typename E, int N>
+  __device__ __forceinline__ static void store_vec(E* p, const E (&x)[N]) {
+    constexpr int bytes = (int)sizeof(E) * N;
     if constexpr (bytes % 16 == 0) {
 #pragma unroll
       for (int k = 0; k < bytes / 16; ++k) __stcs(reinterpret_cast<int4*>(p) + k, reinterpret_cast<const int4*>(x)[k]);
@@ -142,7 +153,7 @@ struct Emitter {
       __stcs(reinterpret_cast<int*>(p), *reinterpret_cast<const int*>(x));
     } else {
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) p[e] = x[e];
+      for (int e = 0; e < N; ++e) p[e] = x[e];
     }
   }
 };
