@@ -502,12 +502,14 @@ def emulated_split_product(A, B, d, drop=None):
     return C, L
 
 
+@pytest.mark.parametrize("kc", [None, 128])
 @pytest.mark.parametrize("d", [1, 2])
-def test_split_bounds_pass_correct_and_catch_a_dropped_tile(d):
+def test_split_bounds_pass_correct_and_catch_a_dropped_tile(d, kc):
     # the bars of the GPU parity tests (tests/bounds.py): the emulated split
     # product meets them, and the same product with one 128 x 128 output
     # tile of one leaf left out fails both the componentwise bound and the
-    # relative RMS bound
+    # relative RMS bound -- also with the tighter bars of accumulator
+    # promotion every kc of K
     import bounds
     n = 512
     A = synth.normal(n, 50 + d, 0)
@@ -515,11 +517,36 @@ def test_split_bounds_pass_correct_and_catch_a_dropped_tile(d):
     want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
     S = oracle.strassen_abs(A.astype(np.float64), B.astype(np.float64), d)
     C, L = emulated_split_product(A, B, d)
-    c = bounds.componentwise_c("F32_SPLIT_BF16", L, d)
+    c = bounds.componentwise_c("F32_SPLIT_BF16", L, d, kc)
+    rms = bounds.rms_bound("F32_SPLIT_BF16", L, d, kc)
     rel = lambda X: np.sqrt(np.mean((X - want) ** 2)) / np.sqrt(np.mean(want ** 2))  # noqa: E731
     assert np.all(np.abs(C - want) <= c * S)
-    assert rel(C) <= bounds.rms_bound("F32_SPLIT_BF16", L, d)
+    assert rel(C) <= rms
     leaf = 7 ** d - 3  # a leaf with targets in several quadrants
     Cbad, _ = emulated_split_product(A, B, d, drop=(leaf, L - 128, 0, 128))
     assert not np.all(np.abs(Cbad - want) <= c * S)
-    assert rel(Cbad) > bounds.rms_bound("F32_SPLIT_BF16", L, d)
+    assert rel(Cbad) > rms
+
+
+def test_promoted_bounds_shrink_the_accumulation_term():
+    # promotion every kc of K: one tensor-core accumulation spans kc instead
+    # of L (3 kc / k MMA steps of at most 2 ulp) plus ceil(L / kc) - 1
+    # round-to-nearest fp32 additions; kc >= L or 0 leaves the bound as is
+    import bounds
+    for dt in ("F32_SPLIT_BF16", "F32_SPLIT_TF32"):
+        for L, d in ((4096, 2), (2048, 3), (768, 1)):
+            base_c, base_r = bounds.componentwise_c(dt, L, d), bounds.rms_bound(dt, L, d)
+            assert bounds.componentwise_c(dt, L, d, 0) == base_c
+            assert bounds.componentwise_c(dt, L, d, L) == base_c
+            assert bounds.rms_bound(dt, L, d, 2 * L) == base_r
+            prev = base_c
+            for kc in (512, 256):
+                if kc >= L:
+                    continue
+                cc = bounds.componentwise_c(dt, L, d, kc)
+                assert cc < prev
+                acc_full = 3 * L / bounds.MMA_K[dt] * 2.0 ** -22
+                acc_kc = 3 * kc / bounds.MMA_K[dt] * 2.0 ** -22 + (-(-L // kc) - 1) * 2.0 ** -24
+                assert cc == pytest.approx(base_c - acc_full + acc_kc)
+                assert bounds.rms_bound(dt, L, d, kc) < base_r
+                prev = cc
