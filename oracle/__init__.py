@@ -20,6 +20,9 @@ Functions (each cites what it follows; see ``stark_oracle.c``):
                                    fp32 operand sum (Alg. 1 / Alg. 3).
 * ``split_bf16(x)``, ``split_tf32(x)`` -- hi = RN(x), lo = RN(x - hi) in the
                                    8- / 11-significant-bit formats.
+* ``split_fp16(x)``               -- the same in IEEE binary16 (11 bits,
+                                   subnormals below 2^-14, overflow to inf).
+* ``round_fp16(x)``               -- one binary16 rounding (the pins).
 * ``round_sig(x, bits)``        -- one round-to-nearest-even to ``bits``
                                    significant bits.
 """
@@ -71,6 +74,9 @@ def _load():
             lib.oracle_strassen_operands_f32.restype = ci
             lib.oracle_split_bf16.argtypes = [i64, vp, vp, vp]
             lib.oracle_split_tf32.argtypes = [i64, vp, vp, vp]
+            lib.oracle_split_fp16.argtypes = [i64, vp, vp, vp]
+            lib.oracle_round_fp16_f32.argtypes = [ctypes.c_float]
+            lib.oracle_round_fp16_f32.restype = ctypes.c_float
             lib.oracle_round_sig_f32.argtypes = [ctypes.c_float, ci]
             lib.oracle_round_sig_f32.restype = ctypes.c_float
             _lib = lib
@@ -176,6 +182,18 @@ def split_tf32(x: np.ndarray):
     hi, lo = np.empty_like(x), np.empty_like(x)
     lib.oracle_split_tf32(x.size, _p(x), _p(hi), _p(lo))
     return hi, lo
+
+
+def split_fp16(x: np.ndarray):
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    hi, lo = np.empty_like(x), np.empty_like(x)
+    lib.oracle_split_fp16(x.size, _p(x), _p(hi), _p(lo))
+    return hi, lo
+
+
+def round_fp16(x: float) -> float:
+    return float(_load().oracle_round_fp16_f32(ctypes.c_float(x)))
 
 
 def round_sig(x: float, bits: int) -> float:

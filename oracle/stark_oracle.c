@@ -38,6 +38,11 @@
  *                                     TF32 (11 significant bits), written from
  *                                     the definition (nearest representable,
  *                                     ties to even significand).
+ *   oracle_round_fp16                 the same to IEEE binary16 (11
+ *                                     significant bits, exponent range
+ *                                     2^-14 .. 2^15, subnormal spacing 2^-24,
+ *                                     overflow to infinity); the split of the
+ *                                     3xFP16 leaves.
  *
  * Integer arithmetic is done in uint64_t so that it wraps modulo 2^64 (two's
  * complement); Strassen's identities hold in any commutative ring, so the
@@ -479,5 +484,41 @@ void oracle_split_tf32(int64_t count, const float *x, float *hi, float *lo)
     }
 }
 
+/* Round a finite fp32 value to IEEE binary16: 11 significant bits where the
+ * exponent is normal (|x| >= 2^-14), the fixed spacing 2^-24 below that, ties
+ * to the candidate whose last kept bit is 0; a result beyond the largest
+ * finite value 65504 is infinity (so |x| >= 65520 overflows). */
+static float round_fp16(float xf)
+{
+    const double x = (double)xf;
+    if (x == 0.0 || !isfinite(x)) return xf;
+    const double ax = fabs(x);
+    int e;
+    frexp(ax, &e);
+    double ulp = ldexp(1.0, e - 11);
+    const double min_ulp = ldexp(1.0, -24);
+    if (ulp < min_ulp) ulp = min_ulp;
+    const double lo = floor(ax / ulp) * ulp;
+    const double hi = lo + ulp;
+    double r;
+    if (ax - lo < hi - ax) r = lo;
+    else if (ax - lo > hi - ax) r = hi;
+    else r = (fmod(lo / ulp, 2.0) == 0.0) ? lo : hi;
+    if (r > 65504.0) r = INFINITY;
+    return (float)(x < 0 ? -r : r);
+}
+
+/* hi = RN_fp16(x), lo = RN_fp16(x - hi) (x - hi is exact in fp32). */
+void oracle_split_fp16(int64_t count, const float *x, float *hi, float *lo)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        const float h = round_fp16(x[i]);
+        const float r = x[i] - h;
+        hi[i] = h;
+        lo[i] = round_fp16(r);
+    }
+}
+
 /* Single rounding, exposed for the pins. */
 float oracle_round_sig_f32(float x, int bits) { return round_sig(x, bits); }
+float oracle_round_fp16_f32(float x) { return round_fp16(x); }

@@ -404,6 +404,53 @@ def test_tf32_split_matches_bit_reference():
     assert np.array_equal(lo, _tf32_bits_reference((x - hi).astype(np.float32)))
 
 
+def _fp16_cases():
+    # normals over the whole binary16 range, the subnormal range, exact
+    # halfway points (ties) at several exponents, the overflow threshold
+    x = [synth.normal(128, 9, 0).reshape(-1),
+         synth.normal(64, 9, 1).reshape(-1) * 1e4,
+         synth.normal(64, 9, 2).reshape(-1) * 3e-5,   # around the normal/subnormal edge
+         synth.normal(64, 9, 3).reshape(-1) * 1e-7]   # subnormal, some below half the spacing
+    ties = []
+    for e in (-20, -14, -3, 0, 7, 14):
+        ulp = 2.0 ** (e - 10) if e >= -14 else 2.0 ** -24
+        for k in (1025, 1026, 2047, 1500):
+            ties.append((k + 0.5) * ulp * (1 if k % 2 else -1))
+    ties += [65504.0, 65519.0, 65520.0, 65536.0, -65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26, 0.0, -0.0]
+    return np.concatenate(x + [np.array(ties)]).astype(np.float32)
+
+
+def test_fp16_rounding_matches_library_conversion():
+    # binary16 round to nearest even, subnormals and overflow included, equals
+    # numpy's float32 -> float16 conversion element for element
+    x = _fp16_cases()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).astype(np.float32)
+    got = np.array([oracle.round_fp16(float(v)) for v in x], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    hi, lo = oracle.split_fp16(x)
+    assert np.array_equal(hi.view(np.uint32), ref.view(np.uint32))
+    fin = np.isfinite(hi)
+    r = (x[fin] - hi[fin]).astype(np.float32)
+    assert np.array_equal(lo[fin].view(np.uint32), r.astype(np.float16).astype(np.float32).view(np.uint32))
+    assert not np.all(fin)  # the overflow cases are there
+
+
+def test_fp16_split_reconstruction_error():
+    # hi and lo carry 11 bits each where lo stays normal: the remainder is
+    # below 2^-22 relative; below that, lo rounds to the fixed subnormal
+    # spacing 2^-24, an absolute error of at most 2^-25
+    x = np.concatenate([synth.normal(512, 10, 0).reshape(-1),
+                        synth.normal(64, 10, 1).reshape(-1) * 1e-5]).astype(np.float32)
+    hi, lo = oracle.split_fp16(x)
+    x64 = x.astype(np.float64)
+    err = np.abs(x64 - (hi.astype(np.float64) + lo.astype(np.float64)))
+    assert np.all(err <= np.maximum(2.0 ** -22 * np.abs(x64), 2.0 ** -25))
+    big = np.abs(x64) >= 2.0 ** -3  # lo normal: the relative bound alone
+    assert np.all(err[big] <= 2.0 ** -22 * np.abs(x64[big]))
+    assert (err[big] / np.abs(x64[big])).max() > 2.0 ** -30  # and lo is really rounded
+
+
 @pytest.mark.parametrize("split,bits", [(oracle.split_bf16, 8), (oracle.split_tf32, 11)])
 def test_split_reconstruction_error(split, bits):
     x = synth.normal(512, 8, 0).reshape(-1)
