@@ -113,6 +113,11 @@ def measured_traffic(n, depth, kernel, combine=0):
         return None
 
 
+def split_dtype(stark, name):
+    return {"bf16": stark.DType.F32_SPLIT_BF16, "tf32": stark.DType.F32_SPLIT_TF32,
+            "fp16": stark.DType.F32_SPLIT_FP16}[name]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -512,7 +517,7 @@ def run_sharded(args, stark, synth, torch, dist, rank, world, local):
     value = 2 n^3 / the slowest rank's time ("scaling": "strong")."""
     from paper_1811_07325_gb300 import shard
     n, d = args.n, args.depth
-    dt = stark.DType.F32_SPLIT_BF16 if args.dtype == "bf16" else stark.DType.F32_SPLIT_TF32
+    dt = split_dtype(stark, args.dtype)
     A = torch.from_numpy(synth.normal(n, args.seed, 0)).cuda()
     B = torch.from_numpy(synth.normal(n, args.seed, 1)).cuda()
     plan = shard.shard_plan(n, d, dt, world, rank)
@@ -628,7 +633,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--depth", type=int, default=2)
-    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32", "fp16"])
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--ref-rows", type=int, default=0,
@@ -676,7 +681,7 @@ def main():
     from paper_1811_07325_gb300 import stark, synth
 
     n, d = args.n, args.depth
-    dt = stark.DType.F32_SPLIT_BF16 if args.dtype == "bf16" else stark.DType.F32_SPLIT_TF32
+    dt = split_dtype(stark, args.dtype)
     if args.shard:
         out = run_sharded(args, stark, synth, torch, dist, rank, world, local)
         if rank == 0:
@@ -818,7 +823,7 @@ def main():
                 "peak_sustained": pk["bf16_sustained"], "frac_of_sustained": achieved / pk["bf16_sustained"],
                 "algorithmic_flops_per_launch": leaf_flops,
                 "launch_ms": phases["leaf_kernel"]}
-    esz = 4 if args.dtype == "bf16" else 8  # bytes per leaf element per operand (hi + lo)
+    esz = 8 if args.dtype == "tf32" else 4  # bytes per leaf element per operand (hi + lo)
     operand_bytes = 2 * plan.leaves * plan.leaf ** 2 * esz
     divide_bytes = 2 * (n * n * 4) + operand_bytes  # read A, B; write every leaf operand (hi+lo)
     # the combine's HBM bytes: fused, C cleared and written once (the L2
@@ -904,14 +909,13 @@ def main():
 
     line["comparators"] = comparators
     progress("comparators done")
-    tf32 = None
+    tf32 = fp16 = None
     if rank == 0 and not args.no_tf32 and args.dtype == "bf16":
-        # the same product with 3xTF32 leaves, for comparison
+        # the same product with 3xTF32 and with 3xFP16 leaves, each also with
+        # accumulator promotion every 256 of K (one tensor-core accumulation
+        # then spans 256 instead of the leaf side)
         del C
         torch.cuda.empty_cache()
-        # (and again with accumulator promotion every 256 of K: the tensor
-        # core's own accumulation then spans 256 instead of the leaf side)
-        p32 = stark.Plan(n, d, stark.DType.F32_SPLIT_TF32)
         C32 = torch.empty_like(A)
         if not args.no_check:
             import oracle
@@ -920,7 +924,7 @@ def main():
             if abs_prod is None:
                 abs_prod = oracle.gemm_rows(np.abs(A_h.numpy()), np.abs(B_h.numpy()), rows)
 
-        def tf32_leg(promotion):
+        def split_leg(p32, promotion):
             p32.set_promotion(promotion)
             for _ in range(2):
                 p32.mul(A, B, C32)
@@ -932,9 +936,10 @@ def main():
                 p32.mul(A, B, C32)
             e1.record()
             torch.cuda.synchronize()
+            p32.check()
             ms32 = e0.elapsed_time(e1) / 5
             leg = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32,
-                   "phases_ms": p32.phase_ms()}
+                   "phases_ms": p32.phase_ms(), "combine": p32.combine}
             p32.set_timing(0)
             if not args.no_check:
                 r = stark.error_norms(A, B, C32, rows, want, abs_prod)
@@ -942,16 +947,26 @@ def main():
                                         "rel_rms": r["rel_rms"], "componentwise_max": r["max_componentwise"]}
             return leg
 
-        tf32 = tf32_leg(0)
-        try:
-            tf32["promoted_k256"] = tf32_leg(256)
-        except stark.StarkError as ex:  # report, do not hide
-            tf32["promoted_k256"] = str(ex)
-        p32.close()
+        legs = {}
+        for name in ("tf32", "fp16"):
+            p32 = stark.Plan(n, d, split_dtype(stark, name))
+            try:
+                p32.set_combine(plan.combine)  # the main line's combine mode
+                legs[name] = split_leg(p32, 0)
+                try:
+                    legs[name]["promoted_k256"] = split_leg(p32, 256)
+                except stark.StarkError as ex:  # report, do not hide
+                    legs[name]["promoted_k256"] = str(ex)
+            except stark.StarkError as ex:
+                legs[name] = str(ex)
+            p32.close()
+            torch.cuda.empty_cache()
+        tf32, fp16 = legs["tf32"], legs["fp16"]
         del C32
         torch.cuda.empty_cache()
 
     line["tf32"] = tf32
+    line["fp16"] = fp16
     progress("tf32 leg done")
     int64 = None
     if rank == 0 and not args.no_batch:

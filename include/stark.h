@@ -49,7 +49,15 @@ typedef enum {
   STARK_F32_SPLIT_BF16 = 1, /* fp32 in/out; leaves as 3 bf16 products (hi*hi + hi*lo +  */
                             /* lo*hi, x = hi + lo) on tcgen05 tensor cores, fp32 accum. */
   STARK_F32_SPLIT_TF32 = 2, /* fp32 in/out; the same with TF32 halves                   */
-  STARK_I64 = 3             /* int64 in/out; exact modulo 2^64 (two's complement)       */
+  STARK_I64 = 3,            /* int64 in/out; exact modulo 2^64 (two's complement)       */
+  STARK_F32_SPLIT_FP16 = 4  /* fp32 in/out; the same with IEEE fp16 halves (11 bits     */
+                            /* each: about 22 bits per operand at the bf16 MMA rate).   */
+                            /* Every leaf operand sum must stay below 65504 in         */
+                            /* magnitude: a larger one sets the plan's device range    */
+                            /* flag (stark_plan_check: STARK_EINVAL, product invalid). */
+                            /* Sums below 2^-14 keep their fp16 value to 2^-24 (an     */
+                            /* absolute error of at most 2^-25 per split). Plans only: */
+                            /* batches, the server and stark_mul_noalloc refuse it.    */
 } stark_dtype;
 
 typedef enum {

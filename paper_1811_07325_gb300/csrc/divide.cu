@@ -45,6 +45,8 @@ cudaError_t launch_divide(const DivideArgs& a, int depth, int side, InType in, O
     return side == 0 ? by_depth<float, kOutSplitBf16, 0>(a, depth, st) : by_depth<float, kOutSplitBf16, 1>(a, depth, st);
   if (in == kInF32 && out == kOutSplitTf32)
     return side == 0 ? by_depth<float, kOutSplitTf32, 0>(a, depth, st) : by_depth<float, kOutSplitTf32, 1>(a, depth, st);
+  if (in == kInF32 && out == kOutSplitFp16)
+    return side == 0 ? by_depth<float, kOutSplitFp16, 0>(a, depth, st) : by_depth<float, kOutSplitFp16, 1>(a, depth, st);
   if (in == kInF64 && out == kOutPlain)
     return side == 0 ? by_depth<double, kOutPlain, 0>(a, depth, st) : by_depth<double, kOutPlain, 1>(a, depth, st);
   if (in == kInI64 && out == kOutPlain)

@@ -3,6 +3,7 @@
 // (divide_top.cu), which are compiled as separate translation units.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <type_traits>
 
@@ -124,6 +125,22 @@ struct Emitter {
       }
       store_vec(reinterpret_cast<__nv_bfloat16*>(hi) + at, h);
       store_vec(reinterpret_cast<__nv_bfloat16*>(lo) + at, l);
+    } else if constexpr (OUT == kOutSplitFp16) {
+      // hi = RN_fp16(x), lo = RN_fp16(x - hi) (x - hi exact in fp32); a sum
+      // beyond the fp16 range (hi infinite) raises the plan's range flag
+      __half2 h[(VEC + 1) / 2], l[(VEC + 1) / 2];
+      bool bad = false;
+#pragma unroll
+      for (int e = 0; e < VEC / 2; ++e) {
+        h[e] = __floats2half2_rn(x.v[2 * e], x.v[2 * e + 1]);
+        const float2 hf = __half22float2(h[e]);
+        bad |= !(fabsf(hf.x) <= 65504.f) || !(fabsf(hf.y) <= 65504.f);
+        l[e] = __floats2half2_rn(x.v[2 * e] - hf.x, x.v[2 * e + 1] - hf.y);
+      }
+      static_assert(VEC % 2 == 0, "fp16 halves are stored in pairs");
+      if (bad) record_error(range_flag, kDevFp16Range);
+      store_vec(reinterpret_cast<__half2*>(hi) + at / 2, h);
+      store_vec(reinterpret_cast<__half2*>(lo) + at / 2, l);
     } else if constexpr (OUT == kOutSplitTf32) {
       float h[VEC], l[VEC];
 #pragma unroll

@@ -120,6 +120,7 @@ bool divide_staged_fits(int64_t L) { return L > 0 && L % 128 == 0; }
 cudaError_t launch_divide_staged(const DivideArgs& a, int side, OutMode out, cudaStream_t st) {
   if (out == kOutSplitBf16) return side == 0 ? launch_staged<kOutSplitBf16, 0>(a, st) : launch_staged<kOutSplitBf16, 1>(a, st);
   if (out == kOutSplitTf32) return side == 0 ? launch_staged<kOutSplitTf32, 0>(a, st) : launch_staged<kOutSplitTf32, 1>(a, st);
+  if (out == kOutSplitFp16) return side == 0 ? launch_staged<kOutSplitFp16, 0>(a, st) : launch_staged<kOutSplitFp16, 1>(a, st);
   return cudaErrorInvalidValue;
 }
 

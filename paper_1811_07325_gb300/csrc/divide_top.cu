@@ -41,6 +41,9 @@ cudaError_t launch_divide_top(const DivideArgs& a, int depth, int side, InType i
   if (in == kInF32 && out == kOutSplitTf32)
     return side == 0 ? by_depth_top<float, kOutSplitTf32, 0>(a, depth, st)
                      : by_depth_top<float, kOutSplitTf32, 1>(a, depth, st);
+  if (in == kInF32 && out == kOutSplitFp16)
+    return side == 0 ? by_depth_top<float, kOutSplitFp16, 0>(a, depth, st)
+                     : by_depth_top<float, kOutSplitFp16, 1>(a, depth, st);
   if (in == kInF64 && out == kOutPlain)
     return side == 0 ? by_depth_top<double, kOutPlain, 0>(a, depth, st) : by_depth_top<double, kOutPlain, 1>(a, depth, st);
   if (in == kInI64 && out == kOutPlain)

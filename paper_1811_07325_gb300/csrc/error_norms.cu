@@ -161,8 +161,7 @@ extern "C" stark_status stark_error_norms(int64_t n, stark_dtype dtype, const vo
                                           const double* absprod, stark_error_report* out, void* stream) {
   if (!out || n < 0 || nrows < 0 || nrows > n || (n > 0 && (!A || !B)) || (nrows > 0 && (!C || !rows || !want)))
     return STARK_EINVAL;
-  if (dtype != STARK_F64 && dtype != STARK_F32_SPLIT_BF16 && dtype != STARK_F32_SPLIT_TF32 && dtype != STARK_I64)
-    return STARK_EINVAL;
+  if (dtype != STARK_F64 && dtype != STARK_I64 && !is_split(dtype)) return STARK_EINVAL;
   *out = stark_error_report{};
   out->compared = nrows * n;
   if (n == 0) return STARK_OK;

@@ -222,9 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_tf32(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
               mma_tf32(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
             } else {
-              mma_f16(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
-              mma_f16(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
-              mma_f16(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
+              const uint32_t idesc = p.fp16 ? idesc_as_fp16(Cfg::IDESC) : Cfg::IDESC;  // fp16 or bf16 halves
+              mma_f16(d_tmem, a_lo, b_hi, idesc, first);
+              mma_f16(d_tmem, a_hi, b_lo, idesc, 1u);
+              mma_f16(d_tmem, a_hi, b_hi, idesc, 1u);
             }
           }
           issued = true;

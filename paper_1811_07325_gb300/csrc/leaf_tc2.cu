@@ -258,9 +258,10 @@ __global__ void __launch_bounds__(kThreads2, 1)
               mma2_tf32(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
               mma2_tf32(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
             } else {
-              mma2_f16(d_tmem, a_lo, b_hi, Cfg::IDESC, first);
-              mma2_f16(d_tmem, a_hi, b_lo, Cfg::IDESC, 1u);
-              mma2_f16(d_tmem, a_hi, b_hi, Cfg::IDESC, 1u);
+              const uint32_t idesc = p.fp16 ? idesc_as_fp16(Cfg::IDESC) : Cfg::IDESC;  // fp16 or bf16 halves
+              mma2_f16(d_tmem, a_lo, b_hi, idesc, first);
+              mma2_f16(d_tmem, a_hi, b_lo, idesc, 1u);
+              mma2_f16(d_tmem, a_hi, b_hi, idesc, 1u);
             }
           }
           issued = true;

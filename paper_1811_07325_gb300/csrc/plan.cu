@@ -169,21 +169,21 @@ int64_t pow7i(int d) {
   return p;
 }
 
-int tile_granularity(stark_dtype dt) { return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? 128 : 64; }
+int tile_granularity(stark_dtype dt) { return is_split(dt) ? 128 : 64; }
 
 int64_t padded_side(int64_t n, int depth, stark_dtype dt) {
   const int64_t g = ((int64_t)1 << depth) * tile_granularity(dt);
   return std::max<int64_t>(g, (n + g - 1) / g * g);
 }
 
-size_t element_size(stark_dtype dt) { return dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32 ? 4 : 8; }
+size_t element_size(stark_dtype dt) { return is_split(dt) ? 4 : 8; }
 
 // Device bytes of the leaf operand planes of one product.
 int64_t operand_bytes(int64_t n, int depth, stark_dtype dt) {
   const int64_t npad = padded_side(n, depth, dt);
   const int64_t L = npad >> depth;
   const int64_t P = pow7i(depth);
-  const int64_t per = dt == STARK_F32_SPLIT_BF16 ? 4 : 8;  // hi+lo bf16, hi+lo tf32, or one 8-byte value
+  const int64_t per = half_split(dt) ? 4 : 8;  // hi+lo bf16 or fp16, hi+lo tf32, or one 8-byte value
   return 2 * P * L * L * per;
 }
 
@@ -211,9 +211,10 @@ double model_seconds(int64_t n, int depth, stark_dtype dt) {
   double flops = 2.0 * P * L * L * L, rate, items, slots;
   switch (dt) {
     case STARK_F32_SPLIT_BF16:
+    case STARK_F32_SPLIT_FP16:
     case STARK_F32_SPLIT_TF32: {
       flops *= 3;
-      rate = dt == STARK_F32_SPLIT_BF16 ? 1.76e15 : 0.93e15;
+      rate = half_split(dt) ? 1.76e15 : 0.93e15;
       const bool pair = (npad >> depth) % 256 == 0;  // 256 x 256 tiles on CTA pairs, else 128 x 128 on one CTA
       const double t = pair ? 256.0 : 128.0;
       items = P * (L / t) * (L / t);
@@ -232,8 +233,7 @@ double model_seconds(int64_t n, int depth, stark_dtype dt) {
   // depth 3: the split dtypes divide in one staged pass per operand (leaf
   // side a multiple of 128); otherwise one launch per top-level product,
   // reading the input three times
-  const bool staged = depth == 3 && (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) &&
-                      divide_staged_fits(npad >> depth);
+  const bool staged = depth == 3 && is_split(dt) && divide_staged_fits(npad >> depth);
   const bool per_top = depth == 3 && !staged;
   const double in_bytes = 2.0 * (double)n * n * esz * (per_top ? 3.0 : 1.0);
   const double ws = (double)operand_bytes(n, depth, dt);
@@ -301,12 +301,10 @@ stark_status stark_plan_ex(int64_t n, int depth, stark_dtype dt, unsigned flags,
   if (flags & ~(unsigned)STARK_PLAN_PEEL) return STARK_EINVAL;
   *out = nullptr;
   if (n < 0 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;
-  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
-    return STARK_EINVAL;
+  if (dt != STARK_F64 && dt != STARK_I64 && !is_split(dt)) return STARK_EINVAL;
   if (n > (int64_t)1 << 20) return STARK_EINVAL;
   if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
-  if (depth < 0)
-    depth = (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
+  if (depth < 0) depth = is_split(dt) ? autotune_depth(n, dt) : choose_depth(n, dt);
   auto* p = new (std::nothrow) stark_plan_s();
   if (!p) return STARK_ENOMEM;
   stark_status st = plan_init(p, n, depth, dt, (flags & STARK_PLAN_PEEL) != 0);
@@ -582,7 +580,7 @@ static stark_status plan_tune_combine(stark_plan_t p) {
 
 // Workspace for `planes_per_half` leaves per operand side, with its maps.
 static stark_status plan_alloc_operands(stark_plan_s* p, int64_t planes) {
-  const int64_t per = p->dt == STARK_F32_SPLIT_BF16 ? 4 : 8;  // bytes per leaf element per operand
+  const int64_t per = half_split(p->dt) ? 4 : 8;  // bytes per leaf element per operand
   const int64_t bytes = planes * p->L * p->L * per;
   if (cudaDeviceSynchronize() != cudaSuccess) return STARK_ECUDA;
   const int64_t old = p->P_ws * p->L * p->L * per;
@@ -731,7 +729,7 @@ stark_status stark_plan_check(stark_plan_t p, void* stream) {
   if (cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STARK_ECUDA;
   if (e != 0) {
     cudaMemset(p->d_err, 0, sizeof(int));
-    return e == kDevIntRange ? STARK_EINVAL : STARK_ETIMEOUT;
+    return (e == kDevIntRange || e == kDevFp16Range) ? STARK_EINVAL : STARK_ETIMEOUT;
   }
   return STARK_OK;
 }
@@ -801,7 +799,7 @@ bool traversal_supported(int depth, stark_dtype dt, int levels) {
   if (levels == 0) return true;
   // the subtree below `levels` is at most 2 (one level) or 1 (two levels) deep
   if (levels < 0 || levels > 2 || depth < levels || depth > 3) return false;
-  return levels == 1 || dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+  return levels == 1 || is_split(dt);
 }
 
 stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bool peel, int dfs) {
@@ -809,7 +807,7 @@ stark_status plan_init(stark_plan_s* p, int64_t n, int depth, stark_dtype dt, bo
   p->n = n;
   p->depth = depth;
   p->dt = dt;
-  p->is_tc = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+  p->is_tc = is_split(dt);
   p->esz = element_size(dt);
   const int64_t g = ((int64_t)1 << depth) * tile_granularity(dt);
   p->peel = (peel && n >= g) ? n % g : 0;
@@ -871,6 +869,8 @@ stark_status plan_operand_maps(stark_plan_s* p, int64_t planes) {
   p->has_mapbp = false;
   if (!p->is_tc) return STARK_OK;
   const bool tf32 = p->dt == STARK_F32_SPLIT_TF32;
+  // (16-bit planes -- bf16 or fp16 halves -- use bf16 maps: a tiled load
+  // copies the 2-byte elements bit for bit and fills out-of-range with 0)
   // X: K-major 128-byte rows.  Y: bf16 MN-major 64 x 64 boxes; tf32 either
   // MN-major 32 x 32 boxes with the 32-byte-atom swizzle, or (transposed
   // planes) K-major boxes of a whole tile's rows
@@ -926,22 +926,26 @@ stark_status plan_divide_top(stark_plan_s* p, const void* A, const void* B, cuda
   const int depth = p->depth - lv;
   // bytes per element of a (hi) plane: bf16 for 3xBF16 and for bounded
   // integers, tf32 in fp32 containers, else the input type
-  const size_t ehi = (p->dt == STARK_F32_SPLIT_BF16 || p->int_tc) ? 2 : p->dt == STARK_F32_SPLIT_TF32 ? 4 : 8;
+  const size_t ehi = (half_split(p->dt) || p->int_tc) ? 2 : p->dt == STARK_F32_SPLIT_TF32 ? 4 : 8;
   const size_t off = (size_t)plane_off * (size_t)p->L * p->L * ehi;  // first output plane
   // the core of A and B (all of them unless an edge is peeled), row stride n
   DivideArgs da{A, core_side(p), npad, p->L, static_cast<char*>(p->X) + off, nullptr, p->d_err, top, p->n};
   DivideArgs db{B, core_side(p), npad, p->L, static_cast<char*>(p->Y) + off, nullptr, p->d_err, top, p->n};
   da.top_levels = db.top_levels = lv;
   InType in = p->dt == STARK_F64 ? kInF64 : p->dt == STARK_I64 ? kInI64 : kInF32;
-  OutMode om = p->dt == STARK_F32_SPLIT_BF16 ? kOutSplitBf16 : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32 : kOutPlain;
+  OutMode om = p->dt == STARK_F32_SPLIT_BF16   ? kOutSplitBf16
+              : p->dt == STARK_F32_SPLIT_FP16 ? kOutSplitFp16
+              : p->dt == STARK_F32_SPLIT_TF32 ? kOutSplitTf32
+                                              : kOutPlain;
   if (p->int_tc) om = kOutBf16Exact;  // bounded integers: exact bf16 operands, range checked
   if (p->is_tc) {
-    const int64_t half = p->P_ws * p->L * p->L * (p->dt == STARK_F32_SPLIT_BF16 ? 2 : 4);
+    const int64_t half = p->P_ws * p->L * p->L * (half_split(p->dt) ? 2 : 4);
     da.out_lo = static_cast<char*>(p->X) + half + off;
     db.out_lo = static_cast<char*>(p->Y) + half + off;
   }
   stark_status st = STARK_OK;
-  if (top < 0 && depth == 3 && (om == kOutSplitBf16 || om == kOutSplitTf32) && divide_staged_fits(p->L)) {
+  if (top < 0 && depth == 3 && (om == kOutSplitBf16 || om == kOutSplitTf32 || om == kOutSplitFp16) &&
+      divide_staged_fits(p->L)) {
     // breadth first at depth 3, split fp32: one pass per operand, the
     // input tile staged in shared memory
     st = to_status(launch_divide_staged(da, 0, om, s));
@@ -1009,7 +1013,7 @@ static bool plan_deterministic(const stark_plan_s* p, int64_t lb, int64_t le) {
 static bool plan_sib(const stark_plan_s* p, int64_t lb, int64_t le) {
   return p->is_tc && p->combine_mode == 3 && p->q_planes && lb == 0 && le == p->P && p->pair_mode == 2 &&
          p->bn == 256 && p->L % 256 == 0 && !p->dfs && !p->deep_pipeline && p->depth >= 1 &&
-         (p->dt == STARK_F32_SPLIT_BF16 || p->tf32_mn);
+         (half_split(p->dt) || p->tf32_mn);
 }
 
 // Whether a separate pass writes every element of C (combine modes 2 and 3):
@@ -1055,6 +1059,7 @@ static stark_status plan_leaves(stark_plan_s* p, void* C, int64_t lb, int64_t le
       tmC = p->tmQ;
     }
     a.pair = p->pair_mode;
+    a.fp16 = p->dt == STARK_F32_SPLIT_FP16 ? 1 : 0;
     a.band = p->raster_band;
     a.b_mn = p->tf32_mn;
     a.row_bytes = 128;

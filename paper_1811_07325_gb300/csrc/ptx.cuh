@@ -21,6 +21,7 @@ enum DeviceError : int {
   kDevTimeoutTest = 5,      // the self-test wait on a flag that nobody sets
   kDevBadConfig = 6,        // launch parameters inconsistent with the kernel
   kDevIntRange = 7,         // an integer leaf operand exceeded the declared exact range
+  kDevFp16Range = 8,        // a 3xFP16 leaf operand sum beyond the fp16 range
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -457,6 +458,12 @@ template <int M, int N, bool TF32, bool B_MN_MAJOR>
 __host__ __device__ constexpr uint32_t make_idesc() {
   return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((B_MN_MAJOR ? 1u : 0u) << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The kind::f16 descriptor above with A and B both fp16 (format 0) instead of
+// both bf16: the two format fields change together, never one alone.
+__host__ __device__ constexpr uint32_t idesc_as_fp16(uint32_t idesc_bf16) {
+  return idesc_bf16 & ~((7u << 7) | (7u << 10));
 }
 
 }  // namespace stark

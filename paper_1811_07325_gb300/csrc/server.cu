@@ -483,6 +483,7 @@ stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_s
 stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dtype dt, int staged, int32_t* depth,
                                     int32_t* levels, int64_t* bytes) {
   if (n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
+  if (dt == STARK_F32_SPLIT_FP16) return STARK_EUNSUPPORTED;  // plans only
   if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
     return STARK_EINVAL;
   const bool split = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
@@ -498,6 +499,7 @@ stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dt
 stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const void* A, const void* B, void* C,
                           uint64_t* req_id) {
   if (!s || !req_id || n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
+  if (dt == STARK_F32_SPLIT_FP16) return STARK_EUNSUPPORTED;  // plans only
   if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
     return STARK_EINVAL;
   if (n > 0 && (!A || !B || !C)) return STARK_EINVAL;

@@ -52,8 +52,15 @@ void build_quadrant_table(int depth, int side, std::vector<int32_t>& count, std:
 // Row/column element offsets of base-4 quadrant path q for side npad.
 void quadrant_offsets(int depth, int64_t npad, int32_t q, int64_t* row, int64_t* col);
 
+// The fp32 dtypes with split-precision tensor-core leaves, and among them
+// those whose halves are 16-bit (bf16 or fp16: kind::f16 MMAs, 2-byte planes).
+inline bool is_split(stark_dtype dt) {
+  return dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32 || dt == STARK_F32_SPLIT_FP16;
+}
+inline bool half_split(stark_dtype dt) { return dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_FP16; }
+
 // ------------------------------------------------------------------ launches
-enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2, kOutBf16Exact = 3 };
+enum OutMode { kOutSplitBf16 = 0, kOutSplitTf32 = 1, kOutPlain = 2, kOutBf16Exact = 3, kOutSplitFp16 = 4 };
 enum InType { kInF32 = 0, kInF64 = 1, kInI64 = 2 };
 
 struct DivideArgs {
@@ -152,6 +159,8 @@ struct LeafTcArgs {
                        // run back to back at one tile position and their tiles are stored or added
                        // into the parent's quadrants (tmC = parent planes [P/7][2L][2L]); leaf
                        // range of whole parents
+  int32_t fp16;        // 1: the 16-bit planes hold fp16 halves (kind::f16 A and B format fp16
+                       // instead of bf16); 0 for every other dtype and for grouped launches
   int32_t promo_kb;    // > 0 (CTA-pair kernel): accumulator promotion -- every promo_kb K blocks
                        // the tensor-core partial sum is added into a running fp32 sum on the
                        // CUDA cores (round to nearest); 0: one tensor-core accumulation over K

@@ -25,6 +25,7 @@ class DType(enum.IntEnum):
     F32_SPLIT_BF16 = 1
     F32_SPLIT_TF32 = 2
     I64 = 3
+    F32_SPLIT_FP16 = 4
 
 
 class Status(enum.IntEnum):
@@ -135,13 +136,13 @@ _TORCH_DTYPE = {}
 
 def _torch_dtype(dt):
     import torch
-    return {DType.F64: torch.float64, DType.F32_SPLIT_BF16: torch.float32,
-            DType.F32_SPLIT_TF32: torch.float32, DType.I64: torch.int64}[DType(dt)]
+    return {DType.F64: torch.float64, DType.F32_SPLIT_BF16: torch.float32, DType.F32_SPLIT_TF32: torch.float32,
+            DType.F32_SPLIT_FP16: torch.float32, DType.I64: torch.int64}[DType(dt)]
 
 
 def _numpy_dtype(dt):
-    return {DType.F64: np.float64, DType.F32_SPLIT_BF16: np.float32,
-            DType.F32_SPLIT_TF32: np.float32, DType.I64: np.int64}[DType(dt)]
+    return {DType.F64: np.float64, DType.F32_SPLIT_BF16: np.float32, DType.F32_SPLIT_TF32: np.float32,
+            DType.F32_SPLIT_FP16: np.float32, DType.I64: np.int64}[DType(dt)]
 
 
 def _stream_handle(stream):
@@ -273,6 +274,8 @@ class Plan:
         P, L = info.workspace_leaves, self.leaf  # a shard's workspace holds its subtrees' leaves only
         if self.dtype == DType.F32_SPLIT_BF16:
             shape, ts, view = (2 * P, L, L), "<i2", torch.bfloat16
+        elif self.dtype == DType.F32_SPLIT_FP16:
+            shape, ts, view = (2 * P, L, L), "<i2", torch.float16
         elif self.dtype == DType.F32_SPLIT_TF32:
             shape, ts, view = (2 * P, L, L), "<f4", None
         elif self.dtype == DType.F64:

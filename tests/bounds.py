@@ -34,8 +34,11 @@ import math
 
 import numpy as np
 
-U_SPLIT = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22}
-MMA_K = {"F32_SPLIT_BF16": 16, "F32_SPLIT_TF32": 8}
+U_SPLIT = {"F32_SPLIT_BF16": 2.0 ** -16, "F32_SPLIT_TF32": 2.0 ** -22, "F32_SPLIT_FP16": 2.0 ** -22}
+MMA_K = {"F32_SPLIT_BF16": 16, "F32_SPLIT_TF32": 8, "F32_SPLIT_FP16": 16}
+# fp16 halves: below fp16's normal range (2^-14) values are kept to the
+# fixed spacing 2^-24, so a split's residual is max(2^-22 |x|, 2^-25)
+FLOOR = {"F32_SPLIT_FP16": 2.0 ** -25}
 
 
 def _span(L, kc):
@@ -55,6 +58,15 @@ def componentwise_c(dtype, L, d, kc=None):
 def rms_bound(dtype, L, d, kc=None):
     span, adds = _span(L, kc)
     return 2 ** d * U_SPLIT[dtype] + 3 * (span / MMA_K[dtype]) * 2.0 ** -23 + adds * 2.0 ** -24
+
+
+def floor_majorant(oracle, A, B, d, L):
+    """The absolute part of the split residual: an operand element off by up
+    to f absolutely moves C_ij by at most f times this majorant (Alg. 1 on
+    |A| with the all-ones matrix, and on the all-ones matrix with |B|; the
+    ones cover the n x n inputs, the zero padding splits exactly)."""
+    J = np.ones(A.shape)
+    return majorant(oracle, A, J, d, L) + majorant(oracle, J, B, d, L)
 
 
 def infer_depth(n, L):

@@ -134,7 +134,7 @@ def test_int64_equals_oracle_strassen(S):
 
 
 # ----------------------------------------------------------------- divide phase
-@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
+@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32", "F32_SPLIT_FP16"])
 @pytest.mark.parametrize("n,d", [(256, 0), (300, 1), (500, 2), (1000, 3), (1001, 4),
                                  # depth 3 with L a multiple of 256: the staged one-pass divide
                                  # (aligned rows; ragged rows and columns; unaligned row stride)
@@ -143,7 +143,8 @@ def test_divide_split_bit_exact(S, dtype, n, d):
     dt = S.DType[dtype]
     A = synth.normal(n, 7 + d, 0)
     B = synth.normal(n, 7 + d, 1)
-    split = oracle.split_bf16 if dt == S.DType.F32_SPLIT_BF16 else oracle.split_tf32
+    split = {S.DType.F32_SPLIT_BF16: oracle.split_bf16, S.DType.F32_SPLIT_TF32: oracle.split_tf32,
+             S.DType.F32_SPLIT_FP16: oracle.split_fp16}[dt]
     with S.Plan(n, d, dt) as p:
         xa = oracle.strassen_operands(A, p.n_pad, d, "A")
         yb = oracle.strassen_operands(B, p.n_pad, d, "B")
@@ -242,8 +243,12 @@ def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None
     if A is not None and want.shape[0] == n and n <= 2048:
         S = bounds.majorant(oracle, A.astype(np.float64), B.astype(np.float64), d, L)
         c = bounds.componentwise_c(dtype, L, d, kc)
-        excess = np.abs(diff) / np.maximum(c * S, 1e-300)
-        assert np.all(np.abs(diff) <= c * S), excess.max()
+        bound = c * S
+        if dtype in bounds.FLOOR:
+            bound = bound + bounds.FLOOR[dtype] * bounds.floor_majorant(
+                oracle, A.astype(np.float64), B.astype(np.float64), d, L)
+        excess = np.abs(diff) / np.maximum(bound, 1e-300)
+        assert np.all(np.abs(diff) <= bound), excess.max()
     else:
         assert n >= 64, "small products need the inputs for the componentwise bound"
     if n >= 64:
@@ -252,7 +257,7 @@ def check_split(C, want, A64norm, B64norm, dtype, A=None, B=None, d=None, L=None
     return ratio, rel_rms
 
 
-@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32"])
+@pytest.mark.parametrize("dtype", ["F32_SPLIT_BF16", "F32_SPLIT_TF32", "F32_SPLIT_FP16"])
 @pytest.mark.parametrize("n,depths", [(1, [0, 1]), (37, [0, 1]), (100, [0, 1]), (384, [0, 1]), (1000, [1, 2, 3]),
                                       (2048, [0, 2, 3])])
 def test_split_within_bound(S, dtype, n, depths):
@@ -770,6 +775,8 @@ def test_sibling_fold_conditions_and_fallbacks(S):
     ("F32_SPLIT_TF32", 1024, 1, 256, 0),
     ("F32_SPLIT_TF32", 2048, 1, 256, 2),
     ("F32_SPLIT_TF32", 1536, 1, 512, 0),
+    ("F32_SPLIT_FP16", 2048, 1, 256, 2),
+    ("F32_SPLIT_FP16", 1001, 2, 256, 0),
 ])
 def test_promotion_matches_oracle(S, dtype, n, d, k, combine):
     # every K chunk's tensor-core partial sum joins an fp32 running sum; the
@@ -802,7 +809,7 @@ def test_promotion_matches_oracle(S, dtype, n, d, k, combine):
     assert np.abs(C1 - Cn).max() <= 1e-5 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("dtype,gain", [("F32_SPLIT_TF32", 4.0), ("F32_SPLIT_BF16", 1.0)])
+@pytest.mark.parametrize("dtype,gain", [("F32_SPLIT_TF32", 4.0), ("F32_SPLIT_BF16", 1.0), ("F32_SPLIT_FP16", 2.0)])
 def test_promotion_cuts_accumulation_error(S, dtype, gain):
     # one leaf of side 4096 (depth 0): the tensor core's accumulation over K
     # = 4096 dominates the 3xTF32 error, and it grows in proportion to the K
@@ -868,13 +875,46 @@ def test_promotion_conditions(S):
         assert e.value.status == S.Status.EUNSUPPORTED
 
 
+# ----------------------------------------------------------------- 3xFP16 range
+def test_fp16_split_range_flag(S):
+    # an operand sum beyond fp16's largest finite value (65504) raises the
+    # plan's device range flag: stark_plan_check reports EINVAL once and the
+    # flag is cleared; inputs inside the range then multiply normally
+    n, d = 512, 1
+    A = synth.normal(n, 77, 0)
+    B = synth.normal(n, 77, 1)
+    big = A.copy()
+    big[3, 5] = 40000.0  # A11 + A22 sums stay below 65520 only if A22 is small there
+    big[3 + n // 2, 5 + n // 2] = 30000.0
+    with S.Plan(n, d, S.DType.F32_SPLIT_FP16) as p:
+        p.mul(dev(big), dev(B))
+        with pytest.raises(S.StarkError) as e:
+            p.check()
+        assert e.value.status == S.Status.EINVAL
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        p.check()
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    check_split(C, want, an, bn, "F32_SPLIT_FP16", A, B, d)
+
+
+def test_fp16_split_is_refused_outside_plans(S):
+    with pytest.raises(S.StarkError) as e:
+        S.Batch([512, 1024], 1, S.DType.F32_SPLIT_FP16)
+    assert e.value.status == S.Status.EUNSUPPORTED
+    with pytest.raises(S.StarkError) as e:
+        S.server_admission(1 << 30, 1024, S.DType.F32_SPLIT_FP16)
+    assert e.value.status == S.Status.EUNSUPPORTED
+
+
 # ----------------------------------------------------------------- full size, sampled rows
 @pytest.mark.slow
 @pytest.mark.parametrize("dtype,d,combine", [("F32_SPLIT_BF16", 2, 0), ("F32_SPLIT_BF16", 3, 0),
                                              ("F32_SPLIT_TF32", 2, 0), ("F32_SPLIT_TF32", 3, 0),
                                              ("F32_SPLIT_BF16", 2, 2), ("F32_SPLIT_BF16", 3, 2),
                                              ("F32_SPLIT_BF16", 2, 3), ("F32_SPLIT_BF16", 3, 3),
-                                             ("F32_SPLIT_TF32", 3, 3)])
+                                             ("F32_SPLIT_TF32", 3, 3), ("F32_SPLIT_FP16", 2, 2),
+                                             ("F32_SPLIT_FP16", 3, 0)])
 def test_full_size_sampled_rows(S, dtype, d, combine):
     # the bench workload in the bench's launch configuration (CTA pairs;
     # fused combine, or the deterministic one of its second leg)
