@@ -953,10 +953,11 @@ def main():
             try:
                 p32.set_combine(plan.combine)  # the main line's combine mode
                 legs[name] = split_leg(p32, 0)
-                try:
-                    legs[name]["promoted_k256"] = split_leg(p32, 256)
-                except stark.StarkError as ex:  # report, do not hide
-                    legs[name]["promoted_k256"] = str(ex)
+                for kc in ((256, 512) if name == "fp16" else (256,)):
+                    try:
+                        legs[name][f"promoted_k{kc}"] = split_leg(p32, kc)
+                    except stark.StarkError as ex:  # report, do not hide
+                        legs[name][f"promoted_k{kc}"] = str(ex)
             except stark.StarkError as ex:
                 legs[name] = str(ex)
             p32.close()
