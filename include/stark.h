@@ -56,8 +56,8 @@ typedef enum {
                             /* magnitude: a larger one sets the plan's device range    */
                             /* flag (stark_plan_check: STARK_EINVAL, product invalid). */
                             /* Sums below 2^-14 keep their fp16 value to 2^-24 (an     */
-                            /* absolute error of at most 2^-25 per split). Plans only: */
-                            /* batches, the server and stark_mul_noalloc refuse it.    */
+                            /* absolute error of at most 2^-25 per split).             */
+                            /* stark_mul_noalloc is 3xBF16 only.                        */
 } stark_dtype;
 
 typedef enum {
@@ -367,7 +367,8 @@ STARK_API stark_status stark_plan_phases(stark_plan_t plan, float *out_ms, int c
 typedef struct stark_batch_s *stark_batch_t;
 
 /* A batch of `count` independent products C_i = A_i * B_i of sizes n[i] (any
- * mix), one tensor-core dtype (F32_SPLIT_BF16 or F32_SPLIT_TF32).  Every leaf
+ * mix), one tensor-core dtype (F32_SPLIT_BF16, F32_SPLIT_TF32 or
+ * F32_SPLIT_FP16).  Every leaf
  * product of every member (Alg. 4) is a work item of ONE persistent grouped
  * leaf launch, whose epilogue combines (Alg. 5) into each member's own C;
  * the member divides (Alg. 3) precede it.  The launch sequence is recorded

@@ -176,7 +176,7 @@ extern "C" {
 stark_status stark_batch_create(int32_t count, const int64_t* n, int depth, stark_dtype dt, stark_batch_t* out) {
   if (!out || !n || count <= 0 || count > 4096 || depth < -1 || depth > kMaxDepth) return STARK_EINVAL;
   *out = nullptr;
-  if (dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32) return STARK_EUNSUPPORTED;
+  if (!is_split(dt)) return STARK_EUNSUPPORTED;
   for (int i = 0; i < count; ++i)
     if (n[i] <= 0 || n[i] > (int64_t)1 << 20) return STARK_EINVAL;
   if (!device_is_sm100_family()) return STARK_EUNSUPPORTED;
@@ -375,6 +375,7 @@ stark_status stark_batch_mul(stark_batch_t b, const void* const* A, const void* 
       a.timeout_ns = kDefaultTimeoutNs;
       const bool tf32 = b->dt == STARK_F32_SPLIT_TF32;
       a.b_mn = tf32 && b->plans[0]->tf32_mn;  // every member has the plan default
+      a.fp16 = b->dt == STARK_F32_SPLIT_FP16 ? 1 : 0;
       // the two grouped launches on two branches of the graph: the second
       // takes SMs as the first one's tail frees them
       const bool both = b->split > 0 && b->split < count;

@@ -106,7 +106,7 @@ namespace {
 // Tensor-core dtypes: the measured autotuner (per size class, cached);
 // fp64/int64: the cost model.
 int depth_for(int64_t n, stark_dtype dt) {
-  return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) ? autotune_depth(n, dt) : choose_depth(n, dt);
+  return is_split(dt) ? autotune_depth(n, dt) : choose_depth(n, dt);
 }
 
 // Device bytes of a workspace for side npad over `levels` depth-first levels
@@ -118,7 +118,7 @@ size_t workspace_need(int64_t npad, int d, stark_dtype dt, int levels) {
 // Split dtypes combine a C that TMA cannot address (n % 4 != 0) in the
 // workspace's staging copy of side npad.
 bool needs_stage(int64_t n, stark_dtype dt, const void* C) {
-  return (dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32) && !c_is_tma_target(C, n);
+  return is_split(dt) && !c_is_tma_target(C, n);
 }
 size_t stage_bytes(int64_t npad) { return (size_t)npad * (size_t)staged_ld(npad) * sizeof(float); }
 
@@ -255,7 +255,7 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
   cudaStream_t st = slot.stream;
   std::vector<Request*> tc;
   for (Request* r : reqs) {
-    const bool split = r->dt == STARK_F32_SPLIT_BF16 || r->dt == STARK_F32_SPLIT_TF32;
+    const bool split = is_split(r->dt);
     // C that TMA cannot address is combined in the workspace's staging copy
     // (allocated at admission, inside the budget)
     const bool staged = needs_stage(r->n, r->dt, r->C);
@@ -322,6 +322,7 @@ stark_status launch_micro_batch(stark_server_s* s, Slot& slot, std::vector<Reque
       return STARK_ECUDA;
     LeafTcArgs a{};
     a.b_mn = tf32 && tc[0]->ws->tf32_mn;  // every workspace has the plan default
+    a.fp16 = tc[0]->dt == STARK_F32_SPLIT_FP16 ? 1 : 0;  // one dtype per micro-batch
     a.err = s->d_err;
     a.timeout_ns = kDefaultTimeoutNs;
     if (split > 0) {
@@ -483,10 +484,8 @@ stark_status stark_server_create(size_t hbm_budget_bytes, int32_t slots, stark_s
 stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dtype dt, int staged, int32_t* depth,
                                     int32_t* levels, int64_t* bytes) {
   if (n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
-  if (dt == STARK_F32_SPLIT_FP16) return STARK_EUNSUPPORTED;  // plans only
-  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
-    return STARK_EINVAL;
-  const bool split = dt == STARK_F32_SPLIT_BF16 || dt == STARK_F32_SPLIT_TF32;
+  if (dt != STARK_F64 && dt != STARK_I64 && !is_split(dt)) return STARK_EINVAL;
+  const bool split = is_split(dt);
   int d = 0, l = 0;
   if (!admission(n, dt, split && staged, hbm_budget_bytes, choose_depth(n, dt), &d, &l)) return STARK_ENOMEM;
   const int64_t npad = padded_side(n, d, dt);
@@ -499,9 +498,7 @@ stark_status stark_server_admission(size_t hbm_budget_bytes, int64_t n, stark_dt
 stark_status stark_submit(stark_server_t s, int64_t n, stark_dtype dt, const void* A, const void* B, void* C,
                           uint64_t* req_id) {
   if (!s || !req_id || n < 0 || n > (int64_t)1 << 20) return STARK_EINVAL;
-  if (dt == STARK_F32_SPLIT_FP16) return STARK_EUNSUPPORTED;  // plans only
-  if (dt != STARK_F64 && dt != STARK_F32_SPLIT_BF16 && dt != STARK_F32_SPLIT_TF32 && dt != STARK_I64)
-    return STARK_EINVAL;
+  if (dt != STARK_F64 && dt != STARK_I64 && !is_split(dt)) return STARK_EINVAL;
   if (n > 0 && (!A || !B || !C)) return STARK_EINVAL;
   int d = 0, levels = 0;
   if (!admission(n, dt, needs_stage(n, dt, C), s->budget, -1, &d, &levels)) return STARK_ENOMEM;  // no depth fits

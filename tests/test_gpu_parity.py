@@ -21,6 +21,8 @@ Bars (written here, derived in the comments):
       accumulator promotion every kc of K the term covers kc instead of L
       (plus the fp32 additions of the chunks; tests/bounds.py).
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -898,13 +900,37 @@ def test_fp16_split_range_flag(S):
     check_split(C, want, an, bn, "F32_SPLIT_FP16", A, B, d)
 
 
-def test_fp16_split_is_refused_outside_plans(S):
-    with pytest.raises(S.StarkError) as e:
-        S.Batch([512, 1024], 1, S.DType.F32_SPLIT_FP16)
-    assert e.value.status == S.Status.EUNSUPPORTED
-    with pytest.raises(S.StarkError) as e:
-        S.server_admission(1 << 30, 1024, S.DType.F32_SPLIT_FP16)
-    assert e.value.status == S.Status.EUNSUPPORTED
+def test_fp16_split_in_batches_and_the_server(S):
+    # the grouped launches carry the fp16 format too: a batch and served
+    # requests of 3xFP16 agree with the oracle within the split bounds
+    sizes = [512, 1024, 777]
+    As = [synth.normal(m, 78 + i, 0) for i, m in enumerate(sizes)]
+    Bs = [synth.normal(m, 78 + i, 1) for i, m in enumerate(sizes)]
+    dAs, dBs = [dev(a) for a in As], [dev(b) for b in Bs]
+    Cs = [torch.empty_like(a) for a in dAs]
+    with S.Batch(sizes, 1, S.DType.F32_SPLIT_FP16) as b:
+        b.mul(dAs, dBs, Cs)
+        b.mul(dAs, dBs, Cs)  # a graph replay
+        b.check()
+    with S.Server(1 << 32) as srv:
+        Cr = [torch.empty_like(a) for a in dAs]
+        pending = {srv.submit(a, b, c, S.DType.F32_SPLIT_FP16) for a, b, c in zip(dAs, dBs, Cr)}
+        t0 = time.time()
+        while pending:
+            for rid in list(pending):
+                done, st = srv.poll(rid)
+                if done:
+                    assert st == S.Status.OK
+                    pending.discard(rid)
+            assert time.time() - t0 < 120, "server did not finish"
+            time.sleep(0.0005)
+    for A, B, C, Cs_ in zip(As, Bs, Cs, Cr):
+        want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+        an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+        m = A.shape[0]
+        L = -(-m // 2 // 128) * 128
+        check_split(C.cpu().numpy(), want, an, bn, "F32_SPLIT_FP16", A, B, 1, L)
+        check_split(Cs_.cpu().numpy(), want, an, bn, "F32_SPLIT_FP16")
 
 
 # ----------------------------------------------------------------- full size, sampled rows
