@@ -635,7 +635,7 @@ def main():
     ap.add_argument("--depth", type=int, default=2)
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32", "fp16"])
     ap.add_argument("--seed", type=int, default=2024)
-    ap.add_argument("--e2e-steps", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=36)
     ap.add_argument("--ref-rows", type=int, default=0,
                     help="--impl reference: rows of C per step (0: one per OpenMP thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -777,7 +777,10 @@ def main():
     # ---------------------------------------------------------------- end to end (host buffers)
     # every step copies its inputs host->device and its result device->host
     # (pinned buffers); the asynchronous entry point overlaps one step's
-    # copies with the neighbouring steps' products
+    # copies with the neighbouring steps' products.  On these boxes the first
+    # copies of a round sometimes run at 15-25 GB/s for 50-140 ms (all host
+    # buffers cold at once) before every copy returns to ~200 GB/s; rounds of
+    # 36 products keep that start from dominating the per-product time
     C_hs = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(2)]
     plan.mul_host(A_h, B_h, C_hs[0])
     rounds = []
