@@ -777,10 +777,10 @@ def main():
     # ---------------------------------------------------------------- end to end (host buffers)
     # every step copies its inputs host->device and its result device->host
     # (pinned buffers); the asynchronous entry point overlaps one step's
-    # copies with the neighbouring steps' products.  On these boxes the first
-    # copies of a round sometimes run at 15-25 GB/s for 50-140 ms (all host
-    # buffers cold at once) before every copy returns to ~200 GB/s; rounds of
-    # 36 products keep that start from dominating the per-product time
+    # copies with the neighbouring steps' products.  The host link sometimes
+    # runs a round's first copies at 15-25 GB/s for 50-140 ms before every
+    # copy returns to ~200 GB/s; rounds of 36 products keep that start from
+    # dominating the per-product time
     C_hs = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(2)]
     plan.mul_host(A_h, B_h, C_hs[0])
     rounds = []
