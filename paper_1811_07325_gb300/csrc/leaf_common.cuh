@@ -299,7 +299,9 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        tma_store_3d(it.tC, n0 + chunk * 32, m0 + quarter * 32, it.leaf - p.leaf_begin, ebuf);
+        // the planes are read back only by the combine pass, after the whole
+        // launch: evict-first keeps them from displacing operand panels in L2
+        tma_store_3d_hint(it.tC, n0 + chunk * 32, m0 + quarter * 32, it.leaf - p.leaf_begin, ebuf, pol_c);
         bulk_commit_group();
       }
     } else if (it.use_tma_c) {
