@@ -3,7 +3,6 @@ of the paper's Sec. IV restated with GB300 rates) against the depths timed
 on the device: the model's pick must be within 10 % of the fastest measured
 depth, at several sizes (the U-shaped optimum over the partition count of
 Sec. V-C, found by the model)."""
-import numpy as np
 import pytest
 
 from paper_1811_07325_gb300 import synth
