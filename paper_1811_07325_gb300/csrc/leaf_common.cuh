@@ -361,6 +361,90 @@ __device__ __forceinline__ void epilogue_item(const ItemInfo& it, const LeafTcAr
   }
 }
 
+// One 32 x 32 fp32 box of a tile held in registers (the accumulator-promotion
+// path: a warp holds 32 rows x 128 columns of the promoted sum), combined as
+// epilogue_item does: stored to the leaf's M plane, added into C by TMA bulk
+// reductions (the positive and the negative box one after the other through
+// a single 4 KB staging box), or added by vector atomics.  col0: the box's
+// first column within the tile.
+__device__ __forceinline__ void epilogue_box_regs(const ItemInfo& it, const LeafTcArgs& p, const uint32_t (&r)[32],
+                                                  int col0, int quarter, int lane, uint32_t ebuf, uint64_t pol_c,
+                                                  bool has_pos, bool has_neg, bool vec_ok) {
+  const int m0 = it.m0, n0 = it.n0, nt = it.nt;
+  const CTarget* tg = it.tg;
+  const uint32_t row_addr = ebuf + (uint32_t)lane * 128u;
+  if (p.store_m) {
+    if (lane == 0) bulk_wait_group_read<0>();  // the previous box has been read
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
+      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[4 * c]), "r"(r[4 * c + 1]),
+                   "r"(r[4 * c + 2]), "r"(r[4 * c + 3])
+                   : "memory");
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_3d_hint(it.tC, n0 + col0, m0 + quarter * 32, it.leaf - p.leaf_begin, ebuf, pol_c);
+      bulk_commit_group();
+    }
+  } else if (it.use_tma_c) {
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      if (sg == 0 ? !has_pos : !has_neg) continue;
+      if (lane == 0) bulk_wait_group_read<0>();
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float4 v = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]), __uint_as_float(r[4 * c + 2]),
+                               __uint_as_float(r[4 * c + 3]));
+        if (sg == 1) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+        const uint32_t addr = row_addr + ((uint32_t)(c ^ (lane & 7)) << 4);
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                     : "memory");
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        for (int t = 0; t < nt; ++t) {
+          const CTarget c = tg[t];
+          if ((c.sign > 0) != (sg == 0)) continue;
+          const int64_t y = (int64_t)c.row_off + m0 + quarter * 32;
+          const int64_t x = (int64_t)c.col_off + n0 + col0;
+          if (y >= it.n || x >= it.n) continue;
+          tma_reduce_add_2d(it.tC, (int32_t)x, (int32_t)y, ebuf, pol_c);
+        }
+        bulk_commit_group();
+      }
+    }
+  } else {
+    const int row_in_tile = quarter * 32 + lane;
+#pragma unroll 1
+    for (int t = 0; t < nt; ++t) {
+      const CTarget c = tg[t];
+      const int64_t grow = (int64_t)c.row_off + m0 + row_in_tile;
+      const int64_t gcol = (int64_t)c.col_off + n0 + col0;
+      if (grow >= it.n || gcol >= it.n) continue;
+      float* dst = it.C + grow * it.ldc + gcol;
+      const float sg = (float)c.sign;
+      if (vec_ok && gcol + 32 <= it.n) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 v = make_float4(sg * __uint_as_float(r[4 * j]), sg * __uint_as_float(r[4 * j + 1]),
+                                 sg * __uint_as_float(r[4 * j + 2]), sg * __uint_as_float(r[4 * j + 3]));
+          atomicAdd(reinterpret_cast<float4*>(dst) + j, v);
+        }
+      } else {
+        const int64_t lim = it.n - gcol;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < lim) atomicAdd(dst + j, sg * __uint_as_float(r[j]));
+      }
+    }
+  }
+}
+
 // Persistent launch of a leaf kernel on clusters of two CTAs: as many
 // clusters as can be resident at once (at most one per SM pair), never more
 // than there are work items (items > 0).

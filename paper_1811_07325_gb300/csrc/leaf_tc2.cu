@@ -63,43 +63,24 @@ struct Tc2Cfg {
 };
 
 // Accumulator promotion (LeafTcArgs::promo_kb): a tile's K range is cut
-// into chunks of promo_kb K blocks.  Of the CTA's two TMEM accumulators one
-// holds the tile's running sum (chunk 0 accumulates there directly) and the
-// other takes chunks 1, 2, ...; after each of those the epilogue warps fold
-// it into the running sum on the CUDA cores (fp32, round to nearest) and
-// release it.  The tensor core's own accumulation so spans promo_kb K
-// blocks instead of the whole leaf side.  The two accumulators swap roles
-// from one tile to the next: once the last chunk is folded, the next tile's
-// chunk 0 starts in the released accumulator while the epilogue stores the
-// finished running sum from the other.  The MMAs wait for each fold.
-template <int BN>
-__device__ __forceinline__ void promote_fold(uint32_t tmem_base, uint32_t run_col, uint32_t chunk_col, int quarter) {
-  const uint32_t row = tmem_base + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-  for (int c = 0; c < BN / 64; ++c) {
-    uint32_t a0[32], a1[32], b0[32], b1[32];
-    tmem_ld_32x32b_x32(row + run_col + (uint32_t)(c * 64), a0);
-    tmem_ld_32x32b_x32(row + run_col + (uint32_t)(c * 64 + 32), a1);
-    tmem_ld_32x32b_x32(row + chunk_col + (uint32_t)(c * 64), b0);
-    tmem_ld_32x32b_x32(row + chunk_col + (uint32_t)(c * 64 + 32), b1);
-    tmem_ld_wait();
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      a0[j] = __float_as_uint(__fadd_rn(__uint_as_float(a0[j]), __uint_as_float(b0[j])));
-      a1[j] = __float_as_uint(__fadd_rn(__uint_as_float(a1[j]), __uint_as_float(b1[j])));
-    }
-    tmem_st_32x32b_x32(row + run_col + (uint32_t)(c * 64), a0);
-    tmem_st_32x32b_x32(row + run_col + (uint32_t)(c * 64 + 32), a1);
-  }
-  tmem_st_wait();
-}
+// into chunks of promo_kb K blocks, each accumulated by the tensor core from
+// zero in one of the CTA's two TMEM accumulators, which alternate from chunk
+// to chunk as they alternate from tile to tile otherwise.  Eight epilogue
+// warps (two per TMEM lane quarter, one per 128-column half) load each
+// chunk and add it into a running fp32 sum held in their registers (round
+// to nearest, chunk 0 first), release the accumulator, and after the last
+// chunk combine the sum from registers.  The tensor core's own accumulation
+// so spans promo_kb K blocks instead of the whole leaf side, and the MMAs
+// never wait for the additions: the next chunk goes to the other
+// accumulator.
+constexpr int kThreads2P = 320;  // with promotion: producer, MMA, 8 epilogue warps
 
 // GROUPED: items of several problems (GroupDesc array, tensor maps in global
 // memory), as in the single-CTA kernel's grouped mode.  SIB: sibling-major
 // item order with the sibling-folded combine (LeafTcArgs::sib).  PROMO:
 // accumulator promotion (above; one problem, not with SIB).
 template <bool TF32, bool GROUPED, bool TMN, bool SIB, bool PROMO = false>
-__global__ void __launch_bounds__(kThreads2, 1)
+__global__ void __launch_bounds__(PROMO ? kThreads2P : kThreads2, 1)
     leaf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmC, const LeafTcArgs p) {
   using Cfg = Tc2Cfg<TF32, TMN>;
@@ -139,7 +120,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(accf_bar(a), 1);
-      mbar_init(acce_bar(a), 8);  // even CTA: 4 epilogue warps of each CTA
+      mbar_init(acce_bar(a), PROMO ? 16 : 8);  // even CTA: the epilogue warps of each CTA
     }
     fence_mbar_init();
     if (!GROUPED) {
@@ -278,33 +259,29 @@ __global__ void __launch_bounds__(kThreads2, 1)
         return true;
       };
       if constexpr (PROMO) {
-        // accumulator r is filled f_r times; every fill waits for the
-        // release of the one before (barrier phase parity (f_r & 1) ^ 1).
-        // Tile j keeps its running sum in accumulator j & 1.
-        uint32_t fills0 = 0u, fills1 = 0u;
-        int cur = 0, run = 0;
+        // the two accumulators alternate over the chunks of every item
         const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
-        for (int item = unit; ok && item < num_items; item += units, run ^= 1) {
+        for (int item = unit; ok && item < num_items; item += units) {
           for (int kc = 0; kc < kblocks; kc += ck) {
-            const int r = kc == 0 ? run : run ^ 1;
-            const uint32_t f = r ? fills1 : fills0;
-            if (!mbar_wait_bounded_cluster(acce_bar(r), (f & 1u) ^ 1u, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
+            if (!mbar_wait_bounded_cluster(acce_bar(acc), acc_phase ^ 1, p.err, kDevTimeoutAccEmpty, p.timeout_ns)) {
               ok = false;
               break;
             }
-            cur = r;
             tc_fence_after();
-            if (!run_kblocks(tmem_base + (uint32_t)(r * Cfg::BN), kc, kc + ck < kblocks ? kc + ck : kblocks)) {
+            if (!run_kblocks(tmem_base + (uint32_t)(acc * Cfg::BN), kc, kc + ck < kblocks ? kc + ck : kblocks)) {
               ok = false;
               break;
             }
-            mma2_commit_mc(accf_bar(r), 0x3);  // this chunk is complete in both CTAs
-            if (r) ++fills1; else ++fills0;
+            mma2_commit_mc(accf_bar(acc), 0x3);  // this chunk is complete in both CTAs
+            if (++acc == 2) {
+              acc = 0;
+              acc_phase ^= 1;
+            }
           }
         }
         if (!ok && issued) {
-          mma2_commit_mc(accf_bar(cur), 0x1);
-          mbar_wait_bounded(accf_bar(cur), (cur ? fills1 : fills0) & 1u, nullptr, 0, 200000000ull);
+          mma2_commit_mc(accf_bar(acc), 0x1);
+          mbar_wait_bounded(accf_bar(acc), acc_phase, nullptr, 0, 200000000ull);
         }
       } else {
         for (int item = unit; ok && item < num_items; item += units) {
@@ -339,37 +316,53 @@ __global__ void __launch_bounds__(kThreads2, 1)
     const uint32_t ebuf = epi_base + (uint32_t)(warp - 2) * 8192u;
     const uint64_t pol_c = policy_evict_first();
     if constexpr (PROMO) {
-      uint32_t got0 = 0u, got1 = 0u;  // completed fills of each accumulator seen
+      // warps 2..9: lane quarter warp % 4, columns (warp - 2) / 4 * 128 + 0..127
+      const int half = (warp - 2) >> 2;
+      const uint32_t pbuf = epi_base + (uint32_t)(warp - 2) * 4096u;  // one 32 x 32 fp32 box
+      const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
       const int kblocks = p.L / Cfg::BK, ck = p.promo_kb;
       const int nch = (kblocks + ck - 1) / ck;
+      int acc = 0;
+      uint32_t acc_phase = 0;
       bool ok = true;
-      int run = 0;
-      for (int item = unit; ok && item < num_items; item += units, run ^= 1) {
-        const ItemInfo it = decode(item);
-        const int other = run ^ 1;
-        // chunk 0 in the running accumulator
-        if (!mbar_wait_bounded(accf_bar(run), (run ? got1 : got0) & 1u, p.err, kDevTimeoutAccFull, p.timeout_ns))
-          break;
-        if (run) ++got1; else ++got0;
-        for (int c = 1; c < nch; ++c) {
-          if (!mbar_wait_bounded(accf_bar(other), (other ? got1 : got0) & 1u, p.err, kDevTimeoutAccFull,
-                                 p.timeout_ns)) {
+      for (int item = unit; ok && item < num_items; item += units) {
+        float run[128];
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait_bounded(accf_bar(acc), acc_phase, p.err, kDevTimeoutAccFull, p.timeout_ns)) {
             ok = false;
             break;
           }
-          if (other) ++got1; else ++got0;
           tc_fence_after();
-          promote_fold<Cfg::BN>(tmem_base, (uint32_t)(run * Cfg::BN), (uint32_t)(other * Cfg::BN), quarter);
+          const uint32_t col = lane_base + (uint32_t)(acc * Cfg::BN);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            uint32_t r[16];
+            tmem_ld_32x32b_x16(col + (uint32_t)(j * 16), r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              run[j * 16 + e] = c == 0 ? __uint_as_float(r[e]) : __fadd_rn(run[j * 16 + e], __uint_as_float(r[e]));
+          }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(other), 0));  // the chunk is folded
+          if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(acc), 0));  // the chunk is in registers
+          if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1;
+          }
         }
         if (!ok) break;
-        tc_fence_after();
-        epilogue_item<Cfg::BN, false>(it, p, tmem_base, (uint32_t)(run * Cfg::BN), quarter, lane, ebuf, pol_c);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(mapa_shared(acce_bar(run), 0));
+        const ItemInfo it = decode(item);  // (after the chunks: its registers are not live while they add)
+        bool has_pos = false, has_neg = false;
+        for (int t = 0; t < it.nt; ++t) (it.tg[t].sign > 0 ? has_pos : has_neg) = true;
+        const bool vec_ok = ((reinterpret_cast<uintptr_t>(it.C) & 15) == 0) && ((it.ldc & 3) == 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t r[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(run[j * 32 + e]);
+          epilogue_box_regs(it, p, r, half * 128 + j * 32, quarter, lane, pbuf, pol_c, has_pos, has_neg, vec_ok);
+        }
       }
     } else {
       int acc = 0;
@@ -419,7 +412,7 @@ cudaError_t launch2(const LeafTcArgs& a, const CUtensorMap* tmA, const CUtensorM
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  return launch_cta_pairs(kern, kThreads2, Cfg::SMEM, items, num_sms, st, *tmA, *tmB, *tmC, a);
+  return launch_cta_pairs(kern, PROMO ? kThreads2P : kThreads2, Cfg::SMEM, items, num_sms, st, *tmA, *tmB, *tmC, a);
 }
 
 }  // namespace
