@@ -162,8 +162,9 @@ struct LeafTcArgs {
   int32_t fp16;        // 1: the 16-bit planes hold fp16 halves (kind::f16 A and B format fp16
                        // instead of bf16); 0 for every other dtype and for grouped launches
   int32_t promo_kb;    // > 0 (CTA-pair kernel): accumulator promotion -- every promo_kb K blocks
-                       // the tensor-core partial sum is added into a running fp32 sum on the
-                       // CUDA cores (round to nearest); 0: one tensor-core accumulation over K
+                       // the tensor-core partial sum is added into a running fp32 sum in the
+                       // epilogue warps' registers (round to nearest); 0: one tensor-core
+                       // accumulation over K
   // grouped launch (batch): when groups != nullptr the fields above that
   // describe one problem are ignored and every item is looked up here
   const GroupDesc* groups;
