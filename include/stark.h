@@ -278,8 +278,8 @@ STARK_API stark_status stark_plan_set_tf32_layout(stark_plan_t plan, int mn);
  * additions; the cost is the TMEM reads of each chunk (measured at
  * n = 16384, depth 2: 3xTF32 383 -> 382, 3xFP16 677 -> 654 TFLOP/s with
  * k_chunk = 256).  Applies to the CTA-pair leaf kernel:
- * leaf side a multiple of 256, 256-wide tiles, 3xBF16 or 3xTF32 with the
- * MN-major layout, combine modes 0-2.  Errors: EINVAL (null plan, k_chunk
+ * leaf side a multiple of 256, 256-wide tiles, 3xBF16, 3xFP16 or 3xTF32
+ * with the MN-major layout, combine modes 0-2.  Errors: EINVAL (null plan, k_chunk
  * < 0 or not a multiple of 256), EUNSUPPORTED (another dtype, leaf side or
  * layout, or combine mode 3; a later product whose leaves would run on
  * another kernel also returns EUNSUPPORTED). */
