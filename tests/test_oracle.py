@@ -523,18 +523,20 @@ def test_strassen_abs_2x2_literal():
     assert np.array_equal(oracle.strassen_abs(A, B, 1), want)
 
 
-def emulated_split_product(A, B, d, drop=None):
+def emulated_split_product(A, B, d, drop=None, split=None):
     """The 3xBF16 Strassen product emulated on the CPU from the oracle's
     pieces: fp32 leaf operands (the divide), their bf16 hi/lo split, the
     three kept products per leaf in fp64, combined by W_d.  drop = (leaf,
     row0, col0, size): that tile of that leaf's product is left out, the
-    way a lost output tile of the leaf kernel would be."""
+    way a lost output tile of the leaf kernel would be.  split: another
+    split of the oracle (the fp16 one)."""
+    split = split or oracle.split_bf16
     n = A.shape[0]
     L = n >> d
     X = oracle.strassen_operands(A, n, d, "A")
     Y = oracle.strassen_operands(B, n, d, "B")
-    xh, xl = oracle.split_bf16(X)
-    yh, yl = oracle.split_bf16(Y)
+    xh, xl = split(X)
+    yh, yl = split(Y)
     Wd = kron_table(W, d)
     C = np.zeros((n, n))
     Cq = quadrant_blocks(C, d)
@@ -573,6 +575,35 @@ def test_split_bounds_pass_correct_and_catch_a_dropped_tile(d, kc):
     Cbad, _ = emulated_split_product(A, B, d, drop=(leaf, L - 128, 0, 128))
     assert not np.all(np.abs(Cbad - want) <= c * S)
     assert rel(Cbad) > rms
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_fp16_bound_needs_and_holds_with_its_floor_term(d):
+    # fp16 halves keep values below 2^-14 only to the spacing 2^-24: rows of A
+    # scaled into that range lose relative accuracy, which the relative term
+    # c S alone does not cover; with the absolute floor 2^-25 F (F: the
+    # majorant of |A| with the all-ones matrix and of it with |B|) the bound
+    # holds for the emulated 3xFP16 product, and it still catches a dropped
+    # 128 x 128 output tile
+    import bounds
+    n = 512
+    A = synth.normal(n, 60 + d, 0)
+    B = synth.normal(n, 60 + d, 1)
+    A[: n // 4] *= 2.0 ** -18  # a quarter of the rows far below fp16's normal range
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    S = oracle.strassen_abs(A64, B64, d)
+    L = n >> d
+    F = bounds.floor_majorant(oracle, A64, B64, d, L)
+    c = bounds.componentwise_c("F32_SPLIT_FP16", L, d)
+    C, _ = emulated_split_product(A, B, d, split=oracle.split_fp16)
+    err = np.abs(C - want)
+    assert not np.all(err <= c * S)  # the relative term alone is not enough
+    bound = c * S + bounds.FLOOR["F32_SPLIT_FP16"] * F
+    assert np.all(err <= bound), float((err / bound).max())
+    leaf = 7 ** d - 3
+    Cbad, _ = emulated_split_product(A, B, d, drop=(leaf, L - 128, 0, 128), split=oracle.split_fp16)
+    assert not np.all(np.abs(Cbad - want) <= bound)
 
 
 def test_promoted_bounds_shrink_the_accumulation_term():
