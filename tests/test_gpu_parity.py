@@ -900,6 +900,24 @@ def test_fp16_split_range_flag(S):
     check_split(C, want, an, bn, "F32_SPLIT_FP16", A, B, d)
 
 
+@pytest.mark.parametrize("n,d", [(512, 1), (1000, 2)])
+def test_fp16_split_small_values(S, n, d):
+    # a quarter of A's rows scaled into fp16's subnormal range: their leaf
+    # operands keep only the fixed spacing 2^-24, and the product must still
+    # meet the bound with its absolute floor term (the tensor cores take
+    # fp16 subnormal inputs as they are)
+    A = synth.normal(n, 79 + d, 0)
+    B = synth.normal(n, 79 + d, 1)
+    A[: n // 4] *= 2.0 ** -18
+    want = oracle.gemm_classical(A.astype(np.float64), B.astype(np.float64))
+    an, bn = np.linalg.norm(A.astype(np.float64)), np.linalg.norm(B.astype(np.float64))
+    with S.Plan(n, d, S.DType.F32_SPLIT_FP16) as p:
+        C = p.mul(dev(A), dev(B)).cpu().numpy()
+        p.check()
+        L = p.leaf
+    check_split(C, want, an, bn, "F32_SPLIT_FP16", A, B, d, L)
+
+
 def test_fp16_split_in_batches_and_the_server(S):
     # the grouped launches carry the fp16 format too: a batch and served
     # requests of 3xFP16 agree with the oracle within the split bounds
