@@ -580,7 +580,8 @@ def run_sharded(args, stark, synth, torch, dist, rank, world, local):
 
 def workload_config(args, depth):
     n = args.n
-    return {"workload": f"strassen n={n} depth={depth} fp32 N(0,1) split-{args.dtype}", "n": n, "depth": depth,
+    promo = f", accumulator promotion every {args.promotion} of K" if getattr(args, "promotion", 0) else ""
+    return {"workload": f"strassen n={n} depth={depth} fp32 N(0,1) split-{args.dtype}{promo}", "n": n, "depth": depth,
             "per_rank": "one independent product per rank",
             "l2": "inputs (2 x 1 GiB) and workspace larger than L2; no flush needed"}
 
@@ -650,6 +651,8 @@ def main():
     ap.add_argument("--deep-pipeline", type=int, default=-1)
     ap.add_argument("--raster", type=int, default=-1, help="leaf tile raster band (0: row-major)")
     ap.add_argument("--traversal", type=int, default=0, help="k > 0: depth first over the top k levels")
+    ap.add_argument("--promotion", type=int, default=0,
+                    help="accumulator promotion of the main plan every K of the leaf side (0: off)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--deadline", type=float, default=900.0,
                     help="seconds after which the line gathered so far is printed and the run ends")
@@ -706,6 +709,8 @@ def main():
         plan.set_raster(args.raster)
     if args.traversal:
         plan.set_traversal(args.traversal)
+    if args.promotion:
+        plan.set_promotion(args.promotion)
     stream = torch.cuda.current_stream()
 
     def barrier():
